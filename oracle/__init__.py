@@ -1,0 +1,22 @@
+"""FP64 CPU oracle for the generalized-Poisson pressure solve.
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously correct
+restatement in numpy/scipy (float64) of what the solver computes.  It shares
+no code with the CUDA library and imports nothing from it.  Only the test
+suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import it; the product path never does.
+
+Modules
+  poisson    the discrete operator A = c~ - div(kappa grad) (Eq. Poiss /
+             GeneralizedPoisson with Eqs. cpoiss, kappapoiss), its assembly,
+             and reference solves (dense Cholesky, sparse direct, Jacobi-PCG).
+  multigrid  the geometric-multigrid V-cycle the GPU uses as preconditioner
+             (coarsening, restriction, prolongation, red-black Gauss-Seidel),
+             written level by level.
+  unet       the learned warm start's network layers in float64 (forward and
+             hand-derived backward).
+
+Pins (what fixes each function to something other than itself) live in
+tests/test_oracle_*.py.  Functions whose result has no such pin say
+"parity unpinned" in their docstring.
+"""
