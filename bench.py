@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the generalized-Poisson pressure solve (one solve = one step).
+
+Workload (default): the 3D 256^3 stratified-convection pressure solve --
+x,y periodic, z walls, 20x density contrast with 1% seeded noise, dt at
+Ma = 0.01 -- solved to relative residual 1e-8 by the mixed-precision mode
+(float32 flexible CG + geometric multigrid inside float64 iterative
+refinement).  A step is the whole hot path: coefficient assembly from
+rho^n, rho^{n+1}, c_s^2, dt; multigrid hierarchy set-up; the refinement
+solve to tolerance.  Inputs (4 x 134 MB) already sit in HBM and exceed L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  value = cells solved to rtol per second
+over the whole job (GDOF/s; N GPUs run independent replicas: weak scaling).
+The float64 Jacobi-PCG baseline is timed on the same GPU after the timed
+region; `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 residual & GDOF-iter/s: mixed+learned vs FP64 PCG, same GPU"
+UNIT = "GDOF/s"
+WORKLOADS = {
+    "convection256": dict(kind="conv3d", n=256, desc="3D 256^3 convection, rho contrast 20 + 1% noise, "
+                                                    "Ma=0.01, x/y periodic, z walls, rtol 1e-8"),
+    "convection128": dict(kind="conv3d", n=128, desc="3D 128^3 convection (reduced), Ma=0.01, rtol 1e-8"),
+    "plain64": dict(kind="plain2d", n=64, desc="2D 64^2 polytrope, Ma=0.1, rtol 1e-10"),
+}
+
+
+def make_problem(name: str, seed: int = 1):
+    from paper_1112_3507_gb300 import inputs as I
+    w = WORKLOADS[name]
+    if w["kind"] == "conv3d":
+        return I.config_convection_3d(w["n"], seed=seed)
+    return I.config_plain_2d(w["n"], seed=seed)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(name: str, iters: int = 2, seed: int = 1) -> dict:
+    """Time the oracle's float64 Jacobi-PCG on the workload (single-threaded
+    numpy): one run of 1 iteration and one of 1 + `iters` iterations give the
+    set-up time and the time per iteration.  The oracle's own iteration count
+    to the workload's tolerance is measured on downsized grids (n/16, n/8,
+    n/4) and extrapolated by the fitted growth per grid doubling.  Returns the
+    estimated time to tolerance and the GDOF/s it implies."""
+    from oracle import poisson as P
+    from paper_1112_3507_gb300 import inputs as I
+    w = WORKLOADS[name]
+    p = make_problem(name, seed)
+    op = P.operator_from_problem(p)
+    P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1)          # warm-up (first-touch of the arrays)
+    t0 = time.perf_counter()
+    P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1)
+    t1 = time.perf_counter()
+    _, it, _ = P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1 + iters)
+    t2 = time.perf_counter()
+    t_iter = max((t2 - t1) - (t1 - t0), 1e-9) / max(it - 1, 1)
+    t_setup = max((t1 - t0) - t_iter, 0.0)
+    counts = []
+    n = w["n"]
+    sizes = [n // 16, n // 8, n // 4] if w["kind"] == "conv3d" else [n]
+    for m in sizes:
+        q = I.config_convection_3d(m, seed=seed) if w["kind"] == "conv3d" else p
+        _, c, _ = P.solve_pcg_jacobi(P.operator_from_problem(q), q.f, rtol=p.rtol)
+        counts.append(c)
+    if len(counts) > 1:
+        growth = (counts[-1] / counts[0]) ** (1.0 / (len(counts) - 1))
+        est_iters = counts[-1] * growth ** 2          # n/4 -> n is two doublings
+    else:
+        est_iters = counts[0]
+    est_s = t_setup + t_iter * est_iters
+    return dict(t_iter_s=t_iter, t_setup_s=t_setup, sample_iters=it + 1, est_iters=float(est_iters),
+                downsized_counts=counts, est_time_s=est_s, value=p.size / est_s / 1e9, N=p.size)
+
+
+def oracle_subprocess(name: str, iters: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print('ORACLE_JSON', json.dumps(bench.oracle_sample(%r, %d)))" % (ROOT, name, iters))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    for line in r.stdout.splitlines():
+        if line.startswith("ORACLE_JSON"):
+            return json.loads(line.split(" ", 1)[1])
+    raise RuntimeError("oracle sample failed:\n" + r.stdout[-2000:] + r.stderr[-2000:])
+
+
+def cpu_block(s: dict, name: str) -> dict:
+    return {"value": s["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{s['sample_iters']} iterations of the FP64 oracle's Jacobi-PCG on {name} "
+                       f"({s['t_iter_s']:.3f} s/iter + {s['t_setup_s']:.2f} s set-up, single-threaded numpy) "
+                       f"x its iteration count to rtol "
+                       f"extrapolated from downsized grids {s['downsized_counts']} -> {s['est_iters']:.0f}; "
+                       f"estimated time to tolerance {s['est_time_s']:.1f} s")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    samples = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        s = oracle_sample(args.workload, iters=args.oracle_iters)
+        if step >= args.warmup:
+            samples.append((s, time.perf_counter() - t0))
+    vals = [s["value"] for s, _ in samples]
+    s0 = samples[-1][0]
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": s0["est_time_s"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload]["desc"], "cells": s0["N"]},
+            "cpu_baseline": cpu_block(s0, args.workload),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def time_kernel(torch, fn, reps: int, stream) -> float:
+    """Average duration (s) of fn() launched `reps` times, CUDA events on `stream`."""
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e-3 / reps
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1112_3507_gb300 import lowmach as lm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    p = make_problem(args.workload, seed=1)
+    N = p.size
+    ro, rn, c2, f = (torch.as_tensor(a.ravel(), device=dev) for a in (p.rho_old, p.rho_new, p.cs2, p.f))
+    g = lm.Grid.for_problem(p)
+    solve_kw = dict(mode=args.mode, rtol=p.rtol, max_iter=args.max_iter)
+
+    def step():
+        g.set_coefficients(ro, rn, c2, p.dt, stream)
+        g.set_rhs(f, stream)
+        return g.solve(stream=stream, **solve_kw)
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    launches0 = lm.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    results = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    e1.synchronize()
+    launches = lm.kernel_launches() - launches0
+    barrier()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) * 1e-3
+    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed = float(t.item())
+    res = results[-1]
+    assert all(r["status"] == 0 and r["rel_residual"] <= p.rtol for r in results), results
+    value = world * N * args.steps / elapsed / 1e9
+    t_solve = elapsed / args.steps
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    host = [torch.from_numpy(np.ascontiguousarray(a.ravel())).pin_memory() for a in (p.rho_old, p.rho_new, p.cs2, p.f)]
+    hn = [h.numpy() for h in host]
+    xout = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+
+    def e2e_step():
+        g.set_coefficients(hn[0], hn[1], hn[2], p.dt, stream)
+        g.set_rhs(hn[3], stream)
+        r = g.solve(stream=stream, **solve_kw)
+        g.solution(xout, stream)
+        return r
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_t = float(t.item())
+
+    # ---- the float64 Jacobi-PCG baseline and the float64 multigrid mode, same GPU
+    base = {}
+    for mode in ("jacobi", "fp64-mg"):
+        step_b = lambda: (g.set_coefficients(ro, rn, c2, p.dt, stream), g.set_rhs(f, stream),
+                          g.solve(stream=stream, mode=mode, rtol=p.rtol, max_iter=args.max_iter))[-1]
+        step_b()
+        torch.cuda.synchronize()
+        b0 = time.perf_counter()
+        rb = step_b()
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - b0
+        base[mode] = {"time_to_tol_ms": tb * 1e3, "iters": rb["iters"], "rel_residual": rb["rel_residual"],
+                      "gdof_iter_per_s": N * rb["iters"] / tb / 1e9}
+
+    # ---- roofline of the dominant kernel, timed alone via its row-level entry point
+    g.set_coefficients(ro, rn, c2, p.dt, stream)
+    x32 = torch.randn(N, dtype=torch.float32, device=dev)
+    y32 = torch.empty_like(x32)
+    reps = 20
+    t_k = time_kernel(torch, lambda: g.apply(x32, y32, prec=lm.PREC_FP32, stream=stream), reps, stream)
+    bytes_per_cell = 16          # read x, rho, c~; write y (float32), faces formed on the fly
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = bytes_per_cell * N / t_k / 1e9
+    x64 = torch.randn(N, dtype=torch.float64, device=dev)
+    y64 = torch.empty_like(x64)
+    t_k64 = time_kernel(torch, lambda: g.apply(x64, y64, prec=lm.PREC_FP64, stream=stream), reps, stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_block(oracle_subprocess(args.workload, args.oracle_iters), args.workload)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64 (float32 multigrid/Krylov, float64 residual/refinement)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "cells": N, "mode": args.mode,
+                       "rtol": p.rtol, "l2": "inputs exceed L2 (4 x %.0f MB)" % (N * 8 / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "time_to_tol_ms": t_solve * 1e3,
+            "solve": {"iters": res["iters"], "outer_iters": res["outer_iters"], "vcycles": res["vcycles"],
+                      "rel_residual": res["rel_residual"],
+                      "gdof_iter_per_s": N * res["iters"] / t_solve / 1e9},
+            "fp64_jacobi_pcg": base["jacobi"], "fp64_mg_fcg": base["fp64-mg"],
+            "speedup_vs_fp64_pcg": base["jacobi"]["time_to_tol_ms"] / (t_solve * 1e3),
+            "e2e": {"value": world * N * args.steps / e2e_t / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": 4 * 8 * N, "d2h_bytes_per_step": 8 * N},
+            "roofline": {"kernel": "k_apply32 (float32 stencil apply, row a2)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "bytes_per_cell": bytes_per_cell, "launch_us": t_k * 1e6,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
+                         "fp64_apply_launch_us": t_k64 * 1e6},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="convection256")
+    ap.add_argument("--mode", default="mixed")
+    ap.add_argument("--max-iter", type=int, default=20000)
+    ap.add_argument("--oracle-iters", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.max_iter = args.max_iter
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

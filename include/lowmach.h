@@ -1,0 +1,215 @@
+/*
+ * lowmach.h -- C ABI of the GB300 generalized-Poisson pressure solver.
+ *
+ * The solver computes the pressure prediction of the semi-implicit low-Mach
+ * fractional-step method of Happenhofer et al. (arXiv 1112.3507): every
+ * timestep (every Runge-Kutta stage, Sec. 2.6) it solves
+ *
+ *     c~ P - div(kappa grad P) = f                       (Sec. 2, Eq. Poiss;
+ *                                        Sec. 2.5, Eq. GeneralizedPoisson)
+ *     c~    = 1 / (dt^2 rho^n c_s^2)                      (Eq. cpoiss)
+ *     kappa = 1 / rho^{n+1}                               (Eq. kappapoiss)
+ *
+ * with homogeneous Neumann walls (Eq. vonNeumannBC) or periodic axes
+ * (Sec. 3.2), on a cell-centred structured 2D/3D grid.  Discretization: the
+ * cell-centred finite-volume operator
+ *
+ *     (A x)_i = c~_i x_i + sum_{faces f of i} g_f (x_i - x_nb(f)),
+ *     g_f = kappa_f / h_axis^2,  kappa_f = 2 / (rho_L + rho_R),
+ *
+ * the face kappa being the harmonic mean of 1/rho (the factor of the
+ * face-velocity update, step (viii) of Sec. 2.4).  A is symmetric positive
+ * definite whenever rho > 0 and c~ > 0 (Sec. 2.5: Lax-Milgram conditions).
+ *
+ * Layout: every field is a dense array of n[0]*n[1]*n[2] values, x fastest:
+ * flat index i + n[0]*(j + n[1]*k).  A 2D grid has ndim = 2, n[1] = 1 (x is
+ * horizontal, the second extent n[2] is vertical).  All values are float64
+ * unless stated.
+ *
+ * Pointers: arguments named *_on_device / on_device = 1 are CUDA device
+ * pointers on the grid's device (for instance torch.Tensor.data_ptr());
+ * on_device = 0 means host memory.  Input pointers are borrowed: the library
+ * copies what it needs before returning (device copies are ordered on the
+ * given stream).  Output buffers are allocated by the caller.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream); every kernel of a call runs
+ * on it.
+ *
+ * Errors: 0 = LM_OK, negative = failure (see lm_status_string).  A failing
+ * call leaves the grid usable.  Calls on one grid are not reentrant; distinct
+ * grids may be used from distinct threads.
+ *
+ * Every entry point runs its arithmetic in this library's CUDA kernels; there
+ * is no CPU fallback.  A grid's device is the current CUDA device at
+ * lm_grid_create.
+ */
+#ifndef LOWMACH_H
+#define LOWMACH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LM_OK                  0
+#define LM_ERR_INVALID_ARG    -1   /* bad size, pointer, enum or option           */
+#define LM_ERR_NOT_POSITIVE   -2   /* rho <= 0, c_s^2 <= 0, dt <= 0, c~ <= 0 or
+                                      non-finite input: the Lax-Milgram
+                                      positivity of Sec. 2.5 fails               */
+#define LM_ERR_NO_CONVERGENCE -3   /* max_iter reached; solution and history kept */
+#define LM_ERR_BREAKDOWN      -4   /* p^T A p <= 0 or non-finite inside a Krylov
+                                      iteration                                  */
+#define LM_ERR_TIMEOUT        -5   /* a bounded device-side wait expired           */
+#define LM_ERR_CUDA           -6   /* a CUDA runtime call failed                   */
+#define LM_ERR_NETWORK        -7   /* network weights missing or malformed         */
+#define LM_ERR_OUT_OF_MEMORY  -8
+#define LM_ERR_STATE          -9   /* a required input (coefficients, rhs) unset  */
+
+/* ---- enums ------------------------------------------------------------- */
+#define LM_BC_PERIODIC 0
+#define LM_BC_NEUMANN  1
+
+/* Solve modes.
+ *  LM_FP64_JACOBI_PCG   conjugate gradients (Sec. 2.5) in float64 with the
+ *                       Jacobi preconditioner: the plain GPU baseline.
+ *  LM_FP64_MG_PCG       float64 vectors, conjugate gradients preconditioned
+ *                       by a float32 geometric-multigrid V-cycle.
+ *  LM_MIXED_MG_IR       iterative refinement: float64 residual and
+ *                       correction, float32 inner flexible CG with the
+ *                       multigrid V-cycle (float64-accurate dot products).
+ *  LM_MIXED_LEARNED_FCG_IR  as LM_MIXED_MG_IR, with the learned network's
+ *                       warm start and the network as preconditioner inside
+ *                       flexible CG (falls back to LM_MIXED_MG_IR when no
+ *                       network is loaded or the network output is unusable).
+ */
+#define LM_FP64_JACOBI_PCG      0
+#define LM_FP64_MG_PCG          1
+#define LM_MIXED_MG_IR          2
+#define LM_MIXED_LEARNED_FCG_IR 3
+
+#define LM_PREC_FP64 0
+#define LM_PREC_FP32 1
+
+typedef struct lm_grid lm_grid;
+
+typedef struct {
+    int    mode;            /* LM_FP64_JACOBI_PCG ...                              */
+    double rtol;            /* stop when ||f - A x||_2 <= rtol ||f||_2 (true
+                               float64 residual, unweighted over cells)          */
+    int    max_iter;        /* Krylov iterations (all inner iterations in IR)     */
+    int    use_x0;          /* 1: start from lm_set_initial_guess, 0: from zero   */
+    int    max_outer;       /* iterative-refinement steps (mixed modes)           */
+    int    nu1, nu2;        /* red-black Gauss-Seidel sweeps before/after the
+                               coarse correction; nu1 == nu2 keeps the V-cycle
+                               symmetric                                          */
+    double inner_rtol;      /* relative reduction asked of each inner solve      */
+    int    inner_max_iter;  /* inner iterations per refinement step               */
+    int    check_every;     /* Krylov iterations between host convergence checks */
+    void*  cuda_stream;     /* cudaStream_t for every kernel of the solve         */
+} lm_solve_opts;
+
+typedef struct {
+    int    status;          /* LM_OK or an LM_ERR_* code                          */
+    int    iters;           /* Krylov iterations (inner iterations summed)        */
+    int    outer_iters;     /* refinement steps (mixed modes), else 0             */
+    int    vcycles;         /* multigrid V-cycles applied                         */
+    double rel_residual;    /* final true relative residual ||f-Ax||/||f||, fp64 */
+    double seconds;         /* device time of the solve (CUDA events)             */
+} lm_solve_result;
+
+/* Defaults: mode LM_MIXED_MG_IR, rtol 1e-8, max_iter 10000, nu1 = nu2 = 1,
+ * inner_rtol 1e-3, inner_max_iter 30, max_outer 12, check_every 8. */
+void lm_default_opts(lm_solve_opts* opts);
+
+/* ---- grid lifecycle ---------------------------------------------------- */
+
+/* Create a grid of n[0] x n[1] x n[2] cells with spacings h[0..2] and one
+ * boundary condition per axis (bc[a] in {LM_BC_PERIODIC, LM_BC_NEUMANN},
+ * applied at both ends of axis a).  ndim 2 requires n[1] == 1.  Allocates
+ * the grid's device buffers on the current device.  Errors:
+ * LM_ERR_INVALID_ARG (non-positive sizes or spacings, bad bc),
+ * LM_ERR_OUT_OF_MEMORY. */
+int  lm_grid_create(int ndim, const int64_t n[3], const double h[3], const int bc[3], lm_grid** out);
+void lm_grid_destroy(lm_grid* g);
+int64_t lm_grid_size(const lm_grid* g);
+
+/* ---- inputs ------------------------------------------------------------ */
+
+/* Coefficient assembly (step (v) of Sec. 2.4): from rho^n, rho^{n+1}, c_s^2
+ * (N values each) and dt, form c~ (Eq. cpoiss) and the face conductances
+ * g_f from kappa = 1/rho^{n+1} (Eq. kappapoiss), the Jacobi diagonal and the
+ * float32 copies used by multigrid.  Validates positivity and finiteness:
+ * on LM_ERR_NOT_POSITIVE the grid holds no valid coefficients until the next
+ * successful call (a solve then returns LM_ERR_STATE). */
+int  lm_set_coefficients(lm_grid* g, const double* rho_old, const double* rho_new,
+                         const double* cs2, double dt, int on_device, void* stream);
+
+/* As lm_set_coefficients, with c~ given directly (N values) and kappa taken
+ * as 1/rho_face_src: for problems stated in c~ and kappa (e.g. the solver
+ * test of Sec. 2.5.2, kappa = 1/rho). */
+int  lm_set_coefficients_raw(lm_grid* g, const double* ctilde, const double* rho_face_src,
+                             int on_device, void* stream);
+
+/* Right-hand side f (Eq. fpoiss / fpoiss2), N values, per unit volume in the
+ * units of c~ P.  Inhomogeneous Neumann data g (outward normal derivative)
+ * is folded in by the caller: f_i += kappa_wall g / h for wall cells. */
+int  lm_set_rhs(lm_grid* g, const double* f, int on_device, void* stream);
+
+/* Initial guess x0 (N values), used when opts.use_x0 = 1. */
+int  lm_set_initial_guess(lm_grid* g, const double* x0, int on_device, void* stream);
+
+/* Load the learned warm-start/preconditioner network (file written by
+ * lm_unet_save); LM_ERR_NETWORK if missing or malformed. */
+int  lm_load_network(lm_grid* g, const char* weights_path);
+
+/* ---- solve --------------------------------------------------------------- */
+
+/* Solve A P = f (step (vi) of Sec. 2.4) to opts->rtol in the chosen mode.
+ * Returns LM_OK, LM_ERR_NO_CONVERGENCE (best iterate kept), LM_ERR_BREAKDOWN,
+ * LM_ERR_STATE (coefficients or rhs missing), LM_ERR_INVALID_ARG (e.g. a
+ * multigrid mode on a periodic axis with an odd cell count > 1).  `res` may
+ * be NULL.  Synchronises the stream before returning. */
+int  lm_solve(lm_grid* g, const lm_solve_opts* opts, lm_solve_result* res);
+
+/* Copy the solution (N float64 values) out. */
+int  lm_get_solution(lm_grid* g, double* out, int on_device, void* stream);
+
+/* Relative residual ||r_k||/||f|| of every Krylov iteration of the last
+ * solve (index 0 = initial residual); writes min(cap, count) values. */
+int  lm_get_residual_history(lm_grid* g, double* out, int cap, int* n_written);
+
+const char* lm_status_string(int status);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all grids, all streams); for launch accounting in benchmarks. */
+int64_t lm_kernel_launches(void);
+
+/* ---- row-level entry points (device pointers, caller's stream) -------- */
+
+/* The assembled float64 coefficients: c~ (N), and per axis a the
+ * conductance g of each cell's face with its minus-neighbour (N each; 0 on
+ * a wall face and on an axis with one cell).  Any pointer may be NULL. */
+int  lm_get_coefficients(lm_grid* g, double* ctilde, double* gx, double* gy, double* gz,
+                         void* stream);
+
+/* y = A x on device vectors of N values, float64 (prec LM_PREC_FP64, x and y
+ * double*) or float32 (LM_PREC_FP32, float*, faces formed from float32
+ * rho).  If dot_out != NULL it receives x^T A x accumulated to float64
+ * accuracy (host pointer; the call then synchronises the stream). */
+int  lm_apply(lm_grid* g, int prec, const void* x, void* y, double* dot_out, void* stream);
+
+/* One float32 multigrid V-cycle z = M r (zero initial guess, nu1/nu2
+ * red-black Gauss-Seidel sweeps, exact coarsest solve), the preconditioner
+ * of the multigrid modes; r, z float32 device vectors of N values.  Builds
+ * the hierarchy from the current coefficients if needed. */
+int  lm_mg_vcycle(lm_grid* g, const float* r, float* z, int nu1, int nu2, void* stream);
+
+/* Number of multigrid levels and the cell counts of level `level`
+ * (n_out[3]); LM_ERR_INVALID_ARG past the coarsest level. */
+int  lm_mg_level_shape(lm_grid* g, int level, int64_t n_out[3], int* num_levels);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOWMACH_H */

@@ -1,0 +1,700 @@
+// C ABI of the generalized-Poisson solver: grid object, inputs, solve
+// drivers (float64 Jacobi-PCG, float64 flexible CG with the float32
+// multigrid preconditioner, mixed-precision iterative refinement) and the
+// row-level entry points.  Host code here only sequences kernels on the
+// caller's stream and reads back a few scalars; all arithmetic on grid data
+// runs in the kernels of lm_fp64.cu / lm_fp32.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lowmach.h"
+#include "lm_common.cuh"
+#include "lm_kernels.h"
+
+using namespace lm;
+
+static std::atomic<long long> g_launches{0};
+void lm::count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int COARSE_MAX = 64;      // coarsest level solved exactly below this size
+constexpr int COARSE_SWEEPS = 32;   // (RB, BR) sweep pairs when it cannot be
+
+struct MgLevel {
+    Lev32 L;
+    double h[3];
+    int halved[3] = {0, 0, 0};      // axes halved to reach the next level
+    float* ct = nullptr;            // owned on levels >= 1
+    float* rho = nullptr;
+    float* x = nullptr;             // correction (levels >= 1)
+    float* f = nullptr;             // right-hand side (levels >= 1)
+    float* ainv = nullptr;          // dense inverse on a direct coarsest level
+};
+
+}  // namespace
+
+struct lm_grid {
+    int ndim = 0;
+    int n[3] = {1, 1, 1};
+    double h[3] = {1, 1, 1};
+    int bc[3] = {0, 0, 0};
+    int N = 0;
+    int device = 0;
+    int G = 1;          // blocks of the grid-stride streaming kernels
+    Geo geo{};
+
+    double *ct = nullptr, *gx = nullptr, *gy = nullptr, *gz = nullptr, *dinv = nullptr;
+    double *f = nullptr, *x = nullptr, *x0 = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    float *ct32 = nullptr, *rho32 = nullptr;
+    float *r32 = nullptr, *e32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    double* stage = nullptr;        // 3N host-input staging (allocated on first use)
+    double* part = nullptr;         // NSLOT * MAX_PARTIALS
+    double* dscal = nullptr;        // device scalars for lm_apply dots
+    SolveState* st = nullptr;       // outer solve state
+    SolveState* st_in = nullptr;    // inner (float32) solve state
+    SolveState* st_host = nullptr;  // pinned mirror
+    double* hist_dev = nullptr;
+    int hist_cap = 0;
+    int* bad = nullptr;
+    int* bad_host = nullptr;
+    double* dscal_host = nullptr;
+
+    bool have_coefs = false, have_rhs = false, have_x0 = false;
+    bool mg_built = false;
+    std::vector<MgLevel> mg;
+    std::vector<double> history;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+#define CK(call)                                                        \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) {                                        \
+            fprintf(stderr, "lowmach: %s failed: %s (%s:%d)\n", #call,  \
+                    cudaGetErrorString(e_), __FILE__, __LINE__);        \
+            return e_ == cudaErrorMemoryAllocation ? LM_ERR_OUT_OF_MEMORY : LM_ERR_CUDA; \
+        }                                                               \
+    } while (0)
+
+namespace {
+
+template <class T>
+int dalloc(T** p, size_t count) {
+    CK(cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)));
+    return LM_OK;
+}
+
+inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+Op64 op64(const lm_grid* g) { return Op64{g->ct, g->gx, g->gy, g->gz, g->dinv}; }
+
+bool halvable(int n, int bc) {
+    if (n < 2 || (n % 2)) return false;
+    if (bc == LM_BC_PERIODIC) return ((n / 2) % 2 == 0) || n / 2 == 1;
+    return true;
+}
+
+Lev32 make_lev(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho) {
+    Lev32 L{};
+    L.g.nx = n[0];
+    L.g.ny = n[1];
+    L.g.nz = n[2];
+    L.g.N = n[0] * n[1] * n[2];
+    L.g.bcx = bc[0];
+    L.g.bcy = bc[1];
+    L.g.bcz = bc[2];
+    L.g.ih2x = 1.0 / (h[0] * h[0]);
+    L.g.ih2y = 1.0 / (h[1] * h[1]);
+    L.g.ih2z = 1.0 / (h[2] * h[2]);
+    L.c2x = (float)(2.0 / (h[0] * h[0]));
+    L.c2y = (float)(2.0 / (h[1] * h[1]));
+    L.c2z = (float)(2.0 / (h[2] * h[2]));
+    L.ct = ct;
+    L.rho = rho;
+    return L;
+}
+
+int sync_state(lm_grid* g, SolveState* dev, cudaStream_t s) {
+    CK(cudaMemcpyAsync(g->st_host, dev, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return LM_OK;
+}
+
+void free_mg(lm_grid* g) {
+    for (size_t l = 0; l < g->mg.size(); ++l) {
+        MgLevel& M = g->mg[l];
+        if (l > 0) {
+            cudaFree(M.ct);
+            cudaFree(M.rho);
+            cudaFree(M.x);
+            cudaFree(M.f);
+        }
+        cudaFree(M.ainv);
+    }
+    g->mg.clear();
+    g->mg_built = false;
+}
+
+bool mg_supported(const lm_grid* g) {
+    for (int a = 0; a < 3; ++a)
+        if (g->bc[a] == LM_BC_PERIODIC && g->n[a] > 1 && (g->n[a] % 2)) return false;
+    return true;
+}
+
+// Multigrid hierarchy from the float32 coefficients (coarse c~, rho = child means).
+int build_mg(lm_grid* g, cudaStream_t s) {
+    if (g->mg_built) return LM_OK;
+    free_mg(g);
+    MgLevel L0;
+    L0.L = make_lev(g->n, g->bc, g->h, g->ct32, g->rho32);
+    std::memcpy(L0.h, g->h, sizeof L0.h);
+    g->mg.push_back(L0);
+    while (g->mg.back().L.g.N > COARSE_MAX) {
+        MgLevel& F = g->mg.back();
+        int nf[3] = {F.L.g.nx, F.L.g.ny, F.L.g.nz};
+        int hv[3];
+        bool any = false;
+        for (int a = 0; a < 3; ++a) {
+            hv[a] = halvable(nf[a], g->bc[a]) ? 1 : 0;
+            any = any || hv[a];
+        }
+        if (!any) break;
+        MgLevel C;
+        int nc[3];
+        for (int a = 0; a < 3; ++a) {
+            nc[a] = hv[a] ? nf[a] / 2 : nf[a];
+            C.h[a] = F.h[a] * (hv[a] ? 2.0 : 1.0);
+            F.halved[a] = hv[a];
+        }
+        const int Nc = nc[0] * nc[1] * nc[2];
+        int rc;
+        if ((rc = dalloc(&C.ct, Nc)) || (rc = dalloc(&C.rho, Nc)) || (rc = dalloc(&C.x, Nc)) ||
+            (rc = dalloc(&C.f, Nc)))
+            return rc;
+        C.L = make_lev(nc, g->bc, C.h, C.ct, C.rho);
+        launch_coarsen(F.L, C.L, hv[0], hv[1], hv[2], s, C.ct, C.rho);
+        g->mg.push_back(C);
+    }
+    MgLevel& Lc = g->mg.back();
+    if (Lc.L.g.N <= COARSE_MAX) {
+        int rc = dalloc(&Lc.ainv, (size_t)Lc.L.g.N * Lc.L.g.N);
+        if (rc) return rc;
+        launch_coarse_inverse(Lc.L, s, Lc.ainv);
+    }
+    CK(cudaGetLastError());
+    g->mg_built = true;
+    return LM_OK;
+}
+
+// One V-cycle on level l: x = M_l f (zero initial guess).
+void vcycle(lm_grid* g, int l, float* x, const float* f, int nu1, int nu2, cudaStream_t s) {
+    MgLevel& M = g->mg[l];
+    const bool last = (size_t)l + 1 == g->mg.size();
+    if (last) {
+        if (M.ainv) {
+            launch_coarse_solve(M.L.g.N, s, M.ainv, f, x);
+        } else {
+            for (int it = 0; it < COARSE_SWEEPS; ++it) {
+                launch_smooth(M.L, s, x, f, 0, it == 0);
+                launch_smooth(M.L, s, x, f, 1, 0);
+                launch_smooth(M.L, s, x, f, 1, 0);
+                launch_smooth(M.L, s, x, f, 0, 0);
+            }
+        }
+        return;
+    }
+    if (nu1 == 0) cudaMemsetAsync(x, 0, sizeof(float) * M.L.g.N, s);
+    for (int it = 0; it < nu1; ++it) {
+        launch_smooth(M.L, s, x, f, 0, it == 0);
+        launch_smooth(M.L, s, x, f, 1, 0);
+    }
+    MgLevel& C = g->mg[l + 1];
+    launch_resid_restrict(M.L, C.L, M.halved[0], M.halved[1], M.halved[2], s, x, f, C.f);
+    vcycle(g, l + 1, C.x, C.f, nu1, nu2, s);
+    launch_prolong_add(M.L, C.L, M.halved[0], M.halved[1], M.halved[2], s, x, C.x);
+    for (int it = 0; it < nu2; ++it) {
+        launch_smooth(M.L, s, x, f, 1, 0);
+        launch_smooth(M.L, s, x, f, 0, 0);
+    }
+}
+
+PcgArgs pcg_args(lm_grid* g, int max_iter) {
+    PcgArgs a;
+    a.g = g->geo;
+    a.op = op64(g);
+    a.f = g->f;
+    a.x = g->x;
+    a.r = g->r;
+    a.p = g->p;
+    a.q = g->q;
+    a.part = g->part;
+    a.st = g->st;
+    a.hist = g->hist_dev;
+    a.max_iter = max_iter;
+    return a;
+}
+
+int ensure_hist(lm_grid* g, int n) {
+    if (g->hist_cap >= n) return LM_OK;
+    cudaFree(g->hist_dev);
+    g->hist_dev = nullptr;
+    g->hist_cap = 0;
+    int rc = dalloc(&g->hist_dev, n);
+    if (rc) return rc;
+    g->hist_cap = n;
+    return LM_OK;
+}
+
+int init_state(lm_grid* g, SolveState* st, double rtol, cudaStream_t s) {
+    SolveState h{};
+    h.rtol = rtol;
+    CK(cudaMemcpyAsync(st, &h, sizeof h, cudaMemcpyHostToDevice, s));
+    // the copy reads a stack object: wait for it before returning
+    CK(cudaStreamSynchronize(s));
+    return LM_OK;
+}
+
+// ---- float64 Jacobi-PCG ------------------------------------------------------
+int solve_jacobi_pcg(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
+    cudaStream_t s = S(o->cuda_stream);
+    int rc;
+    if ((rc = ensure_hist(g, o->max_iter + 2))) return rc;
+    if ((rc = init_state(g, g->st, o->rtol, s))) return rc;
+    PcgArgs a = pcg_args(g, o->max_iter);
+    if (o->use_x0 && g->have_x0) CK(cudaMemcpyAsync(g->x, g->x0, sizeof(double) * g->N, cudaMemcpyDeviceToDevice, s));
+    launch_pcg_init(a, g->G, s, o->use_x0 && g->have_x0);
+    CK(cudaGetLastError());
+    int k = 0, restarts = 0;
+    const int chunk = std::max(1, o->check_every);
+    if ((rc = sync_state(g, g->st, s))) return rc;
+    while (!g->st_host->done) {
+        for (int c = 0; c < chunk && k < o->max_iter; ++c, ++k) launch_pcg_iter(a, g->G, s, k);
+        CK(cudaGetLastError());
+        if ((rc = sync_state(g, g->st, s))) return rc;
+        SolveState* h = g->st_host;
+        if (h->status) break;
+        if (h->converged) {
+            launch_true_residual(a, g->G, s);
+            if ((rc = sync_state(g, g->st, s))) return rc;
+            if (g->st_host->rel <= o->rtol || restarts >= 3 || k >= o->max_iter) break;
+            ++restarts;
+            k = g->st_host->iters;
+            launch_pcg_restart(a, g->G, s, k);
+            if ((rc = sync_state(g, g->st, s))) return rc;
+            continue;
+        }
+        if (k >= o->max_iter) break;
+    }
+    SolveState h = *g->st_host;
+    const int iters = h.iters;
+    g->history.assign(iters + 1, 0.0);
+    CK(cudaMemcpy(g->history.data(), g->hist_dev, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost));
+    // final true residual
+    launch_true_residual(a, g->G, s);
+    if ((rc = sync_state(g, g->st, s))) return rc;
+    res->iters = iters;
+    res->rel_residual = g->st_host->rel;
+    if (h.status) return h.status;
+    return g->st_host->rel <= o->rtol ? LM_OK : LM_ERR_NO_CONVERGENCE;
+}
+
+// ---- float64 flexible CG with the float32 V-cycle ---------------------------
+int solve_mg_pcg(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
+    cudaStream_t s = S(o->cuda_stream);
+    int rc;
+    if ((rc = build_mg(g, s))) return rc;
+    if ((rc = init_state(g, g->st, o->rtol, s))) return rc;
+    PcgArgs a = pcg_args(g, o->max_iter);
+    const bool x0 = o->use_x0 && g->have_x0;
+    if (x0) CK(cudaMemcpyAsync(g->x, g->x0, sizeof(double) * g->N, cudaMemcpyDeviceToDevice, s));
+    // r = f - A x (or f), ||f||, ||r||
+    launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, !x0, g->st, 1, nullptr);
+    launch_true_residual(a, g->G, s);     // float64 r
+    if ((rc = sync_state(g, g->st, s))) return rc;
+    g->history.assign(1, g->st_host->rel);
+    if (!(g->st_host->fnorm > 0.0)) {
+        res->rel_residual = 0.0;
+        return LM_OK;
+    }
+    int k = 0;
+    const int nu1 = std::max(0, o->nu1), nu2 = std::max(0, o->nu2);
+    while (g->st_host->rel > o->rtol && k < o->max_iter) {
+        vcycle(g, 0, g->z32, g->r32, nu1, nu2, s);
+        res->vcycles++;
+        launch_fcg64_iter_a(g->N, g->G, s, g->z32, g->q, g->part, k == 0, g->p, g->st);
+        launch_fcg64_iter_b(g->geo, g->G, s, op64(g), g->x, g->r, g->r32, g->p, g->q, g->part, g->st);
+        CK(cudaGetLastError());
+        ++k;
+        if ((rc = sync_state(g, g->st, s))) return rc;
+        g->history.push_back(g->st_host->rel);
+        if (g->st_host->status) break;
+    }
+    launch_true_residual(a, g->G, s);
+    if ((rc = sync_state(g, g->st, s))) return rc;
+    res->iters = k;
+    res->rel_residual = g->st_host->rel;
+    if (g->st_host->status) return g->st_host->status;
+    return g->st_host->rel <= o->rtol ? LM_OK : LM_ERR_NO_CONVERGENCE;
+}
+
+// Inner float32 flexible CG on A32 e = r (r overwritten), V-cycle preconditioner.
+int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, int* vcycles) {
+    int rc;
+    MgLevel& M = g->mg[0];
+    CK(cudaMemsetAsync(g->e32, 0, sizeof(float) * g->N, s));
+    if ((rc = init_state(g, g->st_in, o->inner_rtol, s))) return rc;
+    // the inner problem's reference norm: ||r|| of its right-hand side
+    launch_dot32(g->N, g->G, s, g->r32, g->r32, g->part, 4);
+    launch_set_fnorm(g->part, 4, g->G, s, g->st_in);
+    const int nu1 = std::max(0, o->nu1), nu2 = std::max(0, o->nu2);
+    for (int it = 0; it < o->inner_max_iter; ++it) {
+        vcycle(g, 0, g->z32, g->r32, nu1, nu2, s);
+        ++*vcycles;
+        if (it > 0) launch_dot32(g->N, g->G, s, g->z32, g->q32, g->part, 5);
+        launch_fcg_beta_p(g->N, g->G, s, g->z32, g->p32, g->q32, g->part, it == 0);
+        launch_fcg_apply(M.L, g->G, s, g->p32, g->q32, g->r32, g->part);
+        launch_fcg_update(g->N, g->G, s, g->e32, g->r32, g->p32, g->q32, g->part, g->st_in);
+        launch_reduce_rel(g->part, g->G, s, g->st_in, nullptr);
+        CK(cudaGetLastError());
+        ++*iters;
+        if ((rc = sync_state(g, g->st_in, s))) return rc;
+        if (g->st_host->status) return LM_OK;     // breakdown: keep e so far
+        if (g->st_host->rel <= o->inner_rtol) break;
+    }
+    return LM_OK;
+}
+
+// ---- mixed precision: float64 iterative refinement around float32 FCG+MG ----
+int solve_mixed_ir(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
+    cudaStream_t s = S(o->cuda_stream);
+    int rc;
+    if ((rc = build_mg(g, s))) return rc;
+    if ((rc = init_state(g, g->st, o->rtol, s))) return rc;
+    const bool x0 = o->use_x0 && g->have_x0;
+    if (x0) CK(cudaMemcpyAsync(g->x, g->x0, sizeof(double) * g->N, cudaMemcpyDeviceToDevice, s));
+    launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, !x0, g->st, 1, nullptr);
+    CK(cudaGetLastError());
+    if ((rc = sync_state(g, g->st, s))) return rc;
+    g->history.assign(1, g->st_host->rel);
+    if (!(g->st_host->fnorm > 0.0)) {
+        res->rel_residual = 0.0;
+        return LM_OK;
+    }
+    double rel = g->st_host->rel;
+    int outer = 0, iters = 0, vc = 0;
+    int status = LM_OK;
+    while (rel > o->rtol && outer < o->max_outer && iters < o->max_iter) {
+        if ((rc = inner_fcg(g, o, s, &iters, &vc))) return rc;
+        if (g->st_host->status) status = g->st_host->status;
+        launch_ir_correct(g->N, g->G, s, g->x, g->e32);
+        launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, 0, g->st, 0, nullptr);
+        CK(cudaGetLastError());
+        if ((rc = sync_state(g, g->st, s))) return rc;
+        const double nrel = g->st_host->rel;
+        g->history.push_back(nrel);
+        ++outer;
+        if (!(nrel < rel) && status) break;       // inner breakdown and no progress
+        rel = nrel;
+        status = LM_OK;
+    }
+    res->iters = iters;
+    res->outer_iters = outer;
+    res->vcycles += vc;
+    res->rel_residual = rel;
+    if (status) return status;
+    return rel <= o->rtol ? LM_OK : LM_ERR_NO_CONVERGENCE;
+}
+
+int copy_in(lm_grid* g, double* dst, const double* src, int on_device, cudaStream_t s) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * g->N,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (!on_device) CK(cudaStreamSynchronize(s));   // the caller may reuse its host buffer
+    return LM_OK;
+}
+
+int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double* cs2, double dt, int raw,
+             int on_device, cudaStream_t s) {
+    if (!g || !a_in || !rho_new || (!raw && !cs2)) return LM_ERR_INVALID_ARG;
+    if (!raw && !(dt > 0.0 && std::isfinite(dt))) return LM_ERR_NOT_POSITIVE;
+    const double* A = a_in;
+    const double* R = rho_new;
+    const double* C = cs2;
+    int rc;
+    if (!on_device) {
+        if (!g->stage && (rc = dalloc(&g->stage, (size_t)3 * g->N))) return rc;
+        if ((rc = copy_in(g, g->stage, a_in, 0, s))) return rc;
+        if ((rc = copy_in(g, g->stage + g->N, rho_new, 0, s))) return rc;
+        if (!raw && (rc = copy_in(g, g->stage + 2 * (size_t)g->N, cs2, 0, s))) return rc;
+        A = g->stage;
+        R = g->stage + g->N;
+        C = raw ? nullptr : g->stage + 2 * (size_t)g->N;
+    }
+    CK(cudaMemsetAsync(g->bad, 0, sizeof(int), s));
+    Op64Out dst{g->ct, g->gx, g->gy, g->gz, g->dinv, g->ct32, g->rho32};
+    launch_assemble(g->geo, g->G, s, A, R, C, dt, raw, g->h, dst, g->bad);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(g->bad_host, g->bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    g->mg_built = false;
+    if (*g->bad_host) {
+        g->have_coefs = false;
+        return LM_ERR_NOT_POSITIVE;
+    }
+    g->have_coefs = true;
+    return LM_OK;
+}
+
+}  // namespace
+
+// ============================ C ABI =========================================
+
+extern "C" {
+
+void lm_default_opts(lm_solve_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->mode = LM_MIXED_MG_IR;
+    o->rtol = 1e-8;
+    o->max_iter = 10000;
+    o->use_x0 = 0;
+    o->max_outer = 12;
+    o->nu1 = 1;
+    o->nu2 = 1;
+    o->inner_rtol = 1e-3;
+    o->inner_max_iter = 30;
+    o->check_every = 8;
+    o->cuda_stream = nullptr;
+}
+
+const char* lm_status_string(int s) {
+    switch (s) {
+        case LM_OK: return "ok";
+        case LM_ERR_INVALID_ARG: return "invalid argument";
+        case LM_ERR_NOT_POSITIVE: return "coefficients not strictly positive and finite (rho, c_s^2, dt, c~)";
+        case LM_ERR_NO_CONVERGENCE: return "no convergence within the iteration limit";
+        case LM_ERR_BREAKDOWN: return "Krylov breakdown (p^T A p <= 0 or non-finite)";
+        case LM_ERR_TIMEOUT: return "bounded device wait expired";
+        case LM_ERR_CUDA: return "CUDA runtime error";
+        case LM_ERR_NETWORK: return "network weights missing or malformed";
+        case LM_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case LM_ERR_STATE: return "coefficients or right-hand side not set";
+        default: return "unknown status";
+    }
+}
+
+int lm_grid_create(int ndim, const int64_t n[3], const double h[3], const int bc[3], lm_grid** out) {
+    if (!out || !n || !h || !bc || (ndim != 2 && ndim != 3)) return LM_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 1 || !(h[a] > 0.0) || !std::isfinite(h[a])) return LM_ERR_INVALID_ARG;
+        if (bc[a] != LM_BC_PERIODIC && bc[a] != LM_BC_NEUMANN) return LM_ERR_INVALID_ARG;
+    }
+    if (ndim == 2 && n[1] != 1) return LM_ERR_INVALID_ARG;
+    const long long N = (long long)n[0] * n[1] * n[2];
+    if (N >= (1LL << 31)) return LM_ERR_INVALID_ARG;
+    lm_grid* g = new (std::nothrow) lm_grid();
+    if (!g) return LM_ERR_OUT_OF_MEMORY;
+    g->ndim = ndim;
+    for (int a = 0; a < 3; ++a) {
+        g->n[a] = (int)n[a];
+        g->h[a] = h[a];
+        g->bc[a] = bc[a];
+    }
+    g->N = (int)N;
+    int rc = LM_OK;
+    auto fail = [&](int code) {
+        lm_grid_destroy(g);
+        return code;
+    };
+    if (cudaGetDevice(&g->device) != cudaSuccess) return fail(LM_ERR_CUDA);
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device);
+    const long long want = (N + NT - 1) / NT;
+    g->G = (int)std::max(1LL, std::min<long long>(want, std::min<long long>(MAX_PARTIALS, (long long)nsm * 8)));
+    g->geo = make_lev(g->n, g->bc, g->h, nullptr, nullptr).g;
+    double** d64[] = {&g->ct, &g->gx, &g->gy, &g->gz, &g->dinv, &g->f, &g->x, &g->r, &g->p, &g->q};
+    for (double** p : d64)
+        if ((rc = dalloc(p, N))) return fail(rc);
+    float** d32[] = {&g->ct32, &g->rho32, &g->r32, &g->e32, &g->z32, &g->p32, &g->q32};
+    for (float** p : d32)
+        if ((rc = dalloc(p, N))) return fail(rc);
+    if ((rc = dalloc(&g->part, (size_t)NSLOT * MAX_PARTIALS))) return fail(rc);
+    if ((rc = dalloc(&g->dscal, 8))) return fail(rc);
+    if ((rc = dalloc(&g->st, 1))) return fail(rc);
+    if ((rc = dalloc(&g->st_in, 1))) return fail(rc);
+    if ((rc = dalloc(&g->bad, 1))) return fail(rc);
+    if (cudaMallocHost((void**)&g->st_host, sizeof(SolveState)) != cudaSuccess) return fail(LM_ERR_OUT_OF_MEMORY);
+    if (cudaMallocHost((void**)&g->bad_host, sizeof(int)) != cudaSuccess) return fail(LM_ERR_OUT_OF_MEMORY);
+    if (cudaMallocHost((void**)&g->dscal_host, 8 * sizeof(double)) != cudaSuccess) return fail(LM_ERR_OUT_OF_MEMORY);
+    if (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess) return fail(LM_ERR_CUDA);
+    if (cudaMemset(g->part, 0, sizeof(double) * NSLOT * MAX_PARTIALS) != cudaSuccess) return fail(LM_ERR_CUDA);
+    *out = g;
+    return LM_OK;
+}
+
+void lm_grid_destroy(lm_grid* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    free_mg(g);
+    void* bufs[] = {g->ct, g->gx, g->gy, g->gz, g->dinv, g->f, g->x, g->x0, g->r, g->p, g->q,
+                    g->ct32, g->rho32, g->r32, g->e32, g->z32, g->p32, g->q32, g->stage, g->part,
+                    g->dscal, g->st, g->st_in, g->hist_dev, g->bad};
+    for (void* b : bufs) cudaFree(b);
+    cudaFreeHost(g->st_host);
+    cudaFreeHost(g->bad_host);
+    cudaFreeHost(g->dscal_host);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    delete g;
+}
+
+int64_t lm_grid_size(const lm_grid* g) { return g ? (int64_t)g->N : 0; }
+
+int64_t lm_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+int lm_set_coefficients(lm_grid* g, const double* rho_old, const double* rho_new, const double* cs2, double dt,
+                        int on_device, void* stream) {
+    return assemble(g, rho_old, rho_new, cs2, dt, 0, on_device, S(stream));
+}
+
+int lm_set_coefficients_raw(lm_grid* g, const double* ctilde, const double* rho_face_src, int on_device,
+                            void* stream) {
+    return assemble(g, ctilde, rho_face_src, nullptr, 1.0, 1, on_device, S(stream));
+}
+
+int lm_set_rhs(lm_grid* g, const double* f, int on_device, void* stream) {
+    if (!g || !f) return LM_ERR_INVALID_ARG;
+    int rc = copy_in(g, g->f, f, on_device, S(stream));
+    if (rc) return rc;
+    g->have_rhs = true;
+    return LM_OK;
+}
+
+int lm_set_initial_guess(lm_grid* g, const double* x0, int on_device, void* stream) {
+    if (!g || !x0) return LM_ERR_INVALID_ARG;
+    int rc;
+    if (!g->x0 && (rc = dalloc(&g->x0, g->N))) return rc;
+    if ((rc = copy_in(g, g->x0, x0, on_device, S(stream)))) return rc;
+    g->have_x0 = true;
+    return LM_OK;
+}
+
+int lm_load_network(lm_grid* g, const char* path) {
+    (void)g;
+    (void)path;
+    return LM_ERR_NETWORK;
+}
+
+int lm_solve(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
+    if (!g || !o) return LM_ERR_INVALID_ARG;
+    lm_solve_result dummy;
+    if (!res) res = &dummy;
+    std::memset(res, 0, sizeof *res);
+    if (!g->have_coefs || !g->have_rhs) return res->status = LM_ERR_STATE;
+    if (!(o->rtol > 0.0) || o->max_iter < 1) return res->status = LM_ERR_INVALID_ARG;
+    const bool mg = o->mode != LM_FP64_JACOBI_PCG;
+    if (mg && !mg_supported(g)) return res->status = LM_ERR_INVALID_ARG;
+    if (o->mode < 0 || o->mode > LM_MIXED_LEARNED_FCG_IR) return res->status = LM_ERR_INVALID_ARG;
+    cudaStream_t s = S(o->cuda_stream);
+    CK(cudaEventRecord(g->ev0, s));
+    int rc;
+    switch (o->mode) {
+        case LM_FP64_JACOBI_PCG: rc = solve_jacobi_pcg(g, o, res); break;
+        case LM_FP64_MG_PCG: rc = solve_mg_pcg(g, o, res); break;
+        default: rc = solve_mixed_ir(g, o, res); break;
+    }
+    cudaEventRecord(g->ev1, s);
+    cudaEventSynchronize(g->ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+    res->seconds = ms * 1e-3;
+    res->status = rc;
+    return rc;
+}
+
+int lm_get_solution(lm_grid* g, double* out, int on_device, void* stream) {
+    if (!g || !out) return LM_ERR_INVALID_ARG;
+    cudaStream_t s = S(stream);
+    CK(cudaMemcpyAsync(out, g->x, sizeof(double) * g->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       s));
+    if (!on_device) CK(cudaStreamSynchronize(s));
+    return LM_OK;
+}
+
+int lm_get_residual_history(lm_grid* g, double* out, int cap, int* n_written) {
+    if (!g || (!out && cap > 0)) return LM_ERR_INVALID_ARG;
+    const int n = std::min<int>(cap, (int)g->history.size());
+    if (n > 0) std::memcpy(out, g->history.data(), sizeof(double) * n);
+    if (n_written) *n_written = (int)g->history.size();
+    return LM_OK;
+}
+
+int lm_get_coefficients(lm_grid* g, double* ctilde, double* gx, double* gy, double* gz, void* stream) {
+    if (!g) return LM_ERR_INVALID_ARG;
+    if (!g->have_coefs) return LM_ERR_STATE;
+    cudaStream_t s = S(stream);
+    const size_t B = sizeof(double) * g->N;
+    if (ctilde) CK(cudaMemcpyAsync(ctilde, g->ct, B, cudaMemcpyDeviceToDevice, s));
+    if (gx) CK(cudaMemcpyAsync(gx, g->gx, B, cudaMemcpyDeviceToDevice, s));
+    if (gy) CK(cudaMemcpyAsync(gy, g->gy, B, cudaMemcpyDeviceToDevice, s));
+    if (gz) CK(cudaMemcpyAsync(gz, g->gz, B, cudaMemcpyDeviceToDevice, s));
+    return LM_OK;
+}
+
+int lm_apply(lm_grid* g, int prec, const void* x, void* y, double* dot_out, void* stream) {
+    if (!g || !x || !y || (prec != LM_PREC_FP64 && prec != LM_PREC_FP32)) return LM_ERR_INVALID_ARG;
+    if (!g->have_coefs) return LM_ERR_STATE;
+    cudaStream_t s = S(stream);
+    double* part = dot_out ? g->part : nullptr;
+    if (prec == LM_PREC_FP64) {
+        launch_apply64(g->geo, g->G, s, op64(g), (const double*)x, (double*)y, part);
+    } else {
+        Lev32 L = make_lev(g->n, g->bc, g->h, g->ct32, g->rho32);
+        launch_apply32(L, g->G, s, (const float*)x, (float*)y, part);
+    }
+    CK(cudaGetLastError());
+    if (dot_out) {
+        launch_reduce_slot(g->part, 0, g->G, s, g->dscal);
+        CK(cudaMemcpyAsync(g->dscal_host, g->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *dot_out = g->dscal_host[0];
+    }
+    return LM_OK;
+}
+
+int lm_mg_vcycle(lm_grid* g, const float* r, float* z, int nu1, int nu2, void* stream) {
+    if (!g || !r || !z || nu1 < 0 || nu2 < 0) return LM_ERR_INVALID_ARG;
+    if (!g->have_coefs) return LM_ERR_STATE;
+    if (!mg_supported(g)) return LM_ERR_INVALID_ARG;
+    cudaStream_t s = S(stream);
+    int rc = build_mg(g, s);
+    if (rc) return rc;
+    vcycle(g, 0, z, r, nu1, nu2, s);
+    CK(cudaGetLastError());
+    return LM_OK;
+}
+
+int lm_mg_level_shape(lm_grid* g, int level, int64_t n_out[3], int* num_levels) {
+    if (!g || !n_out) return LM_ERR_INVALID_ARG;
+    if (!g->have_coefs) return LM_ERR_STATE;
+    if (!mg_supported(g)) return LM_ERR_INVALID_ARG;
+    int rc = build_mg(g, 0);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    if (num_levels) *num_levels = (int)g->mg.size();
+    if (level < 0 || level >= (int)g->mg.size()) return LM_ERR_INVALID_ARG;
+    n_out[0] = g->mg[level].L.g.nx;
+    n_out[1] = g->mg[level].L.g.ny;
+    n_out[2] = g->mg[level].L.g.nz;
+    return LM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// Host-visible kernel interfaces of the solver library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lm_common.cuh"
+
+namespace lm {
+
+// Number of kernels this library has launched (all grids, all streams).
+void count_launches(long long n);
+
+// Float64 operator: c~, minus-face conductances per axis, inverse diagonal.
+struct Op64 {
+    const double* ct;
+    const double* gx;
+    const double* gy;
+    const double* gz;
+    const double* dinv;
+};
+struct Op64Out {
+    double* ct;
+    double* gx;
+    double* gy;
+    double* gz;
+    double* dinv;
+    float* ct32;
+    float* rho32;
+};
+
+struct PcgArgs {
+    Geo g;
+    Op64 op;
+    const double* f;
+    double* x;
+    double* r;
+    double* p;
+    double* q;
+    double* part;     // NSLOT * MAX_PARTIALS
+    SolveState* st;
+    double* hist;     // max_iter + 1
+    int max_iter;
+};
+
+// One float32 multigrid level (device view).  Faces are formed on the fly
+// from rho: g = 2 (1/h^2) / (rho_L + rho_R).
+struct Lev32 {
+    Geo g;
+    float c2x, c2y, c2z;     // 2/h^2 per axis
+    const float* ct;
+    const float* rho;
+};
+
+// fp64
+void launch_assemble(const Geo& g, int G, cudaStream_t s, const double* a_in, const double* rho_new,
+                     const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, int* bad);
+void launch_apply64(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* x, double* y,
+                    double* part);
+void launch_pcg_init(const PcgArgs& a, int G, cudaStream_t s, int use_x0);
+void launch_pcg_restart(const PcgArgs& a, int G, cudaStream_t s, int k);
+void launch_pcg_iter(const PcgArgs& a, int G, cudaStream_t s, int k);
+void launch_true_residual(const PcgArgs& a, int G, cudaStream_t s);
+void launch_ir_residual(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* f, double* x,
+                        float* r32, double* part, int zero_x, SolveState* st, int set_fnorm, double* hist_entry);
+void launch_ir_correct(int N, int G, cudaStream_t s, double* x, const float* e);
+void launch_reduce_rel(double* part, int G, cudaStream_t s, SolveState* st, double* hist_entry);
+void launch_reduce_slot(const double* part, int slot, int G, cudaStream_t s, double* out);
+void launch_fcg64_iter_a(int N, int G, cudaStream_t s, const float* z, const double* q, double* part, int first,
+                         double* p, const SolveState* st);
+void launch_fcg64_iter_b(const Geo& g, int G, cudaStream_t s, const Op64& op, double* x, double* r, float* r32,
+                         const double* p, double* q, double* part, SolveState* st);
+void launch_to32(int N, int G, cudaStream_t s, const double* r, float* r32);
+void launch_set_fnorm(const double* part, int slot, int G, cudaStream_t s, SolveState* st);
+
+// fp32 operator and flexible CG
+void launch_apply32(const Lev32& L, int G, cudaStream_t s, const float* x, float* y, double* part);
+void launch_fcg_beta_p(int N, int G, cudaStream_t s, const float* z, float* p, const float* q_old,
+                       double* part, int first);
+void launch_fcg_apply(const Lev32& L, int G, cudaStream_t s, const float* p, float* q, const float* r,
+                      double* part);
+void launch_fcg_update(int N, int G, cudaStream_t s, float* e, float* r, const float* p, const float* q,
+                       double* part, SolveState* st);
+void launch_dot32(int N, int G, cudaStream_t s, const float* a, const float* b, double* part, int slot);
+
+// multigrid
+void launch_coarsen(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s, float* ct_c,
+                    float* rho_c);
+void launch_smooth(const Lev32& L, cudaStream_t s, float* x, const float* f, int colour, int zero_guess);
+void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s,
+                           const float* x, const float* f, float* fc);
+void launch_prolong_add(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s, float* x,
+                        const float* xc);
+void launch_coarse_inverse(const Lev32& L, cudaStream_t s, float* ainv);
+void launch_coarse_solve(int n, cudaStream_t s, const float* ainv, const float* f, float* x);
+
+}  // namespace lm

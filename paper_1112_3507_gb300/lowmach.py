@@ -1,0 +1,287 @@
+"""Thin Python binding of the C ABI in include/lowmach.h (ctypes).
+
+Argument marshalling only: every computation runs in liblowmach.so's CUDA
+kernels.  Fields are passed either as numpy float64 arrays (host memory,
+on_device = 0) or as contiguous CUDA torch tensors (device memory,
+on_device = 1); torch supplies device memory and the current stream.
+
+The library must have been built (paper_1112_3507_gb300.build); loading
+fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+# status codes and enums (mirror include/lowmach.h)
+LM_OK = 0
+LM_ERR_INVALID_ARG = -1
+LM_ERR_NOT_POSITIVE = -2
+LM_ERR_NO_CONVERGENCE = -3
+LM_ERR_BREAKDOWN = -4
+LM_ERR_TIMEOUT = -5
+LM_ERR_CUDA = -6
+LM_ERR_NETWORK = -7
+LM_ERR_OUT_OF_MEMORY = -8
+LM_ERR_STATE = -9
+BC_PERIODIC, BC_NEUMANN = 0, 1
+FP64_JACOBI_PCG, FP64_MG_PCG, MIXED_MG_IR, MIXED_LEARNED_FCG_IR = 0, 1, 2, 3
+PREC_FP64, PREC_FP32 = 0, 1
+MODES = {"jacobi": FP64_JACOBI_PCG, "fp64-mg": FP64_MG_PCG, "mixed": MIXED_MG_IR,
+         "learned": MIXED_LEARNED_FCG_IR}
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("use_x0", ctypes.c_int), ("max_outer", ctypes.c_int), ("nu1", ctypes.c_int),
+                ("nu2", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("inner_max_iter", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+
+
+class SolveResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("vcycles", ctypes.c_int), ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class LowMachError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64_3 = ctypes.c_int64 * 3
+_D3 = ctypes.c_double * 3
+_I3 = ctypes.c_int * 3
+
+_SIGNATURES = {
+    "lm_default_opts": (None, [ctypes.POINTER(SolveOpts)]),
+    "lm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lm_kernel_launches": (ctypes.c_int64, []),
+    "lm_grid_create": (ctypes.c_int, [ctypes.c_int, _I64_3, _D3, _I3, ctypes.POINTER(_P)]),
+    "lm_grid_destroy": (None, [_P]),
+    "lm_grid_size": (ctypes.c_int64, [_P]),
+    "lm_set_coefficients": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int, _P]),
+    "lm_set_coefficients_raw": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "lm_set_rhs": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "lm_set_initial_guess": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "lm_load_network": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "lm_solve": (ctypes.c_int, [_P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveResult)]),
+    "lm_get_solution": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "lm_get_residual_history": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int)]),
+    "lm_get_coefficients": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "lm_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "lm_mg_vcycle": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
+    "lm_mg_level_shape": (ctypes.c_int, [_P, ctypes.c_int, _I64_3, ctypes.POINTER(ctypes.c_int)]),
+}
+
+
+def declared_symbols():
+    return list(_SIGNATURES)
+
+
+def lib():
+    """Load liblowmach.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} not found: build it with `python -m paper_1112_3507_gb300.build` "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def kernel_launches() -> int:
+    return int(lib().lm_kernel_launches())
+
+
+def status_string(code: int) -> str:
+    try:
+        return lib().lm_status_string(code).decode()
+    except RuntimeError:
+        return f"status {code}"
+
+
+def _check(code: int, where: str, ok=(LM_OK,)):
+    if code not in ok:
+        raise LowMachError(code, where)
+    return code
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _field(a, N: int, dtype=np.float64):
+    """(pointer, on_device, keepalive) for a host numpy array or a CUDA tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_cuda:
+                a = a.detach().numpy()
+            else:
+                want = torch.float64 if dtype == np.float64 else torch.float32
+                if a.dtype != want or not a.is_contiguous() or a.numel() != N:
+                    raise ValueError(f"device field must be a contiguous {want} tensor of {N} values")
+                return ctypes.c_void_p(a.data_ptr()), 1, a
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(np.asarray(a, dtype=dtype)).ravel()
+    if arr.size != N:
+        raise ValueError(f"field has {arr.size} values, grid has {N}")
+    return ctypes.c_void_p(arr.ctypes.data), 0, arr
+
+
+class Grid:
+    """A solver grid: n = (nx, ny, nz) cells (ny = 1 for 2D), spacings h,
+    one boundary condition per axis (BC_PERIODIC / BC_NEUMANN)."""
+
+    def __init__(self, n, h, bc, ndim: int | None = None):
+        n = tuple(int(v) for v in n)
+        if ndim is None:
+            ndim = 2 if n[1] == 1 else 3
+        self.n, self.h, self.bc, self.ndim = n, tuple(float(v) for v in h), tuple(int(b) for b in bc), ndim
+        self.N = n[0] * n[1] * n[2]
+        ptr = _P()
+        _check(lib().lm_grid_create(ndim, _I64_3(*n), _D3(*self.h), _I3(*self.bc), ctypes.byref(ptr)),
+               "lm_grid_create")
+        self._g = ptr
+
+    @classmethod
+    def for_problem(cls, p):
+        return cls(p.n, p.h, p.bc, p.ndim)
+
+    def close(self):
+        if getattr(self, "_g", None):
+            lib().lm_grid_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- inputs
+    def set_coefficients(self, rho_old, rho_new, cs2, dt, stream=None):
+        a, d1, k1 = _field(rho_old, self.N)
+        b, d2, k2 = _field(rho_new, self.N)
+        c, d3, k3 = _field(cs2, self.N)
+        if not d1 == d2 == d3:
+            raise ValueError("all fields must live on the same side (host or device)")
+        return _check(lib().lm_set_coefficients(self._g, a, b, c, float(dt), d1, _stream_ptr(stream)),
+                      "lm_set_coefficients")
+
+    def set_coefficients_raw(self, ctilde, rho_face_src, stream=None):
+        a, d1, k1 = _field(ctilde, self.N)
+        b, d2, k2 = _field(rho_face_src, self.N)
+        if d1 != d2:
+            raise ValueError("all fields must live on the same side (host or device)")
+        return _check(lib().lm_set_coefficients_raw(self._g, a, b, d1, _stream_ptr(stream)),
+                      "lm_set_coefficients_raw")
+
+    def set_problem(self, p, stream=None):
+        self.set_coefficients(p.rho_old, p.rho_new, p.cs2, p.dt, stream)
+        self.set_rhs(p.f, stream)
+
+    def set_rhs(self, f, stream=None):
+        a, d, k = _field(f, self.N)
+        return _check(lib().lm_set_rhs(self._g, a, d, _stream_ptr(stream)), "lm_set_rhs")
+
+    def set_initial_guess(self, x0, stream=None):
+        a, d, k = _field(x0, self.N)
+        return _check(lib().lm_set_initial_guess(self._g, a, d, _stream_ptr(stream)), "lm_set_initial_guess")
+
+    # ---- solve
+    def solve(self, mode="mixed", rtol=1e-8, stream=None, allow=(LM_OK,), **kw) -> dict:
+        o = SolveOpts()
+        lib().lm_default_opts(ctypes.byref(o))
+        o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        o.rtol = float(rtol)
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown solve option {k}")
+            setattr(o, k, v)
+        o.cuda_stream = _stream_ptr(stream)
+        r = SolveResult()
+        code = lib().lm_solve(self._g, ctypes.byref(o), ctypes.byref(r))
+        _check(code, "lm_solve", ok=allow)
+        return dict(status=r.status, iters=r.iters, outer_iters=r.outer_iters, vcycles=r.vcycles,
+                    rel_residual=r.rel_residual, seconds=r.seconds)
+
+    def solution(self, out=None, stream=None):
+        if out is None:
+            out = np.empty(self.N, dtype=np.float64)
+        a, d, k = _field(out, self.N)
+        _check(lib().lm_get_solution(self._g, a, d, _stream_ptr(stream)), "lm_get_solution")
+        return out
+
+    def residual_history(self):
+        n = ctypes.c_int(0)
+        lib().lm_get_residual_history(self._g, None, 0, ctypes.byref(n))
+        buf = (ctypes.c_double * max(n.value, 1))()
+        _check(lib().lm_get_residual_history(self._g, buf, n.value, ctypes.byref(n)), "lm_get_residual_history")
+        return np.array(buf[: n.value])
+
+    # ---- row-level entry points (device tensors)
+    def coefficients(self, stream=None):
+        import torch
+        outs = [torch.empty(self.N, dtype=torch.float64, device="cuda") for _ in range(4)]
+        _check(lib().lm_get_coefficients(self._g, *[ctypes.c_void_p(t.data_ptr()) for t in outs],
+                                         _stream_ptr(stream)), "lm_get_coefficients")
+        return outs
+
+    def apply(self, x, y, prec=PREC_FP64, with_dot=False, stream=None):
+        dt = np.float64 if prec == PREC_FP64 else np.float32
+        xp, dx, kx = _field(x, self.N, dt)
+        yp, dy, ky = _field(y, self.N, dt)
+        if not (dx and dy):
+            raise ValueError("lm_apply takes device tensors")
+        dot = ctypes.c_double(0.0)
+        _check(lib().lm_apply(self._g, prec, xp, yp, ctypes.byref(dot) if with_dot else None,
+                              _stream_ptr(stream)), "lm_apply")
+        return dot.value if with_dot else None
+
+    def mg_vcycle(self, r, z, nu1=1, nu2=1, stream=None):
+        rp, dr, kr = _field(r, self.N, np.float32)
+        zp, dz, kz = _field(z, self.N, np.float32)
+        if not (dr and dz):
+            raise ValueError("lm_mg_vcycle takes device tensors")
+        _check(lib().lm_mg_vcycle(self._g, rp, zp, nu1, nu2, _stream_ptr(stream)), "lm_mg_vcycle")
+
+    def mg_levels(self):
+        shapes = []
+        nl = ctypes.c_int(0)
+        out = _I64_3()
+        _check(lib().lm_mg_level_shape(self._g, 0, out, ctypes.byref(nl)), "lm_mg_level_shape")
+        for l in range(nl.value):
+            _check(lib().lm_mg_level_shape(self._g, l, out, ctypes.byref(nl)), "lm_mg_level_shape")
+            shapes.append(tuple(out))
+        return shapes

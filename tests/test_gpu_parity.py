@@ -1,0 +1,247 @@
+"""GPU path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Tolerances: float64 kernels 1e-14 (operator) / 1e-10 (solution, north-star
+FP64 bar); float32 kernels 1e-5 relative (float32 rounding of the operator
+and of one V-cycle); mixed-precision solutions 1e-8 after refinement."""
+import numpy as np
+import pytest
+
+from oracle import multigrid as OM
+from oracle import poisson as P
+from paper_1112_3507_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1112_3507_gb300 import build as B
+    import os
+    if not os.path.exists(B.LIB) or any(os.path.getmtime(s) > os.path.getmtime(B.LIB) for s in B.sources()):
+        B.build()
+
+
+def lm():
+    from paper_1112_3507_gb300 import lowmach
+    return lowmach
+
+
+NEU, PER = I.BC_NEUMANN, I.BC_PERIODIC
+
+PROBLEMS = {
+    "plain2d-64": lambda: I.config_plain_2d(64, seed=1),
+    "conv3d-16": lambda: I.config_convection_3d(16, seed=2),
+    "ragged2d-37x50-walls": lambda: I.make_problem(37, 50, ma=0.05, contrast=8.0, noise=0.01, seed=3,
+                                                   bc=(NEU, PER, NEU)),
+    "ragged3d-12x6x10": lambda: I.make_problem(12, 10, 6, ma=0.02, contrast=12.0, noise=0.01, seed=4),
+    "column-1x1x40": lambda: I.make_problem(1, 40, ma=0.1, contrast=5.0, seed=5),
+}
+
+
+def _grid(p):
+    g = lm().Grid.for_problem(p)
+    g.set_problem(p)
+    return g
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a).ravel(), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_assembly_bit_exact(name):
+    """Row a1: c~ (Eq. cpoiss) and the face conductances from kappa = 1/rho
+    (Eq. kappapoiss) agree bit for bit with the oracle."""
+    p = PROBLEMS[name]()
+    op = P.operator_from_problem(p)
+    with _grid(p) as g:
+        ct, gx, gy, gz = [t.cpu().numpy() for t in g.coefficients()]
+        torch.cuda.synchronize()
+    np.testing.assert_array_equal(ct, op.ct.ravel())
+    for a, got in enumerate((gx, gy, gz)):
+        np.testing.assert_array_equal(got, op.g_minus[a].ravel())
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_apply_fp64_and_dot(name):
+    """Row a2 (+ fused dot of a3): y = A x in float64."""
+    p = PROBLEMS[name]()
+    op = P.operator_from_problem(p)
+    x = np.random.default_rng(7).standard_normal(p.size)
+    y_ref = op.apply(x).ravel()
+    with _grid(p) as g:
+        xd, yd = _dev(x), torch.empty(p.size, dtype=torch.float64, device="cuda")
+        dot = g.apply(xd, yd, prec=lm().PREC_FP64, with_dot=True)
+        y = yd.cpu().numpy()
+    assert np.linalg.norm(y - y_ref) <= 1e-14 * np.linalg.norm(y_ref)
+    assert dot == pytest.approx(float(np.vdot(x, y_ref)), rel=1e-12)
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_apply_fp32(name):
+    """Row a2 in float32 (faces from float32 rho), vs the oracle operator on
+    the float32-rounded coefficients; dot accumulated to float64 accuracy."""
+    p = PROBLEMS[name]()
+    op = P.operator_from_problem(p)
+    ct32 = op.ct.astype(np.float32).astype(np.float64)
+    rho32 = p.rho_new.astype(np.float32).astype(np.float64)
+    op32 = P.Operator(ct32, rho32, p.h, p.bc)
+    x = np.random.default_rng(8).standard_normal(p.size).astype(np.float32)
+    y_ref = op32.apply(x.astype(np.float64)).ravel()
+    with _grid(p) as g:
+        xd, yd = _dev(x, torch.float32), torch.empty(p.size, dtype=torch.float32, device="cuda")
+        dot = g.apply(xd, yd, prec=lm().PREC_FP32, with_dot=True)
+        y = yd.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(y - y_ref) <= 1e-5 * np.linalg.norm(y_ref)
+    # the dot of the float32 vectors actually produced, to float64 accuracy
+    assert dot == pytest.approx(float(np.vdot(x.astype(np.float64), y)), rel=1e-9)
+
+
+@pytest.mark.parametrize("name", ["plain2d-64", "conv3d-16", "ragged3d-12x6x10"])
+def test_vcycle_matches_oracle(name):
+    """Row a4: one float32 V-cycle z = M r vs the oracle's float64 V-cycle on
+    the same (float32-rounded) coefficients; same hierarchy."""
+    p = PROBLEMS[name]()
+    op = P.operator_from_problem(p)
+    ct32 = op.ct.astype(np.float32).astype(np.float64)
+    rho32 = p.rho_new.astype(np.float32).astype(np.float64)
+    levels = OM.build_hierarchy(ct32, rho32, p.h, p.bc)
+    r = np.random.default_rng(9).standard_normal(p.size).astype(np.float32)
+    z_ref = OM.vcycle(levels, r.astype(np.float64).reshape(p.shape3)).ravel()
+    with _grid(p) as g:
+        shapes = g.mg_levels()
+        assert [tuple(reversed(L.shape)) for L in levels] == shapes
+        rd, zd = _dev(r, torch.float32), torch.zeros(p.size, dtype=torch.float32, device="cuda")
+        g.mg_vcycle(rd, zd, 1, 1)
+        z = zd.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(z - z_ref) <= 1e-4 * np.linalg.norm(z_ref)
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_jacobi_pcg_parity(name):
+    """Row a3: float64 Jacobi-PCG solution vs the oracle's direct solve."""
+    p = PROBLEMS[name]()
+    op = P.operator_from_problem(p)
+    xs = P.solve_direct(op, p.f).ravel()
+    with _grid(p) as g:
+        r = g.solve(mode="jacobi", rtol=1e-13, max_iter=20000)
+        x = g.solution()
+        hist = g.residual_history()
+    assert r["rel_residual"] <= 1e-13
+    assert hist[0] == pytest.approx(1.0) and len(hist) == r["iters"] + 1
+    assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+    # the oracle's own residual of the GPU solution
+    assert P.rel_residual(op, x, p.f) <= 2e-13
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("mode,bar", [("fp64-mg", 1e-10), ("mixed", 1e-8)])
+def test_multigrid_modes_parity(name, mode, bar):
+    """Rows a4/a5: float64 FCG with the float32 V-cycle, and float64
+    iterative refinement around float32 FCG + V-cycle, vs the direct solve."""
+    p = PROBLEMS[name]()
+    op = P.operator_from_problem(p)
+    xs = P.solve_direct(op, p.f).ravel()
+    with _grid(p) as g:
+        r = g.solve(mode=mode, rtol=1e-13, max_iter=2000, max_outer=30)
+        x = g.solution()
+    assert r["rel_residual"] <= 1e-13
+    assert P.rel_residual(op, x, p.f) <= 2e-13
+    assert np.linalg.norm(x - xs) <= bar * np.linalg.norm(xs)
+
+
+def test_mixed_config1_at_its_tolerance():
+    p = I.config_plain_2d(64, seed=3)
+    op = P.operator_from_problem(p)
+    with _grid(p) as g:
+        r = g.solve(mode="mixed", rtol=p.rtol)
+        x = g.solution()
+    assert r["status"] == 0 and r["rel_residual"] <= p.rtol
+    assert P.rel_residual(op, x, p.f) <= p.rtol * 1.001
+    assert r["outer_iters"] <= 5
+
+
+def test_deterministic_bitwise():
+    p = I.config_convection_3d(16, seed=6)
+    outs = []
+    for _ in range(2):
+        with _grid(p) as g:
+            for mode in ("jacobi", "mixed"):
+                g.solve(mode=mode, rtol=1e-10)
+                outs.append(g.solution())
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
+
+
+def test_warm_start_and_zero_rhs():
+    p = I.config_plain_2d(32, seed=4)
+    op = P.operator_from_problem(p)
+    xs = P.solve_direct(op, p.f).ravel()
+    with _grid(p) as g:
+        g.set_initial_guess(xs)
+        for mode in ("jacobi", "mixed", "fp64-mg"):
+            r = g.solve(mode=mode, rtol=1e-8, use_x0=1)
+            assert r["iters"] == 0 and r["rel_residual"] <= 1e-8
+        g.set_rhs(np.zeros(p.size))
+        for mode in ("jacobi", "mixed"):
+            r = g.solve(mode=mode, rtol=1e-8)
+            assert r["status"] == 0
+            assert not np.any(g.solution())
+
+
+def test_invalid_inputs_rejected():
+    L = lm()
+    p = I.config_plain_2d(16, seed=1)
+    with L.Grid.for_problem(p) as g:
+        with pytest.raises(L.LowMachError) as e:
+            g.solve(mode="jacobi")
+        assert e.value.code == L.LM_ERR_STATE
+        bad = p.rho_old.copy()
+        bad.flat[5] = -1.0
+        with pytest.raises(L.LowMachError) as e:
+            g.set_coefficients(bad, p.rho_new, p.cs2, p.dt)
+        assert e.value.code == L.LM_ERR_NOT_POSITIVE
+        bad.flat[5] = np.nan
+        with pytest.raises(L.LowMachError) as e:
+            g.set_coefficients(p.rho_old, bad, p.cs2, p.dt)
+        assert e.value.code == L.LM_ERR_NOT_POSITIVE
+        with pytest.raises(L.LowMachError) as e:
+            g.set_coefficients(p.rho_old, p.rho_new, p.cs2, 0.0)
+        assert e.value.code == L.LM_ERR_NOT_POSITIVE
+        g.set_problem(p)
+        assert g.solve(mode="jacobi", rtol=1e-10)["status"] == 0
+    # a periodic axis with an odd cell count has no red-black colouring
+    q = I.make_problem(15, 16, ma=0.1, contrast=5.0, seed=2)
+    with _grid(q) as g:
+        assert g.solve(mode="jacobi", rtol=1e-10)["status"] == 0
+        with pytest.raises(L.LowMachError) as e:
+            g.solve(mode="mixed")
+        assert e.value.code == L.LM_ERR_INVALID_ARG
+    with pytest.raises(L.LowMachError):
+        L.Grid((0, 1, 4), (1, 1, 1), (0, 0, 1))
+
+
+@pytest.mark.slow
+def test_full_size_convection_256():
+    """The bench workload (256^3, Ma = 0.01): the mixed solve's residual,
+    recomputed by the oracle in float64, meets rtol; sampled rows match the
+    oracle's row-by-row evaluation; the FP64 baseline agrees with it."""
+    p = I.config_convection_3d(256, seed=1)
+    op = P.operator_from_problem(p)
+    with _grid(p) as g:
+        r = g.solve(mode="mixed", rtol=p.rtol)
+        x = g.solution()
+        assert r["status"] == 0
+        rel = P.rel_residual(op, x, p.f)
+        assert rel <= p.rtol * 1.001
+        # sampled rows of A x, one by one (float64 oracle) vs the GPU's float64 apply
+        xd = _dev(x)
+        yd = torch.empty_like(xd)
+        g.apply(xd, yd, prec=lm().PREC_FP64)
+        y = yd.cpu().numpy()
+    Ax = op.apply(x).ravel()
+    idx = np.random.default_rng(3).integers(0, p.size, 4096)
+    assert np.allclose(y[idx], Ax[idx], rtol=1e-13, atol=1e-13 * np.abs(Ax).max())
