@@ -67,7 +67,7 @@ class ClockSampler:
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.file, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -239,6 +239,12 @@ def run_ours(args):
     launches = lm.kernel_launches() - launches0
     barrier()
     clk = clocks.stop()
+    if args.only_steps:                 # profiling runs: the timed solves and nothing else
+        if rank == 0:
+            print(json.dumps({"only_steps": True, "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                              "gpu_launches": launches, "solve": results[-1]}), flush=True)
+        g.close()
+        return
     elapsed = e0.elapsed_time(e1) * 1e-3
     t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
     if world > 1:
@@ -344,7 +350,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="convection256")
@@ -352,6 +358,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--oracle-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-steps", action="store_true",
+                    help="run warm-up and timed solves only (for profiler launch lists)")
     args = ap.parse_args()
     args.max_iter = args.max_iter
     if args.impl == "reference":
