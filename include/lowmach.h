@@ -209,6 +209,27 @@ int  lm_mg_vcycle(lm_grid* g, const float* r, float* z, int nu1, int nu2, void* 
  * (n_out[3]); LM_ERR_INVALID_ARG past the coarsest level. */
 int  lm_mg_level_shape(lm_grid* g, int level, int64_t n_out[3], int* num_levels);
 
+/* Allocation-free float64 apply: y = A x and *dot_out = x^T A x, like
+ * lm_apply(LM_PREC_FP64) with dot_out, but with no grid object and no device
+ * allocation at all.  The paper has no counterpart: this serves callers that
+ * cannot call cudaMalloc after start-up (a fixed device-memory budget, a
+ * frozen memory pool).  The operator is given by its assembled float64
+ * coefficients, laid out as lm_get_coefficients returns them (c~, and each
+ * cell's minus-face conductance per axis); n, bc describe the grid as in
+ * lm_grid_create (host arrays); ctilde, gx, gy, gz, x, y and dot_out are
+ * device pointers (dot_out: one double), ordered on `stream`.
+ * Scratch: the reduction's partial sums live in a static device array of
+ * 65536 doubles (512 KiB), held by every GPU that loads the library until
+ * the process exits; a call covers at most 65536 * 4096 = 268435456 cells
+ * and larger grids are rejected with LM_ERR_INVALID_ARG (and a message on
+ * stderr) before any device work.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make it before any
+ * stream capture.  Calls share the array: calls whose kernels overlap on
+ * the GPU (different streams or threads) race on it. */
+int  lm_apply_dot_noalloc(int ndim, const int64_t n[3], const int bc[3], const double* ctilde,
+                          const double* gx, const double* gy, const double* gz, const double* x,
+                          double* y, double* dot_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,7 @@ _SIGNATURES = {
     "lm_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "lm_mg_vcycle": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
     "lm_mg_level_shape": (ctypes.c_int, [_P, ctypes.c_int, _I64_3, ctypes.POINTER(ctypes.c_int)]),
+    "lm_apply_dot_noalloc": (ctypes.c_int, [ctypes.c_int, _I64_3, _I3, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -285,3 +286,18 @@ class Grid:
             _check(lib().lm_mg_level_shape(self._g, l, out, ctypes.byref(nl)), "lm_mg_level_shape")
             shapes.append(tuple(out))
         return shapes
+
+
+def apply_dot_noalloc(ndim, n, bc, ctilde, gx, gy, gz, x, y, dot_out, stream=None):
+    """y = A x and dot_out[0] = x^T A x through lm_apply_dot_noalloc: all
+    arguments are CUDA float64 tensors except n, bc; nothing is allocated."""
+    n = tuple(int(v) for v in n)
+    N = n[0] * n[1] * n[2]
+    ptrs = []
+    for t, size in ((ctilde, N), (gx, N), (gy, N), (gz, N), (x, N), (y, N), (dot_out, 1)):
+        ptr, on_dev, keep = _field(t, size)
+        if not on_dev:
+            raise ValueError("lm_apply_dot_noalloc takes device tensors")
+        ptrs.append(ptr)
+    return _check(lib().lm_apply_dot_noalloc(int(ndim), _I64_3(*n), _I3(*bc), *ptrs, _stream_ptr(stream)),
+                  "lm_apply_dot_noalloc")
