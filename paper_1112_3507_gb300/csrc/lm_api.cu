@@ -32,9 +32,11 @@ struct MgLevel {
     Lev32 L;
     double h[3];
     int halved[3] = {0, 0, 0};      // axes halved to reach the next level
-    float* ct = nullptr;            // owned on levels >= 1
+    float* ct = nullptr;            // coefficients (owned on levels >= 1)
     float* rho = nullptr;
-    float* x = nullptr;             // correction (levels >= 1)
+    float* xa = nullptr;            // sweep buffers (level 0: the grid's tmp_a/tmp_b)
+    float* xb = nullptr;
+    float* xo = nullptr;            // V-cycle output (levels >= 1; level 0 writes the caller's z)
     float* f = nullptr;             // right-hand side (levels >= 1)
     float* ainv = nullptr;          // dense inverse on a direct coarsest level
 };
@@ -55,6 +57,9 @@ struct lm_grid {
     double *f = nullptr, *x = nullptr, *x0 = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     float *ct32 = nullptr, *rho32 = nullptr;
     float *r32 = nullptr, *e32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    float *tmp_a = nullptr, *tmp_b = nullptr;   // level-0 sweep buffers
+    double* scal = nullptr;         // reduction results (float32 kernels)
+    unsigned int* ctr = nullptr;    // last-block arrival counter
     double* stage = nullptr;        // 3N host-input staging (allocated on first use)
     double* part = nullptr;         // NSLOT * MAX_PARTIALS
     double* dscal = nullptr;        // device scalars for lm_apply dots
@@ -68,6 +73,7 @@ struct lm_grid {
     double* dscal_host = nullptr;
 
     bool have_coefs = false, have_rhs = false, have_x0 = false;
+    bool have_dinv = false;         // inverse Jacobi diagonal (formed on the first Jacobi solve)
     bool mg_built = false;
     std::vector<MgLevel> mg;
     std::vector<double> history;
@@ -134,7 +140,9 @@ void free_mg(lm_grid* g) {
         if (l > 0) {
             cudaFree(M.ct);
             cudaFree(M.rho);
-            cudaFree(M.x);
+            cudaFree(M.xa);
+            cudaFree(M.xb);
+            cudaFree(M.xo);
             cudaFree(M.f);
         }
         cudaFree(M.ainv);
@@ -156,6 +164,8 @@ int build_mg(lm_grid* g, cudaStream_t s) {
     MgLevel L0;
     L0.L = make_lev(g->n, g->bc, g->h, g->ct32, g->rho32);
     std::memcpy(L0.h, g->h, sizeof L0.h);
+    L0.xa = g->tmp_a;
+    L0.xb = g->tmp_b;
     g->mg.push_back(L0);
     while (g->mg.back().L.g.N > COARSE_MAX) {
         MgLevel& F = g->mg.back();
@@ -176,8 +186,8 @@ int build_mg(lm_grid* g, cudaStream_t s) {
         }
         const int Nc = nc[0] * nc[1] * nc[2];
         int rc;
-        if ((rc = dalloc(&C.ct, Nc)) || (rc = dalloc(&C.rho, Nc)) || (rc = dalloc(&C.x, Nc)) ||
-            (rc = dalloc(&C.f, Nc)))
+        if ((rc = dalloc(&C.ct, Nc)) || (rc = dalloc(&C.rho, Nc)) || (rc = dalloc(&C.xa, Nc)) ||
+            (rc = dalloc(&C.xb, Nc)) || (rc = dalloc(&C.xo, Nc)) || (rc = dalloc(&C.f, Nc)))
             return rc;
         C.L = make_lev(nc, g->bc, C.h, C.ct, C.rho);
         launch_coarsen(F.L, C.L, hv[0], hv[1], hv[2], s, C.ct, C.rho);
@@ -194,36 +204,52 @@ int build_mg(lm_grid* g, cudaStream_t s) {
     return LM_OK;
 }
 
-// One V-cycle on level l: x = M_l f (zero initial guess).
-void vcycle(lm_grid* g, int l, float* x, const float* f, int nu1, int nu2, cudaStream_t s) {
+// A chain of fused red-black sweeps on one level: sweep 0 reads `src`
+// (or zero, or src + P ec), each later sweep reads the previous result; the
+// last sweep writes `dst`, the others ping-pong through the level's xa/xb
+// without writing the buffer they read.  Returns the buffer holding the result.
+float* sweep_chain(MgLevel& M, cudaStream_t s, int count, const int* first, const float* src, bool zero,
+                   const float* ec, const MgLevel* C, const float* f, float* dst) {
+    const float* cur = src;
+    float* out = dst;
+    for (int it = 0; it < count; ++it) {
+        if (it == count - 1 && dst) {
+            out = dst;
+        } else {
+            out = (cur == M.xa) ? M.xb : M.xa;
+        }
+        const bool z0 = zero && it == 0;
+        const bool pr = ec && it == 0;
+        launch_rbgs(M.L, s, z0 ? nullptr : cur, pr ? ec : nullptr, pr ? &C->L : nullptr,
+                    pr ? M.halved[0] : 0, pr ? M.halved[1] : 0, pr ? M.halved[2] : 0, f, out, first[it], z0, pr);
+        cur = out;
+    }
+    return out;
+}
+
+// One V-cycle on level l: xout = M_l f from a zero initial guess.  Pre-
+// smoothing sweeps red then black, post-smoothing black then red (the
+// adjoint order), so the cycle is symmetric for nu1 == nu2.
+void vcycle(lm_grid* g, int l, float* xout, const float* f, int nu1, int nu2, cudaStream_t s) {
     MgLevel& M = g->mg[l];
     const bool last = (size_t)l + 1 == g->mg.size();
+    int order[2 * COARSE_SWEEPS + 8];
     if (last) {
         if (M.ainv) {
-            launch_coarse_solve(M.L.g.N, s, M.ainv, f, x);
+            launch_coarse_solve(M.L.g.N, s, M.ainv, f, xout);
         } else {
-            for (int it = 0; it < COARSE_SWEEPS; ++it) {
-                launch_smooth(M.L, s, x, f, 0, it == 0);
-                launch_smooth(M.L, s, x, f, 1, 0);
-                launch_smooth(M.L, s, x, f, 1, 0);
-                launch_smooth(M.L, s, x, f, 0, 0);
-            }
+            for (int it = 0; it < 2 * COARSE_SWEEPS; ++it) order[it] = it & 1;   // (RB, BR) pairs
+            sweep_chain(M, s, 2 * COARSE_SWEEPS, order, nullptr, true, nullptr, nullptr, f, xout);
         }
         return;
     }
-    if (nu1 == 0) cudaMemsetAsync(x, 0, sizeof(float) * M.L.g.N, s);
-    for (int it = 0; it < nu1; ++it) {
-        launch_smooth(M.L, s, x, f, 0, it == 0);
-        launch_smooth(M.L, s, x, f, 1, 0);
-    }
+    for (int it = 0; it < nu1; ++it) order[it] = 0;
+    float* pre = sweep_chain(M, s, nu1, order, nullptr, true, nullptr, nullptr, f, nullptr);
     MgLevel& C = g->mg[l + 1];
-    launch_resid_restrict(M.L, C.L, M.halved[0], M.halved[1], M.halved[2], s, x, f, C.f);
-    vcycle(g, l + 1, C.x, C.f, nu1, nu2, s);
-    launch_prolong_add(M.L, C.L, M.halved[0], M.halved[1], M.halved[2], s, x, C.x);
-    for (int it = 0; it < nu2; ++it) {
-        launch_smooth(M.L, s, x, f, 1, 0);
-        launch_smooth(M.L, s, x, f, 0, 0);
-    }
+    launch_resid_restrict(M.L, C.L, M.halved[0], M.halved[1], M.halved[2], s, pre, f, C.f);
+    vcycle(g, l + 1, C.xo, C.f, nu1, nu2, s);
+    for (int it = 0; it < nu2; ++it) order[it] = 1;
+    sweep_chain(M, s, nu2, order, pre, false, C.xo, &C, f, xout);
 }
 
 PcgArgs pcg_args(lm_grid* g, int max_iter) {
@@ -269,6 +295,10 @@ int solve_jacobi_pcg(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
     if ((rc = ensure_hist(g, o->max_iter + 2))) return rc;
     if ((rc = init_state(g, g->st, o->rtol, s))) return rc;
     PcgArgs a = pcg_args(g, o->max_iter);
+    if (!g->have_dinv) {
+        launch_jacobi_diag(g->geo, g->G, s, op64(g), g->dinv);
+        g->have_dinv = true;
+    }
     if (o->use_x0 && g->have_x0) CK(cudaMemcpyAsync(g->x, g->x0, sizeof(double) * g->N, cudaMemcpyDeviceToDevice, s));
     launch_pcg_init(a, g->G, s, o->use_x0 && g->have_x0);
     CK(cudaGetLastError());
@@ -325,9 +355,8 @@ int solve_mg_pcg(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
         return LM_OK;
     }
     int k = 0;
-    const int nu1 = std::max(0, o->nu1), nu2 = std::max(0, o->nu2);
     while (g->st_host->rel > o->rtol && k < o->max_iter) {
-        vcycle(g, 0, g->z32, g->r32, nu1, nu2, s);
+        vcycle(g, 0, g->z32, g->r32, o->nu1, o->nu2, s);
         res->vcycles++;
         launch_fcg64_iter_a(g->N, g->G, s, g->z32, g->q, g->part, k == 0, g->p, g->st);
         launch_fcg64_iter_b(g->geo, g->G, s, op64(g), g->x, g->r, g->r32, g->p, g->q, g->part, g->st);
@@ -349,20 +378,18 @@ int solve_mg_pcg(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
 int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, int* vcycles) {
     int rc;
     MgLevel& M = g->mg[0];
+    const Red red{g->part, g->scal, g->ctr};
     CK(cudaMemsetAsync(g->e32, 0, sizeof(float) * g->N, s));
     if ((rc = init_state(g, g->st_in, o->inner_rtol, s))) return rc;
     // the inner problem's reference norm: ||r|| of its right-hand side
-    launch_dot32(g->N, g->G, s, g->r32, g->r32, g->part, 4);
-    launch_set_fnorm(g->part, 4, g->G, s, g->st_in);
-    const int nu1 = std::max(0, o->nu1), nu2 = std::max(0, o->nu2);
+    launch_dot32(g->N, g->G, s, g->r32, g->r32, red, 4, g->st_in);
     for (int it = 0; it < o->inner_max_iter; ++it) {
-        vcycle(g, 0, g->z32, g->r32, nu1, nu2, s);
+        vcycle(g, 0, g->z32, g->r32, o->nu1, o->nu2, s);
         ++*vcycles;
-        if (it > 0) launch_dot32(g->N, g->G, s, g->z32, g->q32, g->part, 5);
-        launch_fcg_beta_p(g->N, g->G, s, g->z32, g->p32, g->q32, g->part, it == 0);
-        launch_fcg_apply(M.L, g->G, s, g->p32, g->q32, g->r32, g->part);
-        launch_fcg_update(g->N, g->G, s, g->e32, g->r32, g->p32, g->q32, g->part, g->st_in);
-        launch_reduce_rel(g->part, g->G, s, g->st_in, nullptr);
+        if (it > 0) launch_dot32(g->N, g->G, s, g->z32, g->q32, red, 3, nullptr);
+        launch_fcg_beta_p(g->N, g->G, s, g->z32, g->p32, g->scal, it == 0);
+        launch_apply32(M.L, s, g->p32, g->q32, g->r32, red, 0, 2);
+        launch_fcg_update(g->N, g->G, s, g->e32, g->r32, g->p32, g->q32, red, g->st_in);
         CK(cudaGetLastError());
         ++*iters;
         if ((rc = sync_state(g, g->st_in, s))) return rc;
@@ -444,6 +471,7 @@ int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double
     CK(cudaMemcpyAsync(g->bad_host, g->bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     g->mg_built = false;
+    g->have_dinv = false;
     if (*g->bad_host) {
         g->have_coefs = false;
         return LM_ERR_NOT_POSITIVE;
@@ -523,11 +551,14 @@ int lm_grid_create(int ndim, const int64_t n[3], const double h[3], const int bc
     double** d64[] = {&g->ct, &g->gx, &g->gy, &g->gz, &g->dinv, &g->f, &g->x, &g->r, &g->p, &g->q};
     for (double** p : d64)
         if ((rc = dalloc(p, N))) return fail(rc);
-    float** d32[] = {&g->ct32, &g->rho32, &g->r32, &g->e32, &g->z32, &g->p32, &g->q32};
+    float** d32[] = {&g->ct32, &g->rho32, &g->r32, &g->e32, &g->z32, &g->p32, &g->q32, &g->tmp_a, &g->tmp_b};
     for (float** p : d32)
         if ((rc = dalloc(p, N))) return fail(rc);
     if ((rc = dalloc(&g->part, (size_t)NSLOT * MAX_PARTIALS))) return fail(rc);
     if ((rc = dalloc(&g->dscal, 8))) return fail(rc);
+    if ((rc = dalloc(&g->scal, 16))) return fail(rc);
+    if ((rc = dalloc(&g->ctr, 1))) return fail(rc);
+    if (cudaMemset(g->ctr, 0, sizeof(unsigned int)) != cudaSuccess) return fail(LM_ERR_CUDA);
     if ((rc = dalloc(&g->st, 1))) return fail(rc);
     if ((rc = dalloc(&g->st_in, 1))) return fail(rc);
     if ((rc = dalloc(&g->bad, 1))) return fail(rc);
@@ -545,7 +576,8 @@ void lm_grid_destroy(lm_grid* g) {
     cudaDeviceSynchronize();
     free_mg(g);
     void* bufs[] = {g->ct, g->gx, g->gy, g->gz, g->dinv, g->f, g->x, g->x0, g->r, g->p, g->q,
-                    g->ct32, g->rho32, g->r32, g->e32, g->z32, g->p32, g->q32, g->stage, g->part,
+                    g->ct32, g->rho32, g->r32, g->e32, g->z32, g->p32, g->q32, g->tmp_a, g->tmp_b,
+                    g->scal, g->ctr, g->stage, g->part,
                     g->dscal, g->st, g->st_in, g->hist_dev, g->bad};
     for (void* b : bufs) cudaFree(b);
     cudaFreeHost(g->st_host);
@@ -601,7 +633,8 @@ int lm_solve(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
     if (!g->have_coefs || !g->have_rhs) return res->status = LM_ERR_STATE;
     if (!(o->rtol > 0.0) || o->max_iter < 1) return res->status = LM_ERR_INVALID_ARG;
     const bool mg = o->mode != LM_FP64_JACOBI_PCG;
-    if (mg && !mg_supported(g)) return res->status = LM_ERR_INVALID_ARG;
+    if (mg && (!mg_supported(g) || o->nu1 < 1 || o->nu2 < 1 || o->nu1 > 8 || o->nu2 > 8))
+        return res->status = LM_ERR_INVALID_ARG;
     if (o->mode < 0 || o->mode > LM_MIXED_LEARNED_FCG_IR) return res->status = LM_ERR_INVALID_ARG;
     cudaStream_t s = S(o->cuda_stream);
     CK(cudaEventRecord(g->ev0, s));
@@ -653,17 +686,19 @@ int lm_apply(lm_grid* g, int prec, const void* x, void* y, double* dot_out, void
     if (!g || !x || !y || (prec != LM_PREC_FP64 && prec != LM_PREC_FP32)) return LM_ERR_INVALID_ARG;
     if (!g->have_coefs) return LM_ERR_STATE;
     cudaStream_t s = S(stream);
-    double* part = dot_out ? g->part : nullptr;
+    const double* dot_dev = g->dscal;
     if (prec == LM_PREC_FP64) {
-        launch_apply64(g->geo, g->G, s, op64(g), (const double*)x, (double*)y, part);
+        launch_apply64(g->geo, g->G, s, op64(g), (const double*)x, (double*)y, dot_out ? g->part : nullptr);
+        if (dot_out) launch_reduce_slot(g->part, 0, g->G, s, g->dscal);
     } else {
         Lev32 L = make_lev(g->n, g->bc, g->h, g->ct32, g->rho32);
-        launch_apply32(L, g->G, s, (const float*)x, (float*)y, part);
+        const Red red{g->part, g->scal, g->ctr};
+        launch_apply32(L, s, (const float*)x, (float*)y, nullptr, red, dot_out ? 0 : -1, -1);
+        dot_dev = g->scal;
     }
     CK(cudaGetLastError());
     if (dot_out) {
-        launch_reduce_slot(g->part, 0, g->G, s, g->dscal);
-        CK(cudaMemcpyAsync(g->dscal_host, g->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(g->dscal_host, dot_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         *dot_out = g->dscal_host[0];
     }
@@ -671,7 +706,7 @@ int lm_apply(lm_grid* g, int prec, const void* x, void* y, double* dot_out, void
 }
 
 int lm_mg_vcycle(lm_grid* g, const float* r, float* z, int nu1, int nu2, void* stream) {
-    if (!g || !r || !z || nu1 < 0 || nu2 < 0) return LM_ERR_INVALID_ARG;
+    if (!g || !r || !z || nu1 < 1 || nu2 < 1 || nu1 > 8 || nu2 > 8) return LM_ERR_INVALID_ARG;
     if (!g->have_coefs) return LM_ERR_STATE;
     if (!mg_supported(g)) return LM_ERR_INVALID_ARG;
     cudaStream_t s = S(stream);

@@ -13,7 +13,7 @@
 namespace lm {
 
 constexpr int NT = 256;             // threads per block of the streaming kernels
-constexpr int MAX_PARTIALS = 4096;  // upper bound on blocks of a reducing kernel
+constexpr int MAX_PARTIALS = 65536; // upper bound on blocks of a reducing kernel
 constexpr int NSLOT = 8;            // partial-sum slots per reduction buffer
 
 struct Geo {
@@ -71,14 +71,22 @@ __device__ __forceinline__ bool face_plus(int c, int n, int bc) {
 
 // ---- reductions ------------------------------------------------------------
 
-// Sum of v over the block; result valid in thread 0 only.  Fixed order.
+__device__ __forceinline__ int lin_tid() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }
+__device__ __forceinline__ int lin_nthreads() { return blockDim.x * blockDim.y * blockDim.z; }
+__device__ __forceinline__ unsigned lin_block() {
+    return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+}
+
+// Sum of v over the block (any shape, whole warps); result valid in linear
+// thread 0 only.  Fixed order.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double* smem /* K*32 */) {
 #pragma unroll
     for (int q = 0; q < K; ++q)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int t = lin_tid();
+    const int w = t >> 5, l = t & 31, nw = lin_nthreads() >> 5;
     if (l == 0)
 #pragma unroll
         for (int q = 0; q < K; ++q) smem[q * 32 + w] = v[q];
@@ -95,27 +103,60 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* smem /* K*32 *
     __syncthreads();
 }
 
-// Write the block's K partial sums to part[q*MAX_PARTIALS + blockIdx.x].
+// Write the block's K partial sums to part[q*MAX_PARTIALS + block].
 template <int K>
 __device__ __forceinline__ void write_partials(double (&v)[K], double* part, double* smem) {
     block_sum<K>(v, smem);
-    if (threadIdx.x == 0)
+    if (lin_tid() == 0)
 #pragma unroll
-        for (int q = 0; q < K; ++q) part[q * MAX_PARTIALS + blockIdx.x] = v[q];
+        for (int q = 0; q < K; ++q) part[q * MAX_PARTIALS + lin_block()] = v[q];
 }
 
 // Deterministic sum of G block partials, computed identically by every block
 // that calls it (same data, same order); the value is returned to all threads.
 __device__ __forceinline__ double reduce_partials(const double* part, int G, double* smem) {
     double v[1] = {0.0};
-    for (int t = threadIdx.x; t < G; t += blockDim.x) v[0] += part[t];
+    for (int t = lin_tid(); t < G; t += lin_nthreads()) v[0] += __ldcg(part + t);
     block_sum<1>(v, smem);
     __shared__ double bcast;
-    if (threadIdx.x == 0) bcast = v[0];
+    if (lin_tid() == 0) bcast = v[0];
     __syncthreads();
     double r = bcast;
     __syncthreads();
     return r;
+}
+
+// Grid-wide reduction by the last block to finish (no waiting): every block
+// stores its partial sums, counts itself in, and the block that arrives last
+// sums all partials in block order -- the same order every run -- into
+// scal[slot[q]] and re-arms the counter.  Returns true in that block.
+struct Red {
+    double* part;        // K * MAX_PARTIALS
+    double* scal;        // result slots
+    unsigned int* ctr;   // arrival counter, 0 between launches
+};
+
+template <int K>
+__device__ __forceinline__ bool grid_reduce(double (&v)[K], const Red& red, const int (&slot)[K], double* smem) {
+    block_sum<K>(v, smem);
+    __shared__ unsigned int s_last;
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    if (lin_tid() == 0) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) red.part[q * MAX_PARTIALS + lin_block()] = v[q];
+        __threadfence();
+        s_last = (atomicAdd(red.ctr, 1u) == nb - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const double tot = reduce_partials(red.part + q * MAX_PARTIALS, (int)nb, smem);
+        if (lin_tid() == 0) red.scal[slot[q]] = tot;
+    }
+    if (lin_tid() == 0) *red.ctr = 0u;
+    return true;
 }
 
 // Float-float accumulator: products formed exactly (TwoProduct by FMA) and

@@ -1,9 +1,13 @@
 // Float32 kernels: the operator with faces formed on the fly from rho, the
 // flexible-CG vector steps with float64-accurate dot products, and the
-// geometric-multigrid V-cycle pieces (coefficient coarsening, red-black
-// Gauss-Seidel, fused residual + restriction, prolongation, exact coarsest
-// solve).  These are HBM-bound: each reads its vectors once and recomputes
-// face conductances from rho instead of storing them.
+// geometric-multigrid V-cycle (coefficient coarsening, a fused red-black
+// Gauss-Seidel sweep, fused residual + restriction, exact coarsest solve).
+//
+// These kernels are HBM-bound.  They stream each array once: face
+// conductances are recomputed from rho instead of stored; cells are mapped
+// to threads with 2D/3D launches (no integer division per cell); the
+// stencils march along z keeping the z-neighbours in registers; and a whole
+// red-black sweep is one pass over memory (see k_rbgs).
 #include "lm_common.cuh"
 #include "lm_kernels.h"
 
@@ -12,6 +16,158 @@ namespace lm {
 // g = (2/h^2) / (rho_a + rho_b); the sum is commutative, so both cells of a
 // face compute the same bits and the operator stays exactly symmetric.
 __device__ __forceinline__ float face32(float ra, float rb, float c2) { return __fdividef(c2, ra + rb); }
+
+// ---- y = A x, marching along z --------------------------------------------
+// 3D: block (32, 8) covers an x-y tile, blockIdx.z a chunk of KZ_APPLY planes.
+// 2D (ny = 1): block (32, 8) covers 32 columns x 8 chunks of KZ_APPLY rows.
+constexpr int KZ_APPLY = 16;
+
+template <bool HAS_Y, bool DOT_XY, bool DOT_XR>
+__global__ void __launch_bounds__(256) k_apply32z(Lev32 L, const float* __restrict__ x, float* __restrict__ y,
+                                                  const float* __restrict__ r, Red red, int slot_xy, int slot_xr) {
+    __shared__ double sm[64];
+    const Geo& g = L.g;
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    int j, kb;
+    if (HAS_Y) {
+        j = blockIdx.y * 8 + threadIdx.y;
+        kb = blockIdx.z * KZ_APPLY;
+    } else {
+        j = 0;
+        kb = (blockIdx.y * 8 + threadIdx.y) * KZ_APPLY;
+    }
+    FF axy{0.f, 0.f}, axr{0.f, 0.f};
+    if (i < g.nx && j < g.ny && kb < g.nz) {
+        const int ke = min(kb + KZ_APPLY, g.nz);
+        const int sz = g.nx * g.ny;
+        const int col = i + g.nx * j;
+        const int cxm = i > 0 ? col - 1 : col + g.nx - 1;
+        const int cxp = i < g.nx - 1 ? col + 1 : col - (g.nx - 1);
+        const bool fxm = face_minus(i, g.nx, g.bcx), fxp = face_plus(i, g.nx, g.bcx);
+        int cym = col, cyp = col;
+        bool fym = false, fyp = false;
+        if (HAS_Y) {
+            cym = j > 0 ? col - g.nx : col + (g.ny - 1) * g.nx;
+            cyp = j < g.ny - 1 ? col + g.nx : col - (g.ny - 1) * g.nx;
+            fym = face_minus(j, g.ny, g.bcy);
+            fyp = face_plus(j, g.ny, g.bcy);
+        }
+        const int kd0 = kb > 0 ? kb - 1 : g.nz - 1;
+        float xd = x[col + sz * kd0], rd = L.rho[col + sz * kd0];
+        float xc = x[col + sz * kb], rc = L.rho[col + sz * kb];
+        float ctc = L.ct[col + sz * kb], rrc = DOT_XR ? r[col + sz * kb] : 0.f;
+        for (int k = kb; k < ke; ++k) {
+            const int ku = k < g.nz - 1 ? k + 1 : 0;
+            // next plane's streams are requested before this plane's arithmetic
+            const float xu = x[col + sz * ku], ru = L.rho[col + sz * ku];
+            const float ctn = L.ct[col + sz * ku], rrn = DOT_XR ? r[col + sz * ku] : 0.f;
+            const int o = sz * k;
+            float v = ctc * xc;
+            if (fxm) v += face32(rc, L.rho[cxm + o], L.c2x) * (xc - x[cxm + o]);
+            if (fxp) v += face32(rc, L.rho[cxp + o], L.c2x) * (xc - x[cxp + o]);
+            if (HAS_Y) {
+                if (fym) v += face32(rc, L.rho[cym + o], L.c2y) * (xc - x[cym + o]);
+                if (fyp) v += face32(rc, L.rho[cyp + o], L.c2y) * (xc - x[cyp + o]);
+            }
+            if (face_minus(k, g.nz, g.bcz)) v += face32(rc, rd, L.c2z) * (xc - xd);
+            if (face_plus(k, g.nz, g.bcz)) v += face32(rc, ru, L.c2z) * (xc - xu);
+            y[col + o] = v;
+            if (DOT_XY) ff_add_prod(axy, xc, v);
+            if (DOT_XR) ff_add_prod(axr, xc, rrc);
+            xd = xc;
+            rd = rc;
+            xc = xu;
+            rc = ru;
+            ctc = ctn;
+            rrc = rrn;
+        }
+    }
+    if (DOT_XY && DOT_XR) {
+        double v[2] = {ff_value(axy), ff_value(axr)};
+        const int sl[2] = {slot_xy, slot_xr};
+        grid_reduce<2>(v, red, sl, sm);
+    } else if (DOT_XY) {
+        double v[1] = {ff_value(axy)};
+        const int sl[1] = {slot_xy};
+        grid_reduce<1>(v, red, sl, sm);
+    }
+}
+
+// ---- flexible-CG vector steps (1D, grid-stride) ---------------------------
+// scal slots: 0 p.q, 1 r.r, 2 p.r, 3 z.q_old, 4 r0.r0
+
+// scal[slot] = a.b; if fnorm_st: also fnorm_st->fnorm = sqrt(a.b), rel = 1.
+__global__ void __launch_bounds__(NT) k_dot32(int N, const float* __restrict__ a, const float* __restrict__ b,
+                                              Red red, int slot, SolveState* fnorm_st) {
+    __shared__ double sm[32];
+    FF acc{0.f, 0.f};
+    const int stride = gridDim.x * blockDim.x;
+#pragma unroll 4
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride) ff_add_prod(acc, a[idx], b[idx]);
+    double v[1] = {ff_value(acc)};
+    const int sl[1] = {slot};
+    if (grid_reduce<1>(v, red, sl, sm) && fnorm_st && lin_tid() == 0) {
+        fnorm_st->fnorm = sqrt(red.scal[slot]);
+        fnorm_st->rel = 1.0;
+    }
+}
+
+// Flexible CG, truncation 1 (Notay 2000): p = z - (z.q_old / p_old.q_old) p_old.
+__global__ void __launch_bounds__(NT) k_fcg_beta_p(int N, const float* __restrict__ z, float* __restrict__ p,
+                                                   const double* __restrict__ scal, int first) {
+    float beta = 0.f;
+    if (!first) {
+        const double pq = scal[0];
+        beta = pq > 0.0 ? (float)(-scal[3] / pq) : 0.f;
+    }
+    const int stride = gridDim.x * blockDim.x;
+#pragma unroll 4
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride)
+        p[idx] = first ? z[idx] : fmaf(beta, p[idx], z[idx]);
+}
+
+// alpha = p.r / p.q; e += alpha p; r -= alpha q; scal[1] = r.r; the last
+// block sets st->rel = ||r|| / st->fnorm (and the breakdown status).
+__global__ void __launch_bounds__(NT) k_fcg_update(int N, float* __restrict__ e, float* __restrict__ r,
+                                                   const float* __restrict__ p, const float* __restrict__ q,
+                                                   Red red, SolveState* st) {
+    __shared__ double sm[32];
+    const double pq = red.scal[0], pr = red.scal[2];
+    const bool bad = !(pq > 0.0) || !isfinite(pq) || !isfinite(pr);
+    const float alpha = bad ? 0.f : (float)(pr / pq);
+    FF rr{0.f, 0.f};
+    const int stride = gridDim.x * blockDim.x;
+#pragma unroll 4
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride) {
+        const float pi = p[idx];
+        e[idx] = fmaf(alpha, pi, e[idx]);
+        const float ri = fmaf(-alpha, q[idx], r[idx]);
+        r[idx] = ri;
+        ff_add_prod(rr, ri, ri);
+    }
+    double v[1] = {ff_value(rr)};
+    const int sl[1] = {1};
+    if (grid_reduce<1>(v, red, sl, sm) && lin_tid() == 0) {
+        if (bad) st->status = LM_ERR_BREAKDOWN;
+        st->rel = sqrt(red.scal[1]) / st->fnorm;
+    }
+}
+
+// ---- multigrid --------------------------------------------------------------
+
+// Cell of a 2D/3D-mapped launch: block (32, 8); 3D grid (nx/32, ny/8, nz),
+// 2D grid (nx/32, nz/8, 1).
+__device__ __forceinline__ bool map_cell(const Geo& g, int& i, int& j, int& k) {
+    i = blockIdx.x * 32 + threadIdx.x;
+    if (g.ny > 1) {
+        j = blockIdx.y * 8 + threadIdx.y;
+        k = blockIdx.z;
+    } else {
+        j = 0;
+        k = blockIdx.y * 8 + threadIdx.y;
+    }
+    return i < g.nx && j < g.ny && k < g.nz;
+}
 
 __device__ __forceinline__ float apply32_at(int idx, int i, int j, int k, const Lev32& L,
                                             const float* __restrict__ x) {
@@ -32,192 +188,31 @@ __device__ __forceinline__ float apply32_at(int idx, int i, int j, int k, const 
     return y;
 }
 
-// ---- operator and flexible CG ---------------------------------------------
-
-__global__ void __launch_bounds__(NT) k_apply32(Lev32 L, const float* __restrict__ x, float* __restrict__ y,
-                                                double* __restrict__ part) {
-    __shared__ double sm[32];
-    FF acc{0.f, 0.f};
-    const int stride = gridDim.x * blockDim.x;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.g.N; idx += stride) {
-        int i, j, k;
-        cell_coords(idx, L.g, i, j, k);
-        const float v = apply32_at(idx, i, j, k, L, x);
-        y[idx] = v;
-        ff_add_prod(acc, x[idx], v);
-    }
-    if (part) {
-        double v[1] = {ff_value(acc)};
-        write_partials<1>(v, part, sm);
-    }
-}
-
-__global__ void __launch_bounds__(NT) k_dot32(int N, const float* __restrict__ a, const float* __restrict__ b,
-                                              double* __restrict__ part) {
-    __shared__ double sm[32];
-    FF acc{0.f, 0.f};
-    const int stride = gridDim.x * blockDim.x;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride) ff_add_prod(acc, a[idx], b[idx]);
-    double v[1] = {ff_value(acc)};
-    write_partials<1>(v, part, sm);
-}
-
-// Flexible CG, truncation 1 (Notay 2000): p = z - (z.q_old / p_old.q_old) p_old.
-// Slots: 0 p.q, 1 r.r, 5 z.q_old, 6 p.r
-__global__ void __launch_bounds__(NT) k_fcg_beta_p(int N, const float* __restrict__ z, float* __restrict__ p,
-                                                   const double* __restrict__ part, int first) {
-    __shared__ double sm[32];
-    float beta = 0.f;
-    if (!first) {
-        const double zq = reduce_partials(part + 5 * MAX_PARTIALS, gridDim.x, sm);
-        const double pq = reduce_partials(part + 0 * MAX_PARTIALS, gridDim.x, sm);
-        beta = pq > 0.0 ? (float)(-zq / pq) : 0.f;
-    }
-    const int stride = gridDim.x * blockDim.x;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride)
-        p[idx] = first ? z[idx] : fmaf(beta, p[idx], z[idx]);
-}
-
-__global__ void __launch_bounds__(NT) k_fcg_apply(Lev32 L, const float* __restrict__ p, float* __restrict__ q,
-                                                  const float* __restrict__ r, double* __restrict__ part) {
-    __shared__ double sm[64];
-    FF pq{0.f, 0.f}, pr{0.f, 0.f};
-    const int stride = gridDim.x * blockDim.x;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.g.N; idx += stride) {
-        int i, j, k;
-        cell_coords(idx, L.g, i, j, k);
-        const float v = apply32_at(idx, i, j, k, L, p);
-        q[idx] = v;
-        const float pi = p[idx];
-        ff_add_prod(pq, pi, v);
-        ff_add_prod(pr, pi, r[idx]);
-    }
-    double v[2] = {ff_value(pq), ff_value(pr)};
-    block_sum<2>(v, sm);
-    if (threadIdx.x == 0) {
-        part[0 * MAX_PARTIALS + blockIdx.x] = v[0];
-        part[6 * MAX_PARTIALS + blockIdx.x] = v[1];
-    }
-}
-
-// alpha = p.r / p.q; e += alpha p; r -= alpha q; partial r.r (slot 1)
-__global__ void __launch_bounds__(NT) k_fcg_update(int N, float* __restrict__ e, float* __restrict__ r,
-                                                   const float* __restrict__ p, const float* __restrict__ q,
-                                                   double* __restrict__ part, SolveState* st) {
-    __shared__ double sm[32];
-    const double pq = reduce_partials(part + 0 * MAX_PARTIALS, gridDim.x, sm);
-    const double pr = reduce_partials(part + 6 * MAX_PARTIALS, gridDim.x, sm);
-    const bool bad = !(pq > 0.0) || !isfinite(pq) || !isfinite(pr);
-    if (bad) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) st->status = LM_ERR_BREAKDOWN;
-    }
-    const float alpha = bad ? 0.f : (float)(pr / pq);
-    FF rr{0.f, 0.f};
-    const int stride = gridDim.x * blockDim.x;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride) {
-        const float pi = p[idx];
-        e[idx] = fmaf(alpha, pi, e[idx]);
-        const float ri = fmaf(-alpha, q[idx], r[idx]);
-        r[idx] = ri;
-        ff_add_prod(rr, ri, ri);
-    }
-    double v[1] = {ff_value(rr)};
-    write_partials<1>(v, part + 1 * MAX_PARTIALS, sm);
-}
-
-// ---- multigrid ----------------------------------------------------------------
-
-__device__ __forceinline__ void coords3(int t, int nx, int ny, int& i, int& j, int& k) {
-    i = t % nx;
-    const int u = t / nx;
-    j = u % ny;
-    k = u / ny;
-}
-
-// Mean of the children's c~ and rho (coarse coefficients).
-__global__ void k_coarsen(Lev32 F, Geo C, int hx, int hy, int hz, float* __restrict__ ct_c,
-                          float* __restrict__ rho_c) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= C.N) return;
+// Mean of the children's c~ and rho (coarse coefficients); one thread per coarse cell.
+__global__ void __launch_bounds__(256) k_coarsen(Lev32 F, Geo C, int hx, int hy, int hz, float* __restrict__ ct_c,
+                                                 float* __restrict__ rho_c) {
     int I, J, K;
-    coords3(t, C.nx, C.ny, I, J, K);
+    if (!map_cell(C, I, J, K)) return;
     float sc = 0.f, sr = 0.f;
-    const int nch = (1 << hx) << hy << hz;
     for (int c = 0; c <= hz; ++c)
         for (int b = 0; b <= hy; ++b)
             for (int a = 0; a <= hx; ++a) {
-                const int i = (I << hx) + a, j = (J << hy) + b, k = (K << hz) + c;
-                const int idx = i + F.g.nx * (j + F.g.ny * k);
+                const int idx = ((I << hx) + a) + F.g.nx * (((J << hy) + b) + F.g.ny * ((K << hz) + c));
                 sc += F.ct[idx];
                 sr += F.rho[idx];
             }
-    ct_c[t] = sc / (float)nch;
-    rho_c[t] = sr / (float)nch;
+    const float inv = 1.f / (float)((1 << hx) << hy << hz);
+    const int t = I + C.nx * (J + C.ny * K);
+    ct_c[t] = sc * inv;
+    rho_c[t] = sr * inv;
 }
 
-// Red-black Gauss-Seidel: update every cell of colour `colour`
-// ((i + j + k) mod 2) from its row: x_i = (f_i + sum g x_nb) / (c~_i + sum g).
-// One thread per cell of the colour.  zero_guess: neighbours are taken as 0.
-__global__ void __launch_bounds__(NT) k_smooth(Lev32 L, float* __restrict__ x, const float* __restrict__ f,
-                                               int colour, int zero_guess) {
-    const Geo& g = L.g;
-    const int hw = (g.nx + 1) >> 1;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= hw * g.ny * g.nz) return;
-    const int m = t % hw;
-    const int row = t / hw;
-    const int j = row % g.ny, k = row / g.ny;
-    const int i = 2 * m + ((colour + j + k) & 1);
-    if (i >= g.nx) return;
-    const int idx = i + g.nx * row;
-    const float rc = L.rho[idx];
-    float d = L.ct[idx], num = f[idx];
-    Nbr n = nbr_x(idx, i, g);
-    if (face_minus(i, g.nx, g.bcx)) {
-        const float w = face32(rc, L.rho[n.im], L.c2x);
-        d += w;
-        if (!zero_guess) num += w * x[n.im];
-    }
-    if (face_plus(i, g.nx, g.bcx)) {
-        const float w = face32(rc, L.rho[n.ip], L.c2x);
-        d += w;
-        if (!zero_guess) num += w * x[n.ip];
-    }
-    if (g.ny > 1) {
-        n = nbr_y(idx, j, g);
-        if (face_minus(j, g.ny, g.bcy)) {
-            const float w = face32(rc, L.rho[n.im], L.c2y);
-            d += w;
-            if (!zero_guess) num += w * x[n.im];
-        }
-        if (face_plus(j, g.ny, g.bcy)) {
-            const float w = face32(rc, L.rho[n.ip], L.c2y);
-            d += w;
-            if (!zero_guess) num += w * x[n.ip];
-        }
-    }
-    n = nbr_z(idx, k, g);
-    if (face_minus(k, g.nz, g.bcz)) {
-        const float w = face32(rc, L.rho[n.im], L.c2z);
-        d += w;
-        if (!zero_guess) num += w * x[n.im];
-    }
-    if (face_plus(k, g.nz, g.bcz)) {
-        const float w = face32(rc, L.rho[n.ip], L.c2z);
-        d += w;
-        if (!zero_guess) num += w * x[n.ip];
-    }
-    x[idx] = __fdividef(num, d);
-}
-
-// fc = mean over children of (f - A x): residual and restriction fused.
-__global__ void __launch_bounds__(NT) k_resid_restrict(Lev32 F, Geo C, int hx, int hy, int hz,
-                                                       const float* __restrict__ x, const float* __restrict__ f,
-                                                       float* __restrict__ fc) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= C.N) return;
+// fc = mean over the children of (f - A x): residual and restriction fused.
+__global__ void __launch_bounds__(256) k_resid_restrict(Lev32 F, Geo C, int hx, int hy, int hz,
+                                                        const float* __restrict__ x, const float* __restrict__ f,
+                                                        float* __restrict__ fc) {
     int I, J, K;
-    coords3(t, C.nx, C.ny, I, J, K);
+    if (!map_cell(C, I, J, K)) return;
     float s = 0.f;
     for (int c = 0; c <= hz; ++c)
         for (int b = 0; b <= hy; ++b)
@@ -226,17 +221,303 @@ __global__ void __launch_bounds__(NT) k_resid_restrict(Lev32 F, Geo C, int hx, i
                 const int idx = i + F.g.nx * (j + F.g.ny * k);
                 s += f[idx] - apply32_at(idx, i, j, k, F, x);
             }
-    fc[t] = s / (float)((1 << hx) << hy << hz);
+    fc[I + C.nx * (J + C.ny * K)] = s * (1.f / (float)((1 << hx) << hy << hz));
 }
 
-// x += P xc (piecewise-constant prolongation)
-__global__ void __launch_bounds__(NT) k_prolong_add(Geo F, Geo C, int hx, int hy, int hz, float* __restrict__ x,
-                                                    const float* __restrict__ xc) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= F.N) return;
-    int i, j, k;
-    coords3(t, F.nx, F.ny, i, j, k);
-    x[t] += xc[(i >> hx) + C.nx * ((j >> hy) + C.ny * (k >> hz))];
+// ---- fused red-black Gauss-Seidel sweep ------------------------------------
+//
+// xout = one red-black Gauss-Seidel sweep applied to xold, the FIRST colour
+// ((i + j + k) mod 2 == FIRST) updated first, then the other colour.  The
+// sweep is out of place (xold is read-only), so a block can recompute the
+// first-colour values it needs on a one-cell halo around its tile from xold
+// exactly as the neighbouring block computes them: every block sees the same
+// values, the result equals the in-place sequential sweep, and the whole
+// sweep is a single pass over memory.
+//
+// A block owns a tile of 2*BX x TY cells and marches along z.  Each thread
+// owns an x-pair of cells, which always holds one cell of each colour, so
+// no lane idles on a colour test; the cell that is first-coloured on plane p
+// is second-coloured on plane p - 1, so each thread updates one of its cells
+// per plane and phase.  Shared memory holds rings of planes of xold and rho
+// on the tile + 2-cell halo and of the new first-colour values on the tile +
+// 1-cell halo; f and c~ of a thread's own cells stay in registers.  A few
+// threads also compute the first colour on the halo ring.  Loads for the
+// next plane are issued before the current plane's arithmetic.
+// ZERO:    xold = 0 (first sweep of a V-cycle level: zero initial guess).
+// PROLONG: xold = xin + P ec (piecewise-constant prolongation of the coarse
+//          correction, fused into the post-smoothing sweep).
+template <int BX, int TY, bool HAS_Y, int FIRST, bool ZERO, bool PROLONG>
+__global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, const float* __restrict__ xin,
+                                                  const float* __restrict__ ec, Geo C, int hx, int hy, int hz,
+                                                  const float* __restrict__ f, float* __restrict__ xout, int KZ) {
+    constexpr int TXC = 2 * BX;
+    constexpr int HY = HAS_Y ? 1 : 0;
+    constexpr int EX2 = TXC + 4, EY2 = TY + 4 * HY;    // tile + 2-cell halo (R2)
+    constexpr int EX1 = TXC + 2, EY1 = TY + 2 * HY;    // tile + 1-cell halo (R1)
+    constexpr int NTH = BX * TY;
+    constexpr int N2 = (EX2 * EY2 + NTH - 1) / NTH;
+    constexpr int NHP = HAS_Y ? EX1 : 0;               // halo pairs: EX1/2 on the top and on the bottom R1 row
+    constexpr int NH = NHP + 2 * TY;                   // + single cells of the left and right R1 columns
+    static_assert(NH <= NTH, "halo tasks exceed the block");
+    __shared__ float XO[3][EY2 * EX2];
+    __shared__ float RH[5][EY2 * EX2];
+    __shared__ float F1[3][EY1 * EX1];
+    const Geo& g = L.g;
+    const int tid = threadIdx.x + BX * threadIdx.y;
+    const int i0 = blockIdx.x * TXC;
+    const int j0 = HAS_Y ? blockIdx.y * TY : 0;
+    const int k0 = (HAS_Y ? blockIdx.z : blockIdx.y) * KZ;
+    const int k1 = min(k0 + KZ, g.nz);
+    const int sz = g.nx * g.ny;
+
+    // coordinates reach at most 2 cells past either end: wrap by adding or
+    // subtracting n (twice for n = 1), no division
+    auto wrap = [](int c, int n, int bc, bool& ok) -> int {
+        ok = (c >= 0 && c < n) || bc == LM_BC_PERIODIC;
+        while (c < 0) c += n;
+        while (c >= n) c -= n;
+        return c;
+    };
+    auto ring = [](int p, int m) { return (p + 6) % m; };   // plane p >= -3 -> slot
+    auto flags = [&](int gi, int gj) {
+        return (face_minus(gi, g.nx, g.bcx) ? 1 : 0) | (face_plus(gi, g.nx, g.bcx) ? 2 : 0) |
+               (HAS_Y && face_minus(gj, g.ny, g.bcy) ? 4 : 0) | (HAS_Y && face_plus(gj, g.ny, g.bcy) ? 8 : 0);
+    };
+
+    // staged R2 elements of this thread: in-plane offset (-1: outside a wall), parent offset
+    int off2[N2], poff2[N2];
+#pragma unroll
+    for (int u = 0; u < N2; ++u) {
+        const int e = tid + u * NTH;
+        off2[u] = -1;
+        poff2[u] = 0;
+        if (e < EX2 * EY2) {
+            bool oki, okj = true;
+            const int gi = wrap(i0 - 2 + e % EX2, g.nx, g.bcx, oki);
+            const int gj = HAS_Y ? wrap(j0 - 2 + e / EX2, g.ny, g.bcy, okj) : 0;
+            if (oki && okj) {
+                off2[u] = gi + g.nx * gj;
+                poff2[u] = (gi >> hx) + C.nx * (gj >> hy);
+            }
+        }
+    }
+    // update cells: c = 0, 1 the thread's own x-pair; c = 2, 3 its halo task
+    // (a pair on the top/bottom R1 row, or one cell of the left/right column)
+    // A tile may be wider than a small grid: an own cell past the end of a
+    // periodic axis is the wrapped copy of a cell of this row, and its
+    // first-colour value is what the row's last cell sees as its neighbour,
+    // so it is computed (from wrapped coordinates) but never written out.
+    int ex1c[4], ey1c[4], offc[4], parc[4], flc[4];
+    bool outc[2];
+    {
+        const int ti = threadIdx.x, tj = HAS_Y ? threadIdx.y : 0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            bool oki, okj = true;
+            const int ui = i0 + 2 * ti + c, uj = j0 + tj;
+            const int gi = wrap(ui, g.nx, g.bcx, oki);
+            const int gj = HAS_Y ? wrap(uj, g.ny, g.bcy, okj) : 0;
+            ex1c[c] = 2 * ti + 1 + c;
+            ey1c[c] = tj + HY;
+            const bool ok = oki && okj;
+            offc[c] = ok ? gi + g.nx * gj : -1;
+            parc[c] = (gi + gj) & 1;
+            flc[c] = ok ? flags(gi, gj) : 0;
+            outc[c] = ok && ui < g.nx && uj < g.ny;
+        }
+        int hxp[2] = {0, 0}, hyp = 0, nh = 0;
+        if (tid < NHP) {
+            const int m = tid % (EX1 / 2);
+            hyp = tid < EX1 / 2 ? 0 : EY1 - 1;
+            hxp[0] = 2 * m;
+            hxp[1] = 2 * m + 1;
+            nh = 2;
+        } else if (tid < NH) {
+            const int sidx = tid - NHP;
+            hxp[0] = sidx < TY ? 0 : EX1 - 1;
+            hyp = (sidx % TY) + HY;
+            nh = 1;
+        }
+#pragma unroll
+        for (int c = 2; c < 4; ++c) {
+            ex1c[c] = hxp[c - 2];
+            ey1c[c] = hyp;
+            offc[c] = -1;
+            parc[c] = 0;
+            flc[c] = 0;
+            if (c - 2 < nh) {
+                bool oki, okj = true;
+                const int gi = wrap(i0 - 1 + hxp[c - 2], g.nx, g.bcx, oki);
+                const int gj = HAS_Y ? wrap(j0 - 1 + hyp, g.ny, g.bcy, okj) : 0;
+                if (oki && okj) {
+                    offc[c] = gi + g.nx * gj;
+                    parc[c] = (gi + gj) & 1;
+                    flc[c] = flags(gi, gj);
+                }
+            }
+        }
+    }
+
+    // Gauss-Seidel value x = (f + sum g v) / (c~ + sum g) of an update cell;
+    // neighbour values v from the plane rows Vm/V0/Vp (row width exv) at vi,
+    // rho from the R2 planes Rm/R0/Rp at ri.
+    auto gs = [&](int fl, bool zm, bool zp, float fv, float cv, const float* Vm, const float* V0, const float* Vp,
+                  int exv, int vi, const float* Rm, const float* R0, const float* Rp, int ri) -> float {
+        const float rc = R0[ri];
+        float d = cv, num = fv;
+        if (fl & 1) {
+            const float w = face32(rc, R0[ri - 1], L.c2x);
+            d += w;
+            num += w * V0[vi - 1];
+        }
+        if (fl & 2) {
+            const float w = face32(rc, R0[ri + 1], L.c2x);
+            d += w;
+            num += w * V0[vi + 1];
+        }
+        if (HAS_Y) {
+            if (fl & 4) {
+                const float w = face32(rc, R0[ri - EX2], L.c2y);
+                d += w;
+                num += w * V0[vi - exv];
+            }
+            if (fl & 8) {
+                const float w = face32(rc, R0[ri + EX2], L.c2y);
+                d += w;
+                num += w * V0[vi + exv];
+            }
+        }
+        if (zm) {
+            const float w = face32(rc, Rm[ri], L.c2z);
+            d += w;
+            num += w * Vm[vi];
+        }
+        if (zp) {
+            const float w = face32(rc, Rp[ri], L.c2z);
+            d += w;
+            num += w * Vp[vi];
+        }
+        return __fdividef(num, d);
+    };
+
+    // register staging: x, rho of plane p + 1 on R2 and f, c~ of the update cells on plane p
+    float px[N2], pr[N2], pf[4], pc[4];
+    auto fetch = [&](int p) {
+        bool okp, okq;
+        const int gp = wrap(p + 1, g.nz, g.bcz, okp);
+        const int gq = wrap(p, g.nz, g.bcz, okq);
+#pragma unroll
+        for (int u = 0; u < N2; ++u) {
+            float xv = 0.f, rv = 1.f;
+            if (okp && off2[u] >= 0) {
+                const int idx = off2[u] + sz * gp;
+                rv = L.rho[idx];
+                if (!ZERO) {
+                    xv = xin[idx];
+                    if (PROLONG) xv += ec[poff2[u] + C.nx * C.ny * (gp >> hz)];
+                }
+            }
+            px[u] = xv;
+            pr[u] = rv;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float fv = 0.f, cv = 1.f;
+            if (okq && offc[c] >= 0) {
+                const int idx = offc[c] + sz * gq;
+                fv = f[idx];
+                cv = L.ct[idx];
+            }
+            pf[c] = fv;
+            pc[c] = cv;
+        }
+    };
+    auto store_xr = [&](int p) {
+        float* xo = XO[ring(p + 1, 3)];
+        float* rh = RH[ring(p + 1, 5)];
+#pragma unroll
+        for (int u = 0; u < N2; ++u) {
+            const int e = tid + u * NTH;
+            if (e < EX2 * EY2) {
+                xo[e] = px[u];
+                rh[e] = pr[u];
+            }
+        }
+    };
+
+    float fcur[4], ccur[4], fprev[2], cprev[2];
+    fetch(k0 - 3);
+    store_xr(k0 - 3);              // plane k0 - 2
+    fetch(k0 - 2);
+    store_xr(k0 - 2);              // plane k0 - 1
+    fetch(k0 - 1);                 // x, rho of plane k0; f, c~ of plane k0 - 1
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        fcur[c] = 0.f;
+        ccur[c] = 1.f;
+    }
+    for (int p = k0 - 1; p <= k1; ++p) {
+        store_xr(p);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            fprev[c] = fcur[c];
+            cprev[c] = ccur[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            fcur[c] = pf[c];
+            ccur[c] = pc[c];
+        }
+        if (p < k1) fetch(p + 1);
+        __syncthreads();
+        // first colour on plane p: the thread's own first-colour cell and its halo task
+        bool okp;
+        const int gp = wrap(p, g.nz, g.bcz, okp);
+        {
+            const float* Xm = XO[ring(p - 1, 3)];
+            const float* X0 = XO[ring(p, 3)];
+            const float* Xp = XO[ring(p + 1, 3)];
+            const float* Rm = RH[ring(p - 1, 5)];
+            const float* R0 = RH[ring(p, 5)];
+            const float* Rp = RH[ring(p + 1, 5)];
+            float* f1 = F1[ring(p, 3)];
+            const bool zm = face_minus(gp, g.nz, g.bcz), zp = face_plus(gp, g.nz, g.bcz);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (offc[c] >= 0 && ((parc[c] + gp) & 1) == FIRST) {
+                    const int vi = (ey1c[c] + HY) * EX2 + ex1c[c] + 1;
+                    float v = 0.f;
+                    if (okp) v = gs(flc[c], zm, zp, fcur[c], ccur[c], Xm, X0, Xp, EX2, vi, Rm, R0, Rp, vi);
+                    f1[ey1c[c] * EX1 + ex1c[c]] = v;
+                }
+            }
+        }
+        __syncthreads();
+        // second colour on plane q = p - 1, from the new first colour
+        const int q = p - 1;
+        if (q >= k0) {
+            const float* Fm = F1[ring(q - 1, 3)];
+            const float* F0 = F1[ring(q, 3)];
+            const float* Fp = F1[ring(q + 1, 3)];
+            const float* Rm = RH[ring(q - 1, 5)];
+            const float* R0 = RH[ring(q, 5)];
+            const float* Rp = RH[ring(q + 1, 5)];
+            const bool zm = face_minus(q, g.nz, g.bcz), zp = face_plus(q, g.nz, g.bcz);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (!outc[c]) continue;
+                float v;
+                if (((parc[c] + q) & 1) == FIRST) {
+                    v = F0[ey1c[c] * EX1 + ex1c[c]];
+                } else {
+                    const int vi = ey1c[c] * EX1 + ex1c[c];
+                    const int ri = (ey1c[c] + HY) * EX2 + ex1c[c] + 1;
+                    v = gs(flc[c], zm, zp, fprev[c], cprev[c], Fm, F0, Fp, EX1, vi, Rm, R0, Rp, ri);
+                }
+                xout[offc[c] + sz * q] = v;
+            }
+        }
+    }
 }
 
 // Inverse of the coarsest level's matrix (n <= 64) by in-place Gauss-Jordan
@@ -250,8 +531,7 @@ __global__ void __launch_bounds__(NT) k_coarse_inverse(Lev32 L, float* __restric
     __syncthreads();
     if (threadIdx.x < n) {
         const int idx = threadIdx.x;
-        int i, j, k;
-        coords3(idx, g.nx, g.ny, i, j, k);
+        const int i = idx % g.nx, j = (idx / g.nx) % g.ny, k = idx / (g.nx * g.ny);
         const double rc = L.rho[idx];
         double d = L.ct[idx];
         auto add = [&](bool has, int nb, float c2) {
@@ -278,14 +558,14 @@ __global__ void __launch_bounds__(NT) k_coarse_inverse(Lev32 L, float* __restric
             rowk[threadIdx.x] = A[kk * n + threadIdx.x];
         }
         __syncthreads();
-        const double piv = rowk[kk];
+        const double ipiv = 1.0 / rowk[kk];
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
             const int i = e / n, j = e % n;
             double v;
-            if (i == kk && j == kk) v = 1.0 / piv;
-            else if (i == kk) v = rowk[j] / piv;
-            else if (j == kk) v = -colk[i] / piv;
-            else v = A[e] - colk[i] * rowk[j] / piv;
+            if (i == kk && j == kk) v = ipiv;
+            else if (i == kk) v = rowk[j] * ipiv;
+            else if (j == kk) v = -colk[i] * ipiv;
+            else v = A[e] - colk[i] * (rowk[j] * ipiv);
             A[e] = v;
         }
         __syncthreads();
@@ -304,50 +584,87 @@ __global__ void k_coarse_solve(int n, const float* __restrict__ ainv, const floa
 
 // ---- host launchers -----------------------------------------------------------
 
-static inline int nblk(long long n) { return (int)((n + NT - 1) / NT); }
+static inline int hdiv(int a, int b) { return (a + b - 1) / b; }
 
-void launch_apply32(const Lev32& L, int G, cudaStream_t s, const float* x, float* y, double* part) {
-    count_launches(1);
-    k_apply32<<<G, NT, 0, s>>>(L, x, y, part);
+static dim3 cell_grid(const Geo& g) {
+    return g.ny > 1 ? dim3(hdiv(g.nx, 32), hdiv(g.ny, 8), g.nz) : dim3(hdiv(g.nx, 32), hdiv(g.nz, 8), 1);
 }
-void launch_dot32(int N, int G, cudaStream_t s, const float* a, const float* b, double* part, int slot) {
+
+void launch_apply32(const Lev32& L, cudaStream_t s, const float* x, float* y, const float* r, const Red& red,
+                    int slot_xy, int slot_xr) {
+    const Geo& g = L.g;
+    const dim3 blk(32, 8);
+    const bool y3 = g.ny > 1;
+    const dim3 grd = y3 ? dim3(hdiv(g.nx, 32), hdiv(g.ny, 8), hdiv(g.nz, KZ_APPLY))
+                        : dim3(hdiv(g.nx, 32), hdiv(hdiv(g.nz, KZ_APPLY), 8), 1);
     count_launches(1);
-    k_dot32<<<G, NT, 0, s>>>(N, a, b, part + slot * MAX_PARTIALS);
+    const bool dxy = slot_xy >= 0, dxr = slot_xr >= 0;
+#define LM_APPLY(Y, A, B) k_apply32z<Y, A, B><<<grd, blk, 0, s>>>(L, x, y, r, red, slot_xy, slot_xr)
+    if (y3) {
+        if (dxy && dxr) LM_APPLY(true, true, true);
+        else if (dxy) LM_APPLY(true, true, false);
+        else LM_APPLY(true, false, false);
+    } else {
+        if (dxy && dxr) LM_APPLY(false, true, true);
+        else if (dxy) LM_APPLY(false, true, false);
+        else LM_APPLY(false, false, false);
+    }
+#undef LM_APPLY
 }
-void launch_fcg_beta_p(int N, int G, cudaStream_t s, const float* z, float* p, const float* /*q_old*/,
-                       double* part, int first) {
+void launch_dot32(int N, int G, cudaStream_t s, const float* a, const float* b, const Red& red, int slot,
+                  SolveState* fnorm_st) {
     count_launches(1);
-    k_fcg_beta_p<<<G, NT, 0, s>>>(N, z, p, part, first);
+    k_dot32<<<G, NT, 0, s>>>(N, a, b, red, slot, fnorm_st);
 }
-void launch_fcg_apply(const Lev32& L, int G, cudaStream_t s, const float* p, float* q, const float* r,
-                      double* part) {
+void launch_fcg_beta_p(int N, int G, cudaStream_t s, const float* z, float* p, const double* scal, int first) {
     count_launches(1);
-    k_fcg_apply<<<G, NT, 0, s>>>(L, p, q, r, part);
+    k_fcg_beta_p<<<G, NT, 0, s>>>(N, z, p, scal, first);
 }
 void launch_fcg_update(int N, int G, cudaStream_t s, float* e, float* r, const float* p, const float* q,
-                       double* part, SolveState* st) {
+                       const Red& red, SolveState* st) {
     count_launches(1);
-    k_fcg_update<<<G, NT, 0, s>>>(N, e, r, p, q, part, st);
+    k_fcg_update<<<G, NT, 0, s>>>(N, e, r, p, q, red, st);
 }
 void launch_coarsen(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s, float* ct_c,
                     float* rho_c) {
     count_launches(1);
-    k_coarsen<<<nblk(C.g.N), NT, 0, s>>>(F, C.g, hx, hy, hz, ct_c, rho_c);
-}
-void launch_smooth(const Lev32& L, cudaStream_t s, float* x, const float* f, int colour, int zero_guess) {
-    const long long n = (long long)((L.g.nx + 1) >> 1) * L.g.ny * L.g.nz;
-    count_launches(1);
-    k_smooth<<<nblk(n), NT, 0, s>>>(L, x, f, colour, zero_guess);
+    k_coarsen<<<cell_grid(C.g), dim3(32, 8), 0, s>>>(F, C.g, hx, hy, hz, ct_c, rho_c);
 }
 void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s,
                            const float* x, const float* f, float* fc) {
     count_launches(1);
-    k_resid_restrict<<<nblk(C.g.N), NT, 0, s>>>(F, C.g, hx, hy, hz, x, f, fc);
+    k_resid_restrict<<<cell_grid(C.g), dim3(32, 8), 0, s>>>(F, C.g, hx, hy, hz, x, f, fc);
 }
-void launch_prolong_add(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s, float* x,
-                        const float* xc) {
+
+// One red-black sweep xout = S(xin [+ P ec]); first = colour updated first.
+void launch_rbgs(const Lev32& L, cudaStream_t s, const float* xin, const float* ec, const Lev32* C, int hx, int hy,
+                 int hz, const float* f, float* xout, int first, int zero, int prolong) {
+    const Geo& g = L.g;
+    const Geo Cg = C ? C->g : g;
     count_launches(1);
-    k_prolong_add<<<nblk(F.g.N), NT, 0, s>>>(F.g, C.g, hx, hy, hz, x, xc);
+    if (g.ny > 1) {
+        constexpr int BX = 32, TY = 8;
+        const int tiles = hdiv(g.nx, 2 * BX) * hdiv(g.ny, TY);
+        int KZ = 16;
+        while (KZ > 4 && (long long)tiles * hdiv(g.nz, KZ) < 1216) KZ /= 2;
+        const dim3 grd(hdiv(g.nx, 2 * BX), hdiv(g.ny, TY), hdiv(g.nz, KZ)), blk(BX, TY);
+#define LM_RB(F, Z, P) k_rbgs<BX, TY, true, F, Z, P><<<grd, blk, 0, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout, KZ)
+        if (zero) { if (first) LM_RB(1, true, false); else LM_RB(0, true, false); }
+        else if (prolong) { if (first) LM_RB(1, false, true); else LM_RB(0, false, true); }
+        else { if (first) LM_RB(1, false, false); else LM_RB(0, false, false); }
+#undef LM_RB
+    } else {
+        constexpr int BX = 128, TY = 1;
+        const int tiles = hdiv(g.nx, 2 * BX);
+        int KZ = 32;
+        while (KZ > 4 && (long long)tiles * hdiv(g.nz, KZ) < 1216) KZ /= 2;
+        const dim3 grd(hdiv(g.nx, 2 * BX), hdiv(g.nz, KZ), 1), blk(BX, TY);
+#define LM_RB(F, Z, P) k_rbgs<BX, TY, false, F, Z, P><<<grd, blk, 0, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout, KZ)
+        if (zero) { if (first) LM_RB(1, true, false); else LM_RB(0, true, false); }
+        else if (prolong) { if (first) LM_RB(1, false, true); else LM_RB(0, false, true); }
+        else { if (first) LM_RB(1, false, false); else LM_RB(0, false, false); }
+#undef LM_RB
+    }
 }
 void launch_coarse_inverse(const Lev32& L, cudaStream_t s, float* ainv) {
     count_launches(1);

@@ -17,7 +17,7 @@ namespace lm {
 __global__ void __launch_bounds__(NT) k_assemble(Geo g, const double* __restrict__ a_in,
                                                  const double* __restrict__ rho_new,
                                                  const double* __restrict__ cs2, double dt, int raw,
-                                                 double hx, double hy, double hz, Op64Out out,
+                                                 double c2x, double c2y, double c2z, Op64Out out,
                                                  int* __restrict__ bad) {
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
@@ -35,23 +35,32 @@ __global__ void __launch_bounds__(NT) k_assemble(Geo g, const double* __restrict
         if (!ok) atomicOr(bad, 1);
         int i, j, k;
         cell_coords(idx, g, i, j, k);
-        // kappa_f = 2/(rho_L + rho_R) (Eq. kappapoiss, harmonic mean), g_f = kappa_f / h^2
-        Nbr n = nbr_x(idx, i, g);
-        const double gxm = face_minus(i, g.nx, g.bcx) ? (2.0 / (rn + rho_new[n.im])) / (hx * hx) : 0.0;
-        const double gxp = face_plus(i, g.nx, g.bcx) ? (2.0 / (rn + rho_new[n.ip])) / (hx * hx) : 0.0;
-        n = nbr_y(idx, j, g);
-        const double gym = face_minus(j, g.ny, g.bcy) ? (2.0 / (rn + rho_new[n.im])) / (hy * hy) : 0.0;
-        const double gyp = face_plus(j, g.ny, g.bcy) ? (2.0 / (rn + rho_new[n.ip])) / (hy * hy) : 0.0;
-        n = nbr_z(idx, k, g);
-        const double gzm = face_minus(k, g.nz, g.bcz) ? (2.0 / (rn + rho_new[n.im])) / (hz * hz) : 0.0;
-        const double gzp = face_plus(k, g.nz, g.bcz) ? (2.0 / (rn + rho_new[n.ip])) / (hz * hz) : 0.0;
+        // g_f = kappa_f / h^2 with kappa_f = 2/(rho_L + rho_R) (Eq. kappapoiss, harmonic
+        // mean), evaluated as (2/h^2)/(rho_L + rho_R): one float64 division per face
+        const double gxm = face_minus(i, g.nx, g.bcx) ? c2x / (rn + rho_new[nbr_x(idx, i, g).im]) : 0.0;
+        const double gym = face_minus(j, g.ny, g.bcy) ? c2y / (rn + rho_new[nbr_y(idx, j, g).im]) : 0.0;
+        const double gzm = face_minus(k, g.nz, g.bcz) ? c2z / (rn + rho_new[nbr_z(idx, k, g).im]) : 0.0;
         out.ct[idx] = c;
         out.gx[idx] = gxm;
         out.gy[idx] = gym;
         out.gz[idx] = gzm;
-        out.dinv[idx] = 1.0 / (((((c + gxm) + gxp) + gym) + gyp) + gzm + gzp);
         out.ct32[idx] = (float)c;
         out.rho32[idx] = (float)rn;
+    }
+}
+
+// Inverse Jacobi diagonal 1/(c~ + sum of the cell's face conductances), from
+// the assembled faces (the plus face of a cell is its plus-neighbour's minus face).
+__global__ void __launch_bounds__(NT) k_jacobi_diag(Geo g, const double* __restrict__ ct,
+                                                    const double* __restrict__ gx, const double* __restrict__ gy,
+                                                    const double* __restrict__ gz, double* __restrict__ dinv) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
+        int i, j, k;
+        cell_coords(idx, g, i, j, k);
+        const double d = ct[idx] + gx[idx] + gx[nbr_x(idx, i, g).ip] + gy[idx] + gy[nbr_y(idx, j, g).ip] +
+                         gz[idx] + gz[nbr_z(idx, k, g).ip];
+        dinv[idx] = 1.0 / d;
     }
 }
 
@@ -395,7 +404,12 @@ __global__ void __launch_bounds__(NT) k_set_fnorm(const double* part, int slot, 
 void launch_assemble(const Geo& g, int G, cudaStream_t s, const double* a_in, const double* rho_new,
                      const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, int* bad) {
     count_launches(1);
-    k_assemble<<<G, NT, 0, s>>>(g, a_in, rho_new, cs2, dt, raw, h[0], h[1], h[2], out, bad);
+    k_assemble<<<G, NT, 0, s>>>(g, a_in, rho_new, cs2, dt, raw, 2.0 / (h[0] * h[0]), 2.0 / (h[1] * h[1]),
+                                2.0 / (h[2] * h[2]), out, bad);
+}
+void launch_jacobi_diag(const Geo& g, int G, cudaStream_t s, const Op64& op, double* dinv) {
+    count_launches(1);
+    k_jacobi_diag<<<G, NT, 0, s>>>(g, op.ct, op.gx, op.gy, op.gz, dinv);
 }
 void launch_apply64(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* x, double* y,
                     double* part) {

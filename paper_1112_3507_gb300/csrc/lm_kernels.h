@@ -54,6 +54,7 @@ struct Lev32 {
 // fp64
 void launch_assemble(const Geo& g, int G, cudaStream_t s, const double* a_in, const double* rho_new,
                      const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, int* bad);
+void launch_jacobi_diag(const Geo& g, int G, cudaStream_t s, const Op64& op, double* dinv);
 void launch_apply64(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* x, double* y,
                     double* part);
 void launch_pcg_init(const PcgArgs& a, int G, cudaStream_t s, int use_x0);
@@ -72,24 +73,22 @@ void launch_fcg64_iter_b(const Geo& g, int G, cudaStream_t s, const Op64& op, do
 void launch_to32(int N, int G, cudaStream_t s, const double* r, float* r32);
 void launch_set_fnorm(const double* part, int slot, int G, cudaStream_t s, SolveState* st);
 
-// fp32 operator and flexible CG
-void launch_apply32(const Lev32& L, int G, cudaStream_t s, const float* x, float* y, double* part);
-void launch_fcg_beta_p(int N, int G, cudaStream_t s, const float* z, float* p, const float* q_old,
-                       double* part, int first);
-void launch_fcg_apply(const Lev32& L, int G, cudaStream_t s, const float* p, float* q, const float* r,
-                      double* part);
+// fp32 operator and flexible CG (reductions land in red.scal[slot]; slot < 0: none)
+void launch_apply32(const Lev32& L, cudaStream_t s, const float* x, float* y, const float* r, const Red& red,
+                    int slot_xy, int slot_xr);
+void launch_dot32(int N, int G, cudaStream_t s, const float* a, const float* b, const Red& red, int slot,
+                  SolveState* fnorm_st);
+void launch_fcg_beta_p(int N, int G, cudaStream_t s, const float* z, float* p, const double* scal, int first);
 void launch_fcg_update(int N, int G, cudaStream_t s, float* e, float* r, const float* p, const float* q,
-                       double* part, SolveState* st);
-void launch_dot32(int N, int G, cudaStream_t s, const float* a, const float* b, double* part, int slot);
+                       const Red& red, SolveState* st);
 
 // multigrid
 void launch_coarsen(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s, float* ct_c,
                     float* rho_c);
-void launch_smooth(const Lev32& L, cudaStream_t s, float* x, const float* f, int colour, int zero_guess);
+void launch_rbgs(const Lev32& L, cudaStream_t s, const float* xin, const float* ec, const Lev32* C, int hx, int hy,
+                 int hz, const float* f, float* xout, int first, int zero, int prolong);
 void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s,
                            const float* x, const float* f, float* fc);
-void launch_prolong_add(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s, float* x,
-                        const float* xc);
 void launch_coarse_inverse(const Lev32& L, cudaStream_t s, float* ainv);
 void launch_coarse_solve(int n, cudaStream_t s, const float* ainv, const float* f, float* x);
 
