@@ -18,13 +18,15 @@ namespace lm {
 __device__ __forceinline__ float face32(float ra, float rb, float c2) { return __fdividef(c2, ra + rb); }
 
 // ---- y = A x, marching along z --------------------------------------------
-// 3D: block (32, 8) covers an x-y tile, blockIdx.z a chunk of KZ_APPLY planes.
-// 2D (ny = 1): block (32, 8) covers 32 columns x 8 chunks of KZ_APPLY rows.
-constexpr int KZ_APPLY = 16;
+// 3D: block (32, 8) covers an x-y tile, blockIdx.z a chunk of kz planes.
+// 2D (ny = 1): block (32, 8) covers 32 columns x 8 chunks of kz rows.
+// kz is the smallest that keeps the launch within 4096 blocks (the
+// last-block reduction sums one partial per block).
 
 template <bool HAS_Y, bool DOT_XY, bool DOT_XR>
 __global__ void __launch_bounds__(256) k_apply32z(Lev32 L, const float* __restrict__ x, float* __restrict__ y,
-                                                  const float* __restrict__ r, Red red, int slot_xy, int slot_xr) {
+                                                  const float* __restrict__ r, Red red, int slot_xy, int slot_xr,
+                                                  int KZ_APPLY) {
     __shared__ double sm[64];
     const Geo& g = L.g;
     const int i = blockIdx.x * 32 + threadIdx.x;
@@ -248,8 +250,9 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Lev32 F, Geo C, int hx, 
 //          correction, fused into the post-smoothing sweep).
 template <int BX, int TY, bool HAS_Y, int FIRST, bool ZERO, bool PROLONG>
 __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, const float* __restrict__ xin,
-                                                  const float* __restrict__ ec, Geo C, int hx, int hy, int hz,
-                                                  const float* __restrict__ f, float* __restrict__ xout, int KZ) {
+                                                                   const float* __restrict__ ec, Geo C, int hx,
+                                                                   int hy, int hz, const float* __restrict__ f,
+                                                                   float* __restrict__ xout, int KZ) {
     constexpr int TXC = 2 * BX;
     constexpr int HY = HAS_Y ? 1 : 0;
     constexpr int EX2 = TXC + 4, EY2 = TY + 4 * HY;    // tile + 2-cell halo (R2)
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, con
         while (c >= n) c -= n;
         return c;
     };
-    auto ring = [](int p, int m) { return (p + 6) % m; };   // plane p >= -3 -> slot
+    auto ring = [](int p, int m) { return (p + 6) % m; };   // plane p >= -4 -> slot
     auto flags = [&](int gi, int gj) {
         return (face_minus(gi, g.nx, g.bcx) ? 1 : 0) | (face_plus(gi, g.nx, g.bcx) ? 2 : 0) |
                (HAS_Y && face_minus(gj, g.ny, g.bcy) ? 4 : 0) | (HAS_Y && face_plus(gj, g.ny, g.bcy) ? 8 : 0);
@@ -301,13 +304,13 @@ __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, con
             }
         }
     }
-    // update cells: c = 0, 1 the thread's own x-pair; c = 2, 3 its halo task
-    // (a pair on the top/bottom R1 row, or one cell of the left/right column)
-    // A tile may be wider than a small grid: an own cell past the end of a
-    // periodic axis is the wrapped copy of a cell of this row, and its
-    // first-colour value is what the row's last cell sees as its neighbour,
-    // so it is computed (from wrapped coordinates) but never written out.
-    int ex1c[4], ey1c[4], offc[4], parc[4], flc[4];
+    // Update cells: c = 0, 1 the thread's own x-pair (a tile wider than a
+    // small grid holds wrapped copies of periodic cells: computed, not
+    // written); c = 2, 3 its halo task (a pair of the top/bottom R1 row or one
+    // cell of the left/right R1 column), spread round-robin over the warps.
+    // Per cell: R1 index, R2 index, in-plane offset (-1: outside a wall),
+    // parity, face flags.
+    int i1c[4], i2c[4], offc[4], parc[4], flc[4];
     bool outc[2];
     {
         const int ti = threadIdx.x, tj = HAS_Y ? threadIdx.y : 0;
@@ -317,37 +320,42 @@ __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, con
             const int ui = i0 + 2 * ti + c, uj = j0 + tj;
             const int gi = wrap(ui, g.nx, g.bcx, oki);
             const int gj = HAS_Y ? wrap(uj, g.ny, g.bcy, okj) : 0;
-            ex1c[c] = 2 * ti + 1 + c;
-            ey1c[c] = tj + HY;
+            const int ex1 = 2 * ti + 1 + c, ey1 = tj + HY;
+            i1c[c] = ey1 * EX1 + ex1;
+            i2c[c] = (ey1 + HY) * EX2 + ex1 + 1;
             const bool ok = oki && okj;
             offc[c] = ok ? gi + g.nx * gj : -1;
             parc[c] = (gi + gj) & 1;
             flc[c] = ok ? flags(gi, gj) : 0;
             outc[c] = ok && ui < g.nx && uj < g.ny;
         }
+        // task number: warps take turns, so every warp carries a share
+        const int lane = tid & 31, warp = tid >> 5, nwarp = NTH / 32;
+        const int t = lane * nwarp + warp;
         int hxp[2] = {0, 0}, hyp = 0, nh = 0;
-        if (tid < NHP) {
-            const int m = tid % (EX1 / 2);
-            hyp = tid < EX1 / 2 ? 0 : EY1 - 1;
+        if (t < NHP) {
+            const int m = t % (EX1 / 2);
+            hyp = t < EX1 / 2 ? 0 : EY1 - 1;
             hxp[0] = 2 * m;
             hxp[1] = 2 * m + 1;
             nh = 2;
-        } else if (tid < NH) {
-            const int sidx = tid - NHP;
+        } else if (t < NH) {
+            const int sidx = t - NHP;
             hxp[0] = sidx < TY ? 0 : EX1 - 1;
             hyp = (sidx % TY) + HY;
             nh = 1;
         }
 #pragma unroll
         for (int c = 2; c < 4; ++c) {
-            ex1c[c] = hxp[c - 2];
-            ey1c[c] = hyp;
+            const int ex1 = hxp[c - 2];
+            i1c[c] = hyp * EX1 + ex1;
+            i2c[c] = (hyp + HY) * EX2 + ex1 + 1;
             offc[c] = -1;
             parc[c] = 0;
             flc[c] = 0;
             if (c - 2 < nh) {
                 bool oki, okj = true;
-                const int gi = wrap(i0 - 1 + hxp[c - 2], g.nx, g.bcx, oki);
+                const int gi = wrap(i0 - 1 + ex1, g.nx, g.bcx, oki);
                 const int gj = HAS_Y ? wrap(j0 - 1 + hyp, g.ny, g.bcy, okj) : 0;
                 if (oki && okj) {
                     offc[c] = gi + g.nx * gj;
@@ -360,48 +368,33 @@ __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, con
 
     // Gauss-Seidel value x = (f + sum g v) / (c~ + sum g) of an update cell;
     // neighbour values v from the plane rows Vm/V0/Vp (row width exv) at vi,
-    // rho from the R2 planes Rm/R0/Rp at ri.
+    // rho from the R2 planes Rm/R0/Rp at ri.  Face weights first, then the
+    // sums, so the reciprocals of the six faces are independent.
     auto gs = [&](int fl, bool zm, bool zp, float fv, float cv, const float* Vm, const float* V0, const float* Vp,
                   int exv, int vi, const float* Rm, const float* R0, const float* Rp, int ri) -> float {
         const float rc = R0[ri];
-        float d = cv, num = fv;
-        if (fl & 1) {
-            const float w = face32(rc, R0[ri - 1], L.c2x);
-            d += w;
-            num += w * V0[vi - 1];
-        }
-        if (fl & 2) {
-            const float w = face32(rc, R0[ri + 1], L.c2x);
-            d += w;
-            num += w * V0[vi + 1];
-        }
+        const float wxm = (fl & 1) ? face32(rc, R0[ri - 1], L.c2x) : 0.f;
+        const float wxp = (fl & 2) ? face32(rc, R0[ri + 1], L.c2x) : 0.f;
+        const float wym = (HAS_Y && (fl & 4)) ? face32(rc, R0[ri - EX2], L.c2y) : 0.f;
+        const float wyp = (HAS_Y && (fl & 8)) ? face32(rc, R0[ri + EX2], L.c2y) : 0.f;
+        const float wzm = zm ? face32(rc, Rm[ri], L.c2z) : 0.f;
+        const float wzp = zp ? face32(rc, Rp[ri], L.c2z) : 0.f;
+        const float d = cv + ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
+        float num = fv;
+        num = fmaf(wxm, V0[vi - 1], num);
+        num = fmaf(wxp, V0[vi + 1], num);
         if (HAS_Y) {
-            if (fl & 4) {
-                const float w = face32(rc, R0[ri - EX2], L.c2y);
-                d += w;
-                num += w * V0[vi - exv];
-            }
-            if (fl & 8) {
-                const float w = face32(rc, R0[ri + EX2], L.c2y);
-                d += w;
-                num += w * V0[vi + exv];
-            }
+            num = fmaf(wym, V0[vi - exv], num);
+            num = fmaf(wyp, V0[vi + exv], num);
         }
-        if (zm) {
-            const float w = face32(rc, Rm[ri], L.c2z);
-            d += w;
-            num += w * Vm[vi];
-        }
-        if (zp) {
-            const float w = face32(rc, Rp[ri], L.c2z);
-            d += w;
-            num += w * Vp[vi];
-        }
+        num = fmaf(wzm, Vm[vi], num);
+        num = fmaf(wzp, Vp[vi], num);
         return __fdividef(num, d);
     };
 
-    // register staging: x, rho of plane p + 1 on R2 and f, c~ of the update cells on plane p
-    float px[N2], pr[N2], pf[4], pc[4];
+    // register staging: x, rho of plane p + 1 on R2 and f, c~ of the update
+    // cells on plane p (own pair; halo task: the cell first-coloured on p)
+    float px[N2], pr[N2], pf[3], pc[3];
     auto fetch = [&](int p) {
         bool okp, okq;
         const int gp = wrap(p + 1, g.nz, g.bcz, okp);
@@ -420,11 +413,16 @@ __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, con
             px[u] = xv;
             pr[u] = rv;
         }
+        // colour parity from the unwrapped plane index (a wrapped periodic
+        // axis has an even count; a plane past a Neumann wall computes nothing)
+        const int hsel = ((parc[2] + p) & 1) == FIRST ? 2 : 3;
+        const int hoff = hsel == 2 ? offc[2] : offc[3];
+        const int offs[3] = {offc[0], offc[1], hoff};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < 3; ++c) {
             float fv = 0.f, cv = 1.f;
-            if (okq && offc[c] >= 0) {
-                const int idx = offc[c] + sz * gq;
+            if (okq && offs[c] >= 0) {
+                const int idx = offs[c] + sz * gq;
                 fv = f[idx];
                 cv = L.ct[idx];
             }
@@ -432,9 +430,9 @@ __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, con
             pc[c] = cv;
         }
     };
-    auto store_xr = [&](int p) {
-        float* xo = XO[ring(p + 1, 3)];
-        float* rh = RH[ring(p + 1, 5)];
+    auto store_xr = [&](int sx, int sr) {
+        float* xo = XO[sx];
+        float* rh = RH[sr];
 #pragma unroll
         for (int u = 0; u < N2; ++u) {
             const int e = tid + u * NTH;
@@ -445,78 +443,97 @@ __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, con
         }
     };
 
-    float fcur[4], ccur[4], fprev[2], cprev[2];
+    // gs() reads neighbour values even where a face weight is 0 (a wall):
+    // first-colour slots that are never written must hold finite values
+    for (int e = tid; e < 3 * EY1 * EX1; e += NTH) (&F1[0][0])[e] = 0.f;
+    float fcur[3], ccur[3], fprev[2], cprev[2];
     fetch(k0 - 3);
-    store_xr(k0 - 3);              // plane k0 - 2
+    store_xr(ring(k0 - 2, 3), ring(k0 - 2, 5));
     fetch(k0 - 2);
-    store_xr(k0 - 2);              // plane k0 - 1
+    store_xr(ring(k0 - 1, 3), ring(k0 - 1, 5));
     fetch(k0 - 1);                 // x, rho of plane k0; f, c~ of plane k0 - 1
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 3; ++c) {
         fcur[c] = 0.f;
         ccur[c] = 1.f;
     }
+    // slots for p = k0 - 1: XO/F1 of planes p-2 .. p+1 (3-ring: p-2 and p+1
+    // share a slot), RH of planes p-3 .. p+1
+    int x2 = ring(k0 - 3, 3), x1 = ring(k0 - 2, 3), x0 = ring(k0 - 1, 3), xp = ring(k0, 3);
+    int r3 = ring(k0 - 4, 5), r2 = ring(k0 - 3, 5), r1 = ring(k0 - 2, 5), r0 = ring(k0 - 1, 5),
+        rp = ring(k0, 5);
+    bool okp;
+    int gp = wrap(k0 - 1, g.nz, g.bcz, okp);
     for (int p = k0 - 1; p <= k1; ++p) {
-        store_xr(p);
+        store_xr(xp, rp);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             fprev[c] = fcur[c];
             cprev[c] = ccur[c];
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < 3; ++c) {
             fcur[c] = pf[c];
             ccur[c] = pc[c];
         }
         if (p < k1) fetch(p + 1);
         __syncthreads();
-        // first colour on plane p: the thread's own first-colour cell and its halo task
-        bool okp;
-        const int gp = wrap(p, g.nz, g.bcz, okp);
+        // first colour on plane p: own cell A (first-coloured on p) and the halo task's cell
+        const int a = ((parc[0] + p) & 1) == FIRST ? 0 : 1;
+        const int i1a = a ? i1c[1] : i1c[0], i2a = a ? i2c[1] : i2c[0];
+        const int fla = a ? flc[1] : flc[0];
+        const int ha = ((parc[2] + p) & 1) == FIRST ? 2 : 3;
+        const int i1h = ha == 2 ? i1c[2] : i1c[3], i2h = ha == 2 ? i2c[2] : i2c[3];
+        const int flh = ha == 2 ? flc[2] : flc[3];
+        const bool hval = (ha == 2 ? offc[2] : offc[3]) >= 0 && (((ha == 2 ? parc[2] : parc[3]) + p) & 1) == FIRST;
         {
-            const float* Xm = XO[ring(p - 1, 3)];
-            const float* X0 = XO[ring(p, 3)];
-            const float* Xp = XO[ring(p + 1, 3)];
-            const float* Rm = RH[ring(p - 1, 5)];
-            const float* R0 = RH[ring(p, 5)];
-            const float* Rp = RH[ring(p + 1, 5)];
-            float* f1 = F1[ring(p, 3)];
+            const float* Xm = XO[x1];
+            const float* X0 = XO[x0];
+            const float* Xp = XO[xp];
+            const float* Rm = RH[r1];
+            const float* R0 = RH[r0];
+            const float* Rp = RH[rp];
+            float* f1 = F1[x0];
             const bool zm = face_minus(gp, g.nz, g.bcz), zp = face_plus(gp, g.nz, g.bcz);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (offc[c] >= 0 && ((parc[c] + gp) & 1) == FIRST) {
-                    const int vi = (ey1c[c] + HY) * EX2 + ex1c[c] + 1;
-                    float v = 0.f;
-                    if (okp) v = gs(flc[c], zm, zp, fcur[c], ccur[c], Xm, X0, Xp, EX2, vi, Rm, R0, Rp, vi);
-                    f1[ey1c[c] * EX1 + ex1c[c]] = v;
-                }
-            }
+            const float va = gs(fla, zm, zp, a ? fcur[1] : fcur[0], a ? ccur[1] : ccur[0], Xm, X0, Xp, EX2, i2a,
+                                Rm, R0, Rp, i2a);
+            const float vh = gs(flh, zm, zp, fcur[2], ccur[2], Xm, X0, Xp, EX2, i2h, Rm, R0, Rp, i2h);
+            if ((a ? offc[1] : offc[0]) >= 0) f1[i1a] = okp ? va : 0.f;
+            if (hval) f1[i1h] = okp ? vh : 0.f;
         }
         __syncthreads();
-        // second colour on plane q = p - 1, from the new first colour
+        // second colour on plane q = p - 1: own cell A (second-coloured on q);
+        // own cell B is first-coloured on q and was computed last plane
         const int q = p - 1;
         if (q >= k0) {
-            const float* Fm = F1[ring(q - 1, 3)];
-            const float* F0 = F1[ring(q, 3)];
-            const float* Fp = F1[ring(q + 1, 3)];
-            const float* Rm = RH[ring(q - 1, 5)];
-            const float* R0 = RH[ring(q, 5)];
-            const float* Rp = RH[ring(q + 1, 5)];
+            const float* Fm = F1[x2];
+            const float* F0 = F1[x1];
+            const float* Fp = F1[x0];
             const bool zm = face_minus(q, g.nz, g.bcz), zp = face_plus(q, g.nz, g.bcz);
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                if (!outc[c]) continue;
-                float v;
-                if (((parc[c] + q) & 1) == FIRST) {
-                    v = F0[ey1c[c] * EX1 + ex1c[c]];
-                } else {
-                    const int vi = ey1c[c] * EX1 + ex1c[c];
-                    const int ri = (ey1c[c] + HY) * EX2 + ex1c[c] + 1;
-                    v = gs(flc[c], zm, zp, fprev[c], cprev[c], Fm, F0, Fp, EX1, vi, Rm, R0, Rp, ri);
-                }
-                xout[offc[c] + sz * q] = v;
-            }
+            const int b = 1 - a;
+            const int i1b = b ? i1c[1] : i1c[0];
+            const float va = gs(fla, zm, zp, a ? fprev[1] : fprev[0], a ? cprev[1] : cprev[0], Fm, F0, Fp, EX1, i1a,
+                                RH[r2], RH[r1], RH[r0], i2a);
+            const float vb = F0[i1b];
+            if (outc[0]) xout[offc[0] + sz * q] = a ? vb : va;
+            if (outc[1]) xout[offc[1] + sz * q] = a ? va : vb;
         }
+        // rotate to plane p + 1 (in the 3-ring, p + 2 takes the slot of p - 1)
+        x2 = x1;
+        x1 = x0;
+        x0 = xp;
+        xp = x2;
+        {
+            const int t5 = r3;
+            r3 = r2;
+            r2 = r1;
+            r1 = r0;
+            r0 = rp;
+            rp = t5;
+        }
+        ++gp;
+        if (gp == g.nz) gp = 0;
+        okp = (p + 1 >= 0 && p + 1 < g.nz) || g.bcz == LM_BC_PERIODIC;
     }
 }
 
@@ -595,11 +612,16 @@ void launch_apply32(const Lev32& L, cudaStream_t s, const float* x, float* y, co
     const Geo& g = L.g;
     const dim3 blk(32, 8);
     const bool y3 = g.ny > 1;
-    const dim3 grd = y3 ? dim3(hdiv(g.nx, 32), hdiv(g.ny, 8), hdiv(g.nz, KZ_APPLY))
-                        : dim3(hdiv(g.nx, 32), hdiv(hdiv(g.nz, KZ_APPLY), 8), 1);
+    int kz = 1;
+    auto grid_for = [&](int k) {
+        return y3 ? dim3(hdiv(g.nx, 32), hdiv(g.ny, 8), hdiv(g.nz, k))
+                  : dim3(hdiv(g.nx, 32), hdiv(hdiv(g.nz, k), 8), 1);
+    };
+    while ((long long)grid_for(kz).x * grid_for(kz).y * grid_for(kz).z > 4096) kz *= 2;
+    const dim3 grd = grid_for(kz);
     count_launches(1);
     const bool dxy = slot_xy >= 0, dxr = slot_xr >= 0;
-#define LM_APPLY(Y, A, B) k_apply32z<Y, A, B><<<grd, blk, 0, s>>>(L, x, y, r, red, slot_xy, slot_xr)
+#define LM_APPLY(Y, A, B) k_apply32z<Y, A, B><<<grd, blk, 0, s>>>(L, x, y, r, red, slot_xy, slot_xr, kz)
     if (y3) {
         if (dxy && dxr) LM_APPLY(true, true, true);
         else if (dxy) LM_APPLY(true, true, false);
