@@ -209,6 +209,32 @@ int  lm_mg_vcycle(lm_grid* g, const float* r, float* z, int nu1, int nu2, void* 
  * (n_out[3]); LM_ERR_INVALID_ARG past the coarsest level. */
 int  lm_mg_level_shape(lm_grid* g, int level, int64_t n_out[3], int* num_levels);
 
+/* ---- batched solves ------------------------------------------------------ */
+
+/* Solve `count` independent 2D grids (distinct lm_grid handles, each with
+ * coefficients and rhs set) in the mixed-precision mode of LM_MIXED_MG_IR,
+ * all at once: every phase of the solve is one launch over the tiles of all
+ * grids, grids that have converged skip their tiles, and the launch sequence
+ * of one refinement step (opts->inner_max_iter inner iterations) is captured
+ * as a CUDA graph and replayed up to opts->max_outer times.  The sweep
+ * z-chunk of every level shape is chosen by the autotuner (see
+ * lm_autotune_set_cache).  The captured plan is cached per (grids,
+ * coefficient versions, inner_max_iter, use_x0) and reused by later calls.
+ * Requirements: 2D grids (ndim 2), nu1 = nu2 = 1, an exactly solved coarsest
+ * level (grids whose halvings reach <= 64 cells), even periodic extents.
+ * results[i] receives grid i's status, inner iterations (iters = vcycles),
+ * refinement steps and final float64 relative residual; `seconds` is the
+ * device time of the whole batch.  Returns LM_OK or the first failing
+ * grid's status; LM_ERR_INVALID_ARG / LM_ERR_STATE before any work. */
+int  lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* opts, lm_solve_result* results);
+
+/* Autotuner cache: a JSON object {"<gpu>|rbgs2d|<nx>x<nz>|bc<x><z>|f32": kz,
+ * ...} of the fastest sweep z-chunk per level shape, read on first use and
+ * rewritten when new shapes are timed.  Default path: $LM_AUTOTUNE_CACHE or
+ * $HOME/.cache/lowmach_autotune.json.  NULL or "" restores the default.
+ * Clears the in-memory table. */
+int  lm_autotune_set_cache(const char* path);
+
 /* Allocation-free float64 apply: y = A x and *dot_out = x^T A x, like
  * lm_apply(LM_PREC_FP64) with dot_out, but with no grid object and no device
  * allocation at all.  The paper has no counterpart: this serves callers that

@@ -17,68 +17,12 @@
 #include "../../include/lowmach.h"
 #include "lm_common.cuh"
 #include "lm_kernels.h"
+#include "lm_internal.h"
 
 using namespace lm;
 
 static std::atomic<long long> g_launches{0};
 void lm::count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
-
-namespace {
-
-constexpr int COARSE_MAX = 64;      // coarsest level solved exactly below this size
-constexpr int COARSE_SWEEPS = 32;   // (RB, BR) sweep pairs when it cannot be
-
-struct MgLevel {
-    Lev32 L;
-    double h[3];
-    int halved[3] = {0, 0, 0};      // axes halved to reach the next level
-    float* ct = nullptr;            // coefficients (owned on levels >= 1)
-    float* rho = nullptr;
-    float* xa = nullptr;            // sweep buffers (level 0: the grid's tmp_a/tmp_b)
-    float* xb = nullptr;
-    float* xo = nullptr;            // V-cycle output (levels >= 1; level 0 writes the caller's z)
-    float* f = nullptr;             // right-hand side (levels >= 1)
-    float* ainv = nullptr;          // dense inverse on a direct coarsest level
-};
-
-}  // namespace
-
-struct lm_grid {
-    int ndim = 0;
-    int n[3] = {1, 1, 1};
-    double h[3] = {1, 1, 1};
-    int bc[3] = {0, 0, 0};
-    int N = 0;
-    int device = 0;
-    int G = 1;          // blocks of the grid-stride streaming kernels
-    Geo geo{};
-
-    double *ct = nullptr, *gx = nullptr, *gy = nullptr, *gz = nullptr, *dinv = nullptr;
-    double *f = nullptr, *x = nullptr, *x0 = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
-    float *ct32 = nullptr, *rho32 = nullptr;
-    float *r32 = nullptr, *e32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
-    float *tmp_a = nullptr, *tmp_b = nullptr;   // level-0 sweep buffers
-    double* scal = nullptr;         // reduction results (float32 kernels)
-    unsigned int* ctr = nullptr;    // last-block arrival counter
-    double* stage = nullptr;        // 3N host-input staging (allocated on first use)
-    double* part = nullptr;         // NSLOT * MAX_PARTIALS
-    double* dscal = nullptr;        // device scalars for lm_apply dots
-    SolveState* st = nullptr;       // outer solve state
-    SolveState* st_in = nullptr;    // inner (float32) solve state
-    SolveState* st_host = nullptr;  // pinned mirror
-    double* hist_dev = nullptr;
-    int hist_cap = 0;
-    int* bad = nullptr;
-    int* bad_host = nullptr;
-    double* dscal_host = nullptr;
-
-    bool have_coefs = false, have_rhs = false, have_x0 = false;
-    bool have_dinv = false;         // inverse Jacobi diagonal (formed on the first Jacobi solve)
-    bool mg_built = false;
-    std::vector<MgLevel> mg;
-    std::vector<double> history;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
 
 #define CK(call)                                                        \
     do {                                                                \
@@ -160,6 +104,7 @@ bool mg_supported(const lm_grid* g) {
 // Multigrid hierarchy from the float32 coefficients (coarse c~, rho = child means).
 int build_mg(lm_grid* g, cudaStream_t s) {
     if (g->mg_built) return LM_OK;
+    ++g->version;
     free_mg(g);
     MgLevel L0;
     L0.L = make_lev(g->n, g->bc, g->h, g->ct32, g->rho32);
@@ -472,6 +417,7 @@ int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double
     CK(cudaStreamSynchronize(s));
     g->mg_built = false;
     g->have_dinv = false;
+    ++g->version;
     if (*g->bad_host) {
         g->have_coefs = false;
         return LM_ERR_NOT_POSITIVE;
@@ -481,6 +427,11 @@ int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double
 }
 
 }  // namespace
+
+int lm::grid_build_mg(lm_grid* g, cudaStream_t s) { return build_mg(g, s); }
+lm::Lev32 lm::make_level(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho) {
+    return make_lev(n, bc, h, ct, rho);
+}
 
 // ============================ C ABI =========================================
 
@@ -574,6 +525,7 @@ int lm_grid_create(int ndim, const int64_t n[3], const double h[3], const int bc
 void lm_grid_destroy(lm_grid* g) {
     if (!g) return;
     cudaDeviceSynchronize();
+    lm::batch_forget_grid(g);
     free_mg(g);
     void* bufs[] = {g->ct, g->gx, g->gy, g->gz, g->dinv, g->f, g->x, g->x0, g->r, g->p, g->q,
                     g->ct32, g->rho32, g->r32, g->e32, g->z32, g->p32, g->q32, g->tmp_a, g->tmp_b,

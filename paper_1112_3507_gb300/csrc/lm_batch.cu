@@ -1,0 +1,694 @@
+// Batched mixed-precision solve of many independent 2D grids of uneven size
+// (lm_batch_solve).
+//
+// Every phase of the solve -- the float64 residual, each level's fused
+// red-black sweeps, the fused residual + restriction, the exact coarsest
+// solves, the flexible-CG vector steps and the float64 correction -- is one
+// launch covering the tiles of every grid, through a task table (block b
+// works on task[b] = grid, level, tile).  Per-grid device flags make the
+// tiles of converged grids no-ops, so a fixed launch sequence serves grids
+// that converge at different iterations; that sequence is captured once as
+// a CUDA graph (one graph for the first residual, one per refinement step)
+// and replayed.  No block ever waits for another: ordering comes from the
+// kernel boundaries inside the graph.
+//
+// The sweep's z-chunk per level size is chosen by an autotuner that times
+// the candidates on the first grid of each size class and keeps the result
+// in a JSON cache file keyed by GPU name, level shape and boundary conditions.
+#include <cuda_runtime.h>
+#include <sys/stat.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lowmach.h"
+#include "lm_common.cuh"
+#include "lm_internal.h"
+#include "lm_kernels.h"
+#include "lm_tiles.cuh"
+
+namespace lm {
+
+// ---- device tables ------------------------------------------------------------
+
+struct BTask {
+    int g, l, bx, by, bz, lblk, nblk;
+};
+
+struct BLev {
+    Lev32 L;            // this level
+    Geo C;              // the next (coarser) level
+    int hx, hy, hz;     // halving to the next level
+    int kz;             // sweep z-chunk (autotuned)
+    float* xa;          // pre-smoothed iterate
+    float* xo;          // V-cycle output (level 0: the grid's z)
+    const float* f;     // right-hand side (level 0: the grid's r32)
+    float* fc;          // the next level's right-hand side
+    const float* ec;    // the next level's output (the coarse correction)
+    const float* ainv;  // dense inverse on the coarsest level
+};
+
+struct BGrid {
+    Geo geo;
+    Op64 op;
+    const double* f;
+    double* x;
+    float *r32, *e32, *z32, *p32, *q32;
+    SolveState* st;     // outer (refinement) state: done = converged or failed
+    SolveState* st_in;  // inner state: done = inner tolerance met
+    Red red;
+    int N;
+    int kz_apply;
+};
+
+// scal slots per grid: 0 p.q, 1 r.r, 2 p.r, 3 z.q_old, 4 r0.r0, 5 float64 r.r, 6 f.f
+
+__device__ __forceinline__ bool inner_off(const BGrid& G) { return G.st->done || G.st_in->done; }
+
+__global__ void __launch_bounds__(NT) kb_init_states(const BGrid* __restrict__ Gs, int count, double rtol,
+                                                     double inner_rtol) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= count) return;
+    SolveState s{};
+    s.rtol = rtol;
+    *Gs[g].st = s;
+    s.rtol = inner_rtol;
+    s.done = 1;
+    *Gs[g].st_in = s;
+}
+
+// r = f - A x in float64 (zero_x: x := 0, r = f), r32 = r; the grid's last
+// block sets ||f|| (first residual of a solve), rel = ||r||/||f||, counts a
+// refinement step (later residuals), and done when rel <= rtol.
+__global__ void __launch_bounds__(NT) kb_ir_residual(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
+                                                     int zero_x, int first) {
+    const BTask t = T[blockIdx.x];
+    const BGrid& G = Gs[t.g];
+    if (G.st->done) return;
+    __shared__ double sm[64];
+    double acc[2] = {0.0, 0.0};
+    const int stride = t.nblk * NT;
+    for (int idx = t.lblk * NT + threadIdx.x; idx < G.N; idx += stride) {
+        const double fi = G.f[idx];
+        const double ri = zero_x ? fi : fi - apply64_at(idx, G.geo, G.op, G.x);
+        G.r32[idx] = (float)ri;
+        acc[0] += ri * ri;
+        acc[1] += fi * fi;
+    }
+    if (zero_x)
+        for (int idx = t.lblk * NT + threadIdx.x; idx < G.N; idx += stride) G.x[idx] = 0.0;
+    const int sl[2] = {5, 6};
+    if (grid_reduce_n<2>(acc, G.red, sl, sm, t.lblk, t.nblk) && lin_tid() == 0) {
+        if (first) G.st->fnorm = sqrt(G.red.scal[6]);
+        const double fn = G.st->fnorm;
+        const double rel = fn > 0.0 ? sqrt(G.red.scal[5]) / fn : 0.0;
+        G.st->rel = rel;
+        if (!first) G.st->iters += 1;
+        if (!isfinite(rel)) {
+            G.st->status = LM_ERR_BREAKDOWN;
+            G.st->done = 1;
+        } else if (rel <= G.st->rtol) {
+            G.st->converged = 1;
+            G.st->done = 1;
+        }
+    }
+}
+
+// e = 0; ||r32|| of the inner problem; re-arm the inner state
+__global__ void __launch_bounds__(NT) kb_inner_init(const BTask* __restrict__ T, const BGrid* __restrict__ Gs) {
+    const BTask t = T[blockIdx.x];
+    const BGrid& G = Gs[t.g];
+    if (G.st->done) return;
+    __shared__ double sm[32];
+    const int stride = t.nblk * NT;
+    for (int idx = t.lblk * NT + threadIdx.x; idx < G.N; idx += stride) G.e32[idx] = 0.f;
+    const FF a = dot32_range(G.N, G.r32, G.r32, t.lblk, t.nblk);
+    double v[1] = {ff_value(a)};
+    const int sl[1] = {4};
+    if (grid_reduce_n<1>(v, G.red, sl, sm, t.lblk, t.nblk) && lin_tid() == 0) {
+        const double fn = sqrt(G.red.scal[4]);
+        G.st_in->fnorm = fn;
+        G.st_in->rel = 1.0;
+        G.st_in->status = 0;
+        G.st_in->done = fn > 0.0 ? 0 : 1;
+    }
+}
+
+__global__ void __launch_bounds__(128, 8) kb_rbgs_pre(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
+                                                      const BLev* __restrict__ Ls) {
+    const BTask t = T[blockIdx.x];
+    if (inner_off(Gs[t.g])) return;
+    const BLev& V = Ls[t.l];
+    rbgs_tile<128, 1, false, 0, true, false>(V.L, nullptr, nullptr, V.C, 0, 0, 0, V.f, V.xa, V.kz, t.bx, t.by, 0);
+}
+
+__global__ void __launch_bounds__(128, 8) kb_rbgs_post(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
+                                                       const BLev* __restrict__ Ls) {
+    const BTask t = T[blockIdx.x];
+    if (inner_off(Gs[t.g])) return;
+    const BLev& V = Ls[t.l];
+    rbgs_tile<128, 1, false, 1, false, true>(V.L, V.xa, V.ec, V.C, V.hx, V.hy, V.hz, V.f, V.xo, V.kz, t.bx, t.by,
+                                             0);
+}
+
+__global__ void __launch_bounds__(256) kb_resid_restrict(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
+                                                         const BLev* __restrict__ Ls) {
+    const BTask t = T[blockIdx.x];
+    if (inner_off(Gs[t.g])) return;
+    const BLev& V = Ls[t.l];
+    resid_restrict_tile(V.L, V.C, V.hx, V.hy, V.hz, V.xa, V.f, V.fc, t.bx, t.by, t.bz);
+}
+
+__global__ void kb_coarse(const BTask* __restrict__ T, const BGrid* __restrict__ Gs, const BLev* __restrict__ Ls) {
+    const BTask t = T[blockIdx.x];
+    if (inner_off(Gs[t.g])) return;
+    const BLev& V = Ls[t.l];
+    coarse_solve_block(V.L.g.N, V.ainv, V.f, V.xo);
+}
+
+__global__ void __launch_bounds__(NT) kb_dot_zq(const BTask* __restrict__ T, const BGrid* __restrict__ Gs) {
+    const BTask t = T[blockIdx.x];
+    const BGrid& G = Gs[t.g];
+    if (inner_off(G)) return;
+    __shared__ double sm[32];
+    const FF a = dot32_range(G.N, G.z32, G.q32, t.lblk, t.nblk);
+    double v[1] = {ff_value(a)};
+    const int sl[1] = {3};
+    grid_reduce_n<1>(v, G.red, sl, sm, t.lblk, t.nblk);
+}
+
+__global__ void __launch_bounds__(NT) kb_beta_p(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
+                                                int first) {
+    const BTask t = T[blockIdx.x];
+    const BGrid& G = Gs[t.g];
+    if (inner_off(G)) return;
+    fcg_beta_p_range(G.N, G.z32, G.p32, G.red.scal, first, t.lblk, t.nblk);
+}
+
+__global__ void __launch_bounds__(256) kb_apply(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
+                                                const BLev* __restrict__ Ls, const int* __restrict__ lev0) {
+    const BTask t = T[blockIdx.x];
+    const BGrid& G = Gs[t.g];
+    if (inner_off(G)) return;
+    __shared__ double sm[64];
+    FF axy{0.f, 0.f}, axr{0.f, 0.f};
+    apply32z_tile<false, true, true>(Ls[lev0[t.g]].L, G.p32, G.q32, G.r32, G.kz_apply, t.bx, t.by, 0, axy, axr);
+    double v[2] = {ff_value(axy), ff_value(axr)};
+    const int sl[2] = {0, 2};
+    grid_reduce_n<2>(v, G.red, sl, sm, t.lblk, t.nblk);
+}
+
+__global__ void __launch_bounds__(NT) kb_update(const BTask* __restrict__ T, const BGrid* __restrict__ Gs) {
+    const BTask t = T[blockIdx.x];
+    const BGrid& G = Gs[t.g];
+    if (inner_off(G)) return;
+    __shared__ double sm[32];
+    bool bad;
+    const FF rr = fcg_update_range(G.N, G.e32, G.r32, G.p32, G.q32, G.red.scal, bad, t.lblk, t.nblk);
+    double v[1] = {ff_value(rr)};
+    const int sl[1] = {1};
+    if (grid_reduce_n<1>(v, G.red, sl, sm, t.lblk, t.nblk) && lin_tid() == 0) {
+        const double rel = sqrt(G.red.scal[1]) / G.st_in->fnorm;
+        G.st_in->rel = rel;
+        G.st_in->iters += 1;
+        if (bad || !isfinite(rel)) {
+            G.st_in->status = LM_ERR_BREAKDOWN;
+            G.st_in->done = 1;
+        } else if (rel <= G.st_in->rtol) {
+            G.st_in->done = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NT) kb_ir_correct(const BTask* __restrict__ T, const BGrid* __restrict__ Gs) {
+    const BTask t = T[blockIdx.x];
+    const BGrid& G = Gs[t.g];
+    if (G.st->done) return;
+    const int stride = t.nblk * NT;
+    for (int idx = t.lblk * NT + threadIdx.x; idx < G.N; idx += stride) G.x[idx] += (double)G.e32[idx];
+}
+
+// out[g] = the outer state, out[count + g] = the inner state
+__global__ void kb_gather(const BGrid* __restrict__ Gs, int count, SolveState* __restrict__ out) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= count) return;
+    out[g] = *Gs[g].st;
+    out[count + g] = *Gs[g].st_in;
+}
+
+}  // namespace lm
+
+using namespace lm;
+
+#define BCK(call)                                                                                   \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            fprintf(stderr, "lowmach: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), __FILE__, \
+                    __LINE__);                                                                      \
+            return e_ == cudaErrorMemoryAllocation ? LM_ERR_OUT_OF_MEMORY : LM_ERR_CUDA;            \
+        }                                                                                           \
+    } while (0)
+
+namespace {
+
+// ---- autotuner --------------------------------------------------------------
+
+std::mutex g_tune_mu;
+std::string g_tune_path;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string default_cache_path() {
+    const char* env = getenv("LM_AUTOTUNE_CACHE");
+    if (env && *env) return env;
+    const char* home = getenv("HOME");
+    return std::string(home && *home ? home : "/tmp") + "/.cache/lowmach_autotune.json";
+}
+
+// The cache file is a flat JSON object {"key": value, ...}.
+void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    if (g_tune_path.empty()) g_tune_path = default_cache_path();
+    FILE* fp = fopen(g_tune_path.c_str(), "r");
+    if (!fp) return;
+    std::string txt;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof buf, fp)) > 0) txt.append(buf, n);
+    fclose(fp);
+    size_t i = 0;
+    while ((i = txt.find('"', i)) != std::string::npos) {
+        const size_t j = txt.find('"', i + 1);
+        if (j == std::string::npos) break;
+        const std::string key = txt.substr(i + 1, j - i - 1);
+        const size_t c = txt.find(':', j);
+        if (c == std::string::npos) break;
+        g_tune[key] = atoi(txt.c_str() + c + 1);
+        i = txt.find_first_of(",}", c);
+        if (i == std::string::npos) break;
+    }
+}
+
+void tune_save() {
+    const size_t slash = g_tune_path.find_last_of('/');
+    if (slash != std::string::npos && slash > 0) {
+        const std::string dir = g_tune_path.substr(0, slash);
+        for (size_t k = 1; k <= dir.size(); ++k)       // create the directory level by level
+            if (k == dir.size() || dir[k] == '/') ::mkdir(dir.substr(0, k).c_str(), 0755);
+    }
+    const std::string tmp = g_tune_path + ".tmp";
+    FILE* fp = fopen(tmp.c_str(), "w");
+    if (!fp) return;
+    fputs("{\n", fp);
+    size_t k = 0;
+    for (const auto& kv : g_tune) fprintf(fp, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++k < g_tune.size() ? "," : "");
+    fputs("}\n", fp);
+    fclose(fp);
+    rename(tmp.c_str(), g_tune_path.c_str());
+}
+
+std::string gpu_name() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    std::string s = prop.name;
+    for (char& c : s)
+        if (c == ' ' || c == '"') c = '_';
+    return s;
+}
+
+// z-chunk of the 2D sweep for one level shape: the fastest candidate, timed
+// on this level's own data (into its scratch buffer), remembered per shape.
+int tune_sweep_kz(const MgLevel& M, const float* fin, float* scratch, cudaStream_t s, bool* changed) {
+    char key[256];
+    snprintf(key, sizeof key, "%s|rbgs2d|%dx%d|bc%d%d|f32", gpu_name().c_str(), M.L.g.nx, M.L.g.nz, M.L.g.bcx,
+             M.L.g.bcz);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+    const int cands[] = {4, 8, 16, 32, 64};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 16;
+    float best_ms = 1e30f;
+    for (int kz : cands) {
+        if (kz > M.L.g.nz && kz != cands[0]) continue;
+        launch_rbgs_kz(M.L, s, nullptr, nullptr, nullptr, 0, 0, 0, fin, scratch, 0, 1, 0, kz);
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch_rbgs_kz(M.L, s, nullptr, nullptr, nullptr, 0, 0, 0, fin, scratch, 0, 1, 0, kz);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = kz;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_tune[key] = best;
+    *changed = true;
+    return best;
+}
+
+// ---- plan -----------------------------------------------------------------------
+
+struct Plan {
+    std::vector<lm_grid*> grids;
+    std::vector<unsigned> versions;
+    int inner_max = 0, first = 0, count = 0;
+    BGrid* dgrids = nullptr;
+    BLev* dlevs = nullptr;
+    int* dlev0 = nullptr;
+    BTask* dtasks = nullptr;
+    SolveState* dgather = nullptr;
+    SolveState* hgather = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t g_first = nullptr, g_step = nullptr;
+    int max_depth = 0;
+    long long n_first = 0, n_step = 0;   // kernels per graph launch
+
+    ~Plan() {
+        if (g_first) cudaGraphExecDestroy(g_first);
+        if (g_step) cudaGraphExecDestroy(g_step);
+        if (cap) cudaStreamDestroy(cap);
+        cudaFree(dgrids);
+        cudaFree(dlevs);
+        cudaFree(dlev0);
+        cudaFree(dtasks);
+        cudaFree(dgather);
+        cudaFreeHost(hgather);
+    }
+};
+
+std::mutex g_plan_mu;
+std::vector<Plan*> g_plans;
+
+struct TaskList {
+    int off = 0, n = 0;
+};
+
+int hdiv(int a, int b) { return (a + b - 1) / b; }
+
+int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStream_t s, Plan** out) {
+    Plan* P = new Plan();
+    P->grids.assign(grids, grids + count);
+    for (int i = 0; i < count; ++i) P->versions.push_back(grids[i]->version);
+    P->inner_max = o->inner_max_iter;
+    P->first = !o->use_x0;
+    P->count = count;
+
+    // autotune the sweep chunks of every level shape in the batch
+    bool changed = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load();
+        for (int i = 0; i < count; ++i)
+            for (size_t l = 0; l < grids[i]->mg.size(); ++l) {
+                const MgLevel& M = grids[i]->mg[l];
+                (void)tune_sweep_kz(M, l == 0 ? grids[i]->r32 : M.f, M.xa, s, &changed);
+            }
+        if (changed) tune_save();
+    }
+
+    std::vector<BGrid> hg(count);
+    std::vector<BLev> hl;
+    std::vector<int> lev0(count), nlev(count);
+    for (int i = 0; i < count; ++i) {
+        lm_grid* g = grids[i];
+        BGrid& G = hg[i];
+        G.geo = g->geo;
+        G.op = Op64{g->ct, g->gx, g->gy, g->gz, g->dinv};
+        G.f = g->f;
+        G.x = g->x;
+        G.r32 = g->r32;
+        G.e32 = g->e32;
+        G.z32 = g->z32;
+        G.p32 = g->p32;
+        G.q32 = g->q32;
+        G.st = g->st;
+        G.st_in = g->st_in;
+        G.red = Red{g->part, g->scal, g->ctr};
+        G.N = g->N;
+        int kz = 1;
+        while ((long long)hdiv(g->n[0], 32) * hdiv(hdiv(g->n[2], kz), 8) > 4096) kz *= 2;
+        G.kz_apply = kz;
+        lev0[i] = (int)hl.size();
+        nlev[i] = (int)g->mg.size();
+        P->max_depth = std::max(P->max_depth, nlev[i]);
+        for (size_t l = 0; l < g->mg.size(); ++l) {
+            const MgLevel& M = g->mg[l];
+            BLev V{};
+            V.L = M.L;
+            const bool last = l + 1 == g->mg.size();
+            if (!last) {
+                V.C = g->mg[l + 1].L.g;
+                V.hx = M.halved[0];
+                V.hy = M.halved[1];
+                V.hz = M.halved[2];
+                V.fc = g->mg[l + 1].f;
+                V.ec = g->mg[l + 1].xo;
+            } else {
+                V.C = M.L.g;
+            }
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                V.kz = tune_sweep_kz(M, l == 0 ? g->r32 : M.f, M.xa, s, &changed);
+            }
+            V.xa = M.xa;
+            V.xo = l == 0 ? g->z32 : M.xo;
+            V.f = l == 0 ? g->r32 : M.f;
+            V.ainv = M.ainv;
+            hl.push_back(V);
+        }
+    }
+
+    // task tables
+    std::vector<BTask> tasks;
+    auto one_d = [&]() {
+        TaskList L{(int)tasks.size(), 0};
+        for (int i = 0; i < count; ++i) {
+            const int nb = std::max(1, std::min(1024, hdiv(hg[i].N, NT * 8)));
+            for (int b = 0; b < nb; ++b) tasks.push_back(BTask{i, 0, 0, 0, 0, b, nb});
+        }
+        L.n = (int)tasks.size() - L.off;
+        return L;
+    };
+    const TaskList t1d = one_d();
+    TaskList tap{(int)tasks.size(), 0};
+    for (int i = 0; i < count; ++i) {
+        const Geo& g = hg[i].geo;
+        const int gx = hdiv(g.nx, 32), gy = hdiv(hdiv(g.nz, hg[i].kz_apply), 8);
+        for (int by = 0; by < gy; ++by)
+            for (int bx = 0; bx < gx; ++bx) tasks.push_back(BTask{i, lev0[i], bx, by, 0, bx + gx * by, gx * gy});
+    }
+    tap.n = (int)tasks.size() - tap.off;
+    std::vector<TaskList> tpre(P->max_depth), trr(P->max_depth);
+    for (int d = 0; d < P->max_depth; ++d) {
+        tpre[d].off = (int)tasks.size();
+        for (int i = 0; i < count; ++i) {
+            if (d >= nlev[i] - 1) continue;
+            const BLev& V = hl[lev0[i] + d];
+            const int gx = hdiv(V.L.g.nx, 256), gy = hdiv(V.L.g.nz, V.kz);
+            for (int by = 0; by < gy; ++by)
+                for (int bx = 0; bx < gx; ++bx) tasks.push_back(BTask{i, lev0[i] + d, bx, by, 0, 0, 0});
+        }
+        tpre[d].n = (int)tasks.size() - tpre[d].off;
+        trr[d].off = (int)tasks.size();
+        for (int i = 0; i < count; ++i) {
+            if (d >= nlev[i] - 1) continue;
+            const BLev& V = hl[lev0[i] + d];
+            const int gx = hdiv(V.C.nx, 32), gy = hdiv(V.C.nz, 8);
+            for (int by = 0; by < gy; ++by)
+                for (int bx = 0; bx < gx; ++bx) tasks.push_back(BTask{i, lev0[i] + d, bx, by, 0, 0, 0});
+        }
+        trr[d].n = (int)tasks.size() - trr[d].off;
+    }
+    TaskList tco{(int)tasks.size(), 0};
+    for (int i = 0; i < count; ++i) tasks.push_back(BTask{i, lev0[i] + nlev[i] - 1, 0, 0, 0, 0, 1});
+    tco.n = count;
+
+    BCK(cudaMalloc(&P->dgrids, sizeof(BGrid) * count));
+    BCK(cudaMalloc(&P->dlevs, sizeof(BLev) * hl.size()));
+    BCK(cudaMalloc(&P->dlev0, sizeof(int) * count));
+    BCK(cudaMalloc(&P->dtasks, sizeof(BTask) * tasks.size()));
+    BCK(cudaMalloc(&P->dgather, sizeof(SolveState) * 2 * count));
+    BCK(cudaMallocHost(&P->hgather, sizeof(SolveState) * 2 * count));
+    BCK(cudaMemcpy(P->dgrids, hg.data(), sizeof(BGrid) * count, cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(P->dlevs, hl.data(), sizeof(BLev) * hl.size(), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(P->dlev0, lev0.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(P->dtasks, tasks.data(), sizeof(BTask) * tasks.size(), cudaMemcpyHostToDevice));
+    BCK(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+
+    const BTask* T = P->dtasks;
+    const BGrid* Gs = P->dgrids;
+    const BLev* Ls = P->dlevs;
+    long long nk = 0;
+    auto launch_step = [&](cudaStream_t cs) {
+        // one refinement step: inner flexible CG (fixed length, converged grids idle), correction, residual
+        kb_inner_init<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs);
+        nk += 4;   // inner init, correction, residual, gather
+        for (int it = 0; it < P->inner_max; ++it) {
+            for (int d = 0; d < P->max_depth; ++d) nk += (tpre[d].n ? 2 : 0) + (trr[d].n ? 1 : 0);
+            nk += 1 + (it > 0) + 3;
+            for (int d = 0; d < P->max_depth; ++d) {
+                if (tpre[d].n) kb_rbgs_pre<<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls);
+                if (trr[d].n) kb_resid_restrict<<<trr[d].n, dim3(32, 8), 0, cs>>>(T + trr[d].off, Gs, Ls);
+            }
+            kb_coarse<<<tco.n, 64, 0, cs>>>(T + tco.off, Gs, Ls);
+            for (int d = P->max_depth - 1; d >= 0; --d)
+                if (tpre[d].n) kb_rbgs_post<<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls);
+            if (it > 0) kb_dot_zq<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs);
+            kb_beta_p<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs, it == 0);
+            kb_apply<<<tap.n, dim3(32, 8), 0, cs>>>(T + tap.off, Gs, Ls, P->dlev0);
+            kb_update<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs);
+        }
+        kb_ir_correct<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs);
+        kb_ir_residual<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs, 0, 0);
+        kb_gather<<<hdiv(count, 64), 64, 0, cs>>>(Gs, count, P->dgather);
+    };
+    auto launch_first = [&](cudaStream_t cs) {
+        nk += 2;
+        kb_ir_residual<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs, P->first, 1);
+        kb_gather<<<hdiv(count, 64), 64, 0, cs>>>(Gs, count, P->dgather);
+    };
+    for (int pass = 0; pass < 2; ++pass) {
+        cudaGraph_t graph = nullptr;
+        BCK(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
+        nk = 0;
+        if (pass == 0) launch_first(P->cap);
+        else launch_step(P->cap);
+        (pass == 0 ? P->n_first : P->n_step) = nk;
+        BCK(cudaStreamEndCapture(P->cap, &graph));
+        BCK(cudaGraphInstantiate(pass == 0 ? &P->g_first : &P->g_step, graph, 0));
+        cudaGraphDestroy(graph);
+    }
+    *out = P;
+    return LM_OK;
+}
+
+bool plan_matches(const Plan* P, lm_grid* const* grids, int count, const lm_solve_opts* o) {
+    if (P->count != count || P->inner_max != o->inner_max_iter || P->first != !o->use_x0) return false;
+    for (int i = 0; i < count; ++i)
+        if (P->grids[i] != grids[i] || P->versions[i] != grids[i]->version) return false;
+    return true;
+}
+
+void drop_plans_of(const lm_grid* g) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (size_t i = 0; i < g_plans.size();) {
+        if (std::find(g_plans[i]->grids.begin(), g_plans[i]->grids.end(), g) != g_plans[i]->grids.end()) {
+            delete g_plans[i];
+            g_plans.erase(g_plans.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+}  // namespace
+
+void lm::batch_forget_grid(const lm_grid* g) { drop_plans_of(g); }
+
+extern "C" {
+
+int lm_autotune_set_cache(const char* path) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+    g_tune_loaded = false;
+    g_tune_path = path && *path ? path : default_cache_path();
+    return LM_OK;
+}
+
+int lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* o, lm_solve_result* results) {
+    if (!grids || count < 1 || !o || !results) return LM_ERR_INVALID_ARG;
+    if (!(o->rtol > 0.0) || o->inner_max_iter < 1 || o->max_outer < 1 || o->nu1 != 1 || o->nu2 != 1)
+        return LM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)o->cuda_stream;
+    for (int i = 0; i < count; ++i) {
+        lm_grid* g = grids[i];
+        if (!g) return LM_ERR_INVALID_ARG;
+        std::memset(&results[i], 0, sizeof(lm_solve_result));
+        if (!g->have_coefs || !g->have_rhs) return LM_ERR_STATE;
+        if (g->ndim != 2 || g->n[1] != 1) return LM_ERR_INVALID_ARG;       // the batch path is 2D
+        for (int a = 0; a < 3; ++a)
+            if (g->bc[a] == LM_BC_PERIODIC && g->n[a] > 1 && (g->n[a] % 2)) return LM_ERR_INVALID_ARG;
+        if (o->use_x0 && !g->have_x0) return LM_ERR_STATE;
+        for (int j = 0; j < i; ++j)
+            if (grids[j] == g) return LM_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < count; ++i) {
+        const int rc = grid_build_mg(grids[i], s);
+        if (rc) return rc;
+        if (!grids[i]->mg.back().ainv) return LM_ERR_INVALID_ARG;   // the batch path needs a direct coarsest level
+    }
+    BCK(cudaStreamSynchronize(s));
+    Plan* P = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        for (Plan* q : g_plans)
+            if (plan_matches(q, grids, count, o)) P = q;
+    }
+    if (!P) {
+        for (int i = 0; i < count; ++i) drop_plans_of(grids[i]);
+        const int rc = build_plan(grids, count, o, s, &P);
+        if (rc) return rc;
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        g_plans.push_back(P);
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    BCK(cudaEventRecord(e0, s));
+    for (int i = 0; i < count; ++i)
+        if (o->use_x0)
+            BCK(cudaMemcpyAsync(grids[i]->x, grids[i]->x0, sizeof(double) * grids[i]->N, cudaMemcpyDeviceToDevice, s));
+    count_launches(1);
+    kb_init_states<<<hdiv(count, NT), NT, 0, s>>>(P->dgrids, count, o->rtol, o->inner_rtol);
+    BCK(cudaGraphLaunch(P->g_first, s));
+    count_launches(P->n_first);
+    int outer = 0;
+    for (;;) {
+        BCK(cudaMemcpyAsync(P->hgather, P->dgather, sizeof(SolveState) * 2 * count, cudaMemcpyDeviceToHost, s));
+        BCK(cudaStreamSynchronize(s));
+        bool all = true;
+        for (int i = 0; i < count; ++i) all = all && P->hgather[i].done;
+        if (all || outer >= o->max_outer) break;
+        BCK(cudaGraphLaunch(P->g_step, s));
+        count_launches(P->n_step);
+        ++outer;
+    }
+    BCK(cudaEventRecord(e1, s));
+    BCK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int worst = LM_OK;
+    for (int i = 0; i < count; ++i) {
+        const SolveState& so = P->hgather[i];
+        const SolveState& si = P->hgather[count + i];
+        lm_solve_result& r = results[i];
+        r.iters = si.iters;
+        r.outer_iters = so.iters;
+        r.vcycles = si.iters;
+        r.rel_residual = so.rel;
+        r.seconds = ms * 1e-3;
+        r.status = so.status ? so.status : (so.converged ? LM_OK : LM_ERR_NO_CONVERGENCE);
+        grids[i]->history.assign(1, so.rel);
+        if (r.status && !worst) worst = r.status;
+    }
+    return worst;
+}
+
+}  // extern "C"

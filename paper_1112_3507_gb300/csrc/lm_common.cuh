@@ -137,13 +137,13 @@ struct Red {
 };
 
 template <int K>
-__device__ __forceinline__ bool grid_reduce(double (&v)[K], const Red& red, const int (&slot)[K], double* smem) {
+__device__ __forceinline__ bool grid_reduce_n(double (&v)[K], const Red& red, const int (&slot)[K], double* smem,
+                                              unsigned blk, unsigned nb) {
     block_sum<K>(v, smem);
     __shared__ unsigned int s_last;
-    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
     if (lin_tid() == 0) {
 #pragma unroll
-        for (int q = 0; q < K; ++q) red.part[q * MAX_PARTIALS + lin_block()] = v[q];
+        for (int q = 0; q < K; ++q) red.part[q * MAX_PARTIALS + blk] = v[q];
         __threadfence();
         s_last = (atomicAdd(red.ctr, 1u) == nb - 1) ? 1u : 0u;
     }
@@ -157,6 +157,11 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[K], const Red& red, cons
     }
     if (lin_tid() == 0) *red.ctr = 0u;
     return true;
+}
+
+template <int K>
+__device__ __forceinline__ bool grid_reduce(double (&v)[K], const Red& red, const int (&slot)[K], double* smem) {
+    return grid_reduce_n<K>(v, red, slot, smem, lin_block(), gridDim.x * gridDim.y * gridDim.z);
 }
 
 // Float-float accumulator: products formed exactly (TwoProduct by FMA) and

@@ -9,6 +9,7 @@
 // cell) and stream each vector once per kernel.
 #include "lm_common.cuh"
 #include "lm_kernels.h"
+#include "lm_tiles.cuh"
 
 namespace lm {
 
@@ -65,26 +66,6 @@ __global__ void __launch_bounds__(NT) k_jacobi_diag(Geo g, const double* __restr
 }
 
 // ---- the float64 operator --------------------------------------------------
-
-__device__ __forceinline__ double apply64_at(int idx, const Geo& g, const Op64& op,
-                                             const double* __restrict__ x) {
-    int i, j, k;
-    cell_coords(idx, g, i, j, k);
-    const double xc = x[idx];
-    double y = op.ct[idx] * xc;
-    Nbr n = nbr_x(idx, i, g);
-    y += op.gx[idx] * (xc - x[n.im]);
-    y += op.gx[n.ip] * (xc - x[n.ip]);
-    if (g.ny > 1) {
-        n = nbr_y(idx, j, g);
-        y += op.gy[idx] * (xc - x[n.im]);
-        y += op.gy[n.ip] * (xc - x[n.ip]);
-    }
-    n = nbr_z(idx, k, g);
-    y += op.gz[idx] * (xc - x[n.im]);
-    y += op.gz[n.ip] * (xc - x[n.ip]);
-    return y;
-}
 
 // y = A x; optional partial sums of x^T A x into part slot 0.
 __global__ void __launch_bounds__(NT) k_apply64(Geo g, Op64 op, const double* __restrict__ x,

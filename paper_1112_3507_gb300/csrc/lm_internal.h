@@ -1,0 +1,80 @@
+// Internal definitions shared by the solver's host translation units
+// (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/lowmach.h"
+#include "lm_common.cuh"
+#include "lm_kernels.h"
+
+namespace lm {
+
+constexpr int COARSE_MAX = 64;      // coarsest level solved exactly below this size
+constexpr int COARSE_SWEEPS = 32;   // (RB, BR) sweep pairs when it cannot be
+
+struct MgLevel {
+    Lev32 L;
+    double h[3];
+    int halved[3] = {0, 0, 0};      // axes halved to reach the next level
+    float* ct = nullptr;            // coefficients (owned on levels >= 1)
+    float* rho = nullptr;
+    float* xa = nullptr;            // sweep buffers (level 0: the grid's tmp_a/tmp_b)
+    float* xb = nullptr;
+    float* xo = nullptr;            // V-cycle output (levels >= 1; level 0 writes the caller's z)
+    float* f = nullptr;             // right-hand side (levels >= 1)
+    float* ainv = nullptr;          // dense inverse on a direct coarsest level
+};
+
+}  // namespace lm
+
+using lm::Geo;
+using lm::Op64;
+using lm::SolveState;
+
+struct lm_grid {
+    int ndim = 0;
+    int n[3] = {1, 1, 1};
+    double h[3] = {1, 1, 1};
+    int bc[3] = {0, 0, 0};
+    int N = 0;
+    int device = 0;
+    int G = 1;          // blocks of the grid-stride streaming kernels
+    Geo geo{};
+
+    double *ct = nullptr, *gx = nullptr, *gy = nullptr, *gz = nullptr, *dinv = nullptr;
+    double *f = nullptr, *x = nullptr, *x0 = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    float *ct32 = nullptr, *rho32 = nullptr;
+    float *r32 = nullptr, *e32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    float *tmp_a = nullptr, *tmp_b = nullptr;   // level-0 sweep buffers
+    double* scal = nullptr;         // reduction results (float32 kernels)
+    unsigned int* ctr = nullptr;    // last-block arrival counter
+    double* stage = nullptr;        // 3N host-input staging (allocated on first use)
+    double* part = nullptr;         // NSLOT * MAX_PARTIALS
+    double* dscal = nullptr;        // device scalars for lm_apply dots
+    SolveState* st = nullptr;       // outer solve state
+    SolveState* st_in = nullptr;    // inner (float32) solve state
+    SolveState* st_host = nullptr;  // pinned mirror
+    double* hist_dev = nullptr;
+    int hist_cap = 0;
+    int* bad = nullptr;
+    int* bad_host = nullptr;
+    double* dscal_host = nullptr;
+
+    bool have_coefs = false, have_rhs = false, have_x0 = false;
+    bool have_dinv = false;         // inverse Jacobi diagonal (formed on the first Jacobi solve)
+    bool mg_built = false;
+    unsigned version = 0;           // bumped whenever coefficients or the hierarchy change
+    std::vector<lm::MgLevel> mg;
+    std::vector<double> history;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+
+namespace lm {
+int grid_build_mg(lm_grid* g, cudaStream_t s);      // multigrid hierarchy (idempotent)
+void batch_forget_grid(const lm_grid* g);            // drop cached batch plans that use g
+Lev32 make_level(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho);
+}  // namespace lm

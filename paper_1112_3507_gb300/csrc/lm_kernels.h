@@ -87,6 +87,8 @@ void launch_coarsen(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cuda
                     float* rho_c);
 void launch_rbgs(const Lev32& L, cudaStream_t s, const float* xin, const float* ec, const Lev32* C, int hx, int hy,
                  int hz, const float* f, float* xout, int first, int zero, int prolong);
+void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const float* ec, const Lev32* C, int hx,
+                    int hy, int hz, const float* f, float* xout, int first, int zero, int prolong, int kz);
 void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s,
                            const float* x, const float* f, float* fc);
 void launch_coarse_inverse(const Lev32& L, cudaStream_t s, float* ainv);

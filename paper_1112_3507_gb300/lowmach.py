@@ -79,6 +79,9 @@ _SIGNATURES = {
     "lm_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "lm_mg_vcycle": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
     "lm_mg_level_shape": (ctypes.c_int, [_P, ctypes.c_int, _I64_3, ctypes.POINTER(ctypes.c_int)]),
+    "lm_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(SolveOpts),
+                                       ctypes.POINTER(SolveResult)]),
+    "lm_autotune_set_cache": (ctypes.c_int, [ctypes.c_char_p]),
     "lm_apply_dot_noalloc": (ctypes.c_int, [ctypes.c_int, _I64_3, _I3, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
@@ -286,6 +289,30 @@ class Grid:
             _check(lib().lm_mg_level_shape(self._g, l, out, ctypes.byref(nl)), "lm_mg_level_shape")
             shapes.append(tuple(out))
         return shapes
+
+
+def autotune_set_cache(path=None):
+    return _check(lib().lm_autotune_set_cache(path.encode() if path else None), "lm_autotune_set_cache")
+
+
+def batch_solve(grids, rtol=1e-8, stream=None, allow=(LM_OK,), **kw):
+    """lm_batch_solve over a list of Grid objects; returns one result dict per grid."""
+    o = SolveOpts()
+    lib().lm_default_opts(ctypes.byref(o))
+    o.mode = MIXED_MG_IR
+    o.rtol = float(rtol)
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown solve option {k}")
+        setattr(o, k, v)
+    o.cuda_stream = _stream_ptr(stream)
+    n = len(grids)
+    handles = (_P * n)(*[g._g for g in grids])
+    res = (SolveResult * n)()
+    code = lib().lm_batch_solve(handles, n, ctypes.byref(o), res)
+    _check(code, "lm_batch_solve", ok=allow)
+    return [dict(status=r.status, iters=r.iters, outer_iters=r.outer_iters, vcycles=r.vcycles,
+                 rel_residual=r.rel_residual, seconds=r.seconds) for r in res]
 
 
 def apply_dot_noalloc(ndim, n, bc, ctilde, gx, gy, gz, x, y, dot_out, stream=None):
