@@ -40,6 +40,8 @@ WORKLOADS = {
                                                     "Ma=0.01, x/y periodic, z walls, rtol 1e-8"),
     "convection128": dict(kind="conv3d", n=128, desc="3D 128^3 convection (reduced), Ma=0.01, rtol 1e-8"),
     "plain64": dict(kind="plain2d", n=64, desc="2D 64^2 polytrope, Ma=0.1, rtol 1e-10"),
+    "batch64": dict(kind="batch", n=64, desc="64 uneven 2D solves, sides from {128,256,512,1024}^2, Ma log-uniform "
+                                             "[1e-3,1e-1], density contrast U[5,30], rtol 1e-8, one batched graph"),
 }
 
 
@@ -191,6 +193,75 @@ def time_kernel(torch, fn, reps: int, stream) -> float:
     e1.record(stream)
     e1.synchronize()
     return e0.elapsed_time(e1) * 1e-3 / reps
+
+
+def run_batch(args):
+    """The batched workload: one step = coefficient assembly + rhs for 64
+    uneven 2D grids and one lm_batch_solve; compared with the same solves one
+    grid at a time (mixed mode) and with the float64 Jacobi-PCG baseline."""
+    import torch
+
+    from paper_1112_3507_gb300 import lowmach as lm
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    from paper_1112_3507_gb300 import inputs as I
+    probs = I.config_batch(count=64, seed=42)
+    ncells = sum(p.size for p in probs)
+    tens = [[torch.as_tensor(a.ravel(), device=dev) for a in (p.rho_old, p.rho_new, p.cs2, p.f)] for p in probs]
+    grids = [lm.Grid.for_problem(p) for p in probs]
+
+    def load():
+        for p, g, t in zip(probs, grids, tens):
+            g.set_coefficients(t[0], t[1], t[2], p.dt, stream)
+            g.set_rhs(t[3], stream)
+
+    def step():
+        load()
+        return lm.batch_solve(grids, rtol=1e-8, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = lm.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    results = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    e1.synchronize()
+    launches = lm.kernel_launches() - launches0
+    clk = clocks.stop()
+    t_step = e0.elapsed_time(e1) * 1e-3 / args.steps
+    res = results[-1]
+    assert all(r["status"] == 0 and r["rel_residual"] <= 1e-8 for r in res)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    def seq(mode):
+        load()
+        return [g.solve(mode=mode, rtol=1e-8, stream=stream, max_iter=args.max_iter) for g in grids]
+
+    seq("mixed")
+    t_seq, rs = timed(lambda: seq("mixed"))
+    t_jac, rj = timed(lambda: seq("jacobi"))
+    line = {"workload": WORKLOADS["batch64"]["desc"], "cells": ncells, "ms_per_batch": t_step * 1e3,
+            "gdof_per_s": ncells / t_step / 1e9, "steps": args.steps, "warmup": args.warmup,
+            "inner_iters_max": max(r["iters"] for r in res), "outer_iters_max": max(r["outer_iters"] for r in res),
+            "sequential_mixed_ms": t_seq * 1e3, "sequential_fp64_jacobi_ms": t_jac * 1e3,
+            "speedup_vs_sequential_mixed": t_seq / t_step, "speedup_vs_fp64_pcg": t_jac / t_step,
+            "jacobi_iters_total": sum(r["iters"] for r in rj), "gpu_launches_per_batch": launches / args.steps,
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    for g in grids:
+        g.close()
 
 
 def run_ours(args):
@@ -364,6 +435,8 @@ def main():
     args.max_iter = args.max_iter
     if args.impl == "reference":
         run_reference(args)
+    elif WORKLOADS[args.workload]["kind"] == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

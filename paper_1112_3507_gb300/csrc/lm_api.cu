@@ -104,8 +104,21 @@ bool mg_supported(const lm_grid* g) {
 // Multigrid hierarchy from the float32 coefficients (coarse c~, rho = child means).
 int build_mg(lm_grid* g, cudaStream_t s) {
     if (g->mg_built) return LM_OK;
-    ++g->version;
-    free_mg(g);
+    if (!g->mg.empty()) {
+        // the grid's shape never changes: keep the buffers, recompute the
+        // coarse coefficients and the coarsest inverse from the new values
+        for (size_t l = 1; l < g->mg.size(); ++l) {
+            const MgLevel& F = g->mg[l - 1];
+            MgLevel& C = g->mg[l];
+            launch_coarsen(F.L, C.L, F.halved[0], F.halved[1], F.halved[2], s, C.ct, C.rho);
+        }
+        MgLevel& Lc = g->mg.back();
+        if (Lc.ainv) launch_coarse_inverse(Lc.L, s, Lc.ainv);
+        CK(cudaGetLastError());
+        g->mg_built = true;
+        return LM_OK;
+    }
+    ++g->version;       // new buffers: cached batch plans of this grid are stale
     MgLevel L0;
     L0.L = make_lev(g->n, g->bc, g->h, g->ct32, g->rho32);
     std::memcpy(L0.h, g->h, sizeof L0.h);
@@ -417,7 +430,6 @@ int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double
     CK(cudaStreamSynchronize(s));
     g->mg_built = false;
     g->have_dinv = false;
-    ++g->version;
     if (*g->bad_host) {
         g->have_coefs = false;
         return LM_ERR_NOT_POSITIVE;

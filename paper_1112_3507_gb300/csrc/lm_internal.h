@@ -66,7 +66,7 @@ struct lm_grid {
     bool have_coefs = false, have_rhs = false, have_x0 = false;
     bool have_dinv = false;         // inverse Jacobi diagonal (formed on the first Jacobi solve)
     bool mg_built = false;
-    unsigned version = 0;           // bumped whenever coefficients or the hierarchy change
+    unsigned version = 0;           // bumped when the hierarchy buffers are (re)allocated
     std::vector<lm::MgLevel> mg;
     std::vector<double> history;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
