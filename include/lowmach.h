@@ -209,6 +209,43 @@ int  lm_mg_vcycle(lm_grid* g, const float* r, float* z, int nu1, int nu2, void* 
  * (n_out[3]); LM_ERR_INVALID_ARG past the coarsest level. */
 int  lm_mg_level_shape(lm_grid* g, int level, int64_t n_out[3], int* num_levels);
 
+/* ---- the learned warm start / preconditioner ----------------------------- */
+/* A 4-level U-Net on 2D images (rows = z, columns = x; NHWC, batch B):
+ * encoder e_l = relu(conv3(relu(conv3(in_l, A_l)), B_l)), in_0 = the 3-channel
+ * input, in_l = 2x2 mean of e_{l-1}; decoder d_l = relu(conv3(relu(conv3(
+ * [up2(d_{l+1}), e_l], C_l)), D_l)), d_3 = e_3; output y = conv1(d_0, O).
+ * conv3: 3x3, zero padding, weights [3][3][Cin][Cout]; channels ch[0..3]
+ * (16, 32, 48, 64 by default).  BF16 weights and activations, FP32
+ * accumulation, FP32 master weights trained by Adam.  The paper has no
+ * learned component: this serves the learned mode LM_MIXED_LEARNED_FCG_IR.
+ * Images need H, W divisible by 8.  Device buffers are float32 and ordered
+ * on `stream`; parameter arrays are host float32 in the storage order
+ * A0 a0 B0 b0 A1 a1 B1 b1 A2 a2 B2 b2 A3 a3 B3 b3 C2 c2 D2 d2 C1 c1 D1 d1
+ * C0 c0 D0 d0 O o. */
+typedef struct lm_net lm_net;
+int  lm_net_create(const int ch[4], lm_net** out);
+void lm_net_destroy(lm_net* net);
+int  lm_net_num_params(const lm_net* net);
+int  lm_net_set_params(lm_net* net, const float* host, int n);   /* also resets Adam state */
+int  lm_net_get_params(lm_net* net, float* host, int n);
+int  lm_net_get_grads(lm_net* net, float* host, int n);          /* of the last lm_net_backward */
+/* y (B*H*W) = net(x (B*H*W*3)); keeps the activations for lm_net_backward */
+int  lm_net_forward(lm_net* net, const float* x, float* y, int B, int H, int W, void* stream);
+/* parameter gradients of sum(gy * y) for the last forward (overwritten) */
+int  lm_net_backward(lm_net* net, const float* gy, void* stream);
+/* loss = mean((y - t)^2) over n values, gy = its gradient (device); *loss on host if non-NULL */
+int  lm_net_mse(lm_net* net, const float* y, const float* t, float* gy, long long n, double* loss, void* stream);
+/* one Adam step (Kingma & Ba) with bias correction on the last gradients */
+int  lm_net_adam(lm_net* net, float lr, float beta1, float beta2, float eps, void* stream);
+/* file: "LMUNET01", int32 ch[4], int32 n, float32 params[n], uint64 FNV-1a of the params */
+int  lm_net_save(lm_net* net, const char* path);
+int  lm_net_load(const char* path, lm_net** out);               /* LM_ERR_NETWORK if bad */
+/* Network input of a 2D grid from v (device float64, N): channel 0 = v/rms(v),
+ * 1 = log(rho/mean rho), 2 = log(1/(c~ rho h_z^2))/10 (feat: N*3 float, device);
+ * *scale = rms(v)/(mean c~ + pi^2 mean(1/rho)), the factor that turns the
+ * network output into an approximation of A^-1 v. */
+int  lm_net_features(lm_grid* g, const double* v, float* feat, double* scale, void* stream);
+
 /* ---- batched solves ------------------------------------------------------ */
 
 /* Solve `count` independent 2D grids (distinct lm_grid handles, each with

@@ -102,19 +102,22 @@ def init_params(rng, cin: int = 3, ch=(16, 32, 48, 64)):
     return P
 
 
-def forward(P, x, ch=(16, 32, 48, 64)):
-    """Returns (y, cache)."""
+def forward(P, x, ch=(16, 32, 48, 64), rnd=None):
+    """Returns (y, cache).  rnd, if given, is applied to the input and to
+    every stored activation (after each conv + relu and each pooling), to
+    evaluate the network at the storage precision of an implementation."""
+    r = rnd if rnd is not None else (lambda a: a)
     cache = {}
-    h = x
+    h = r(x)
     enc = []
     for l in range(4):
         if l > 0:
-            h = pool_fwd(enc[-1])
+            h = r(pool_fwd(enc[-1]))
         cache[f"in{l}"] = h
         z1 = conv3_fwd(h, P[f"A{l}"], P[f"a{l}"])
-        a1 = np.maximum(z1, 0.0)
+        a1 = r(np.maximum(z1, 0.0))
         z2 = conv3_fwd(a1, P[f"B{l}"], P[f"b{l}"])
-        e = np.maximum(z2, 0.0)
+        e = r(np.maximum(z2, 0.0))
         cache[f"ez1{l}"], cache[f"ea1{l}"], cache[f"ez2{l}"] = z1, a1, z2
         enc.append(e)
     d = enc[3]
@@ -122,9 +125,9 @@ def forward(P, x, ch=(16, 32, 48, 64)):
         u = up_fwd(d)
         cat = np.concatenate([u, enc[l]], axis=3)
         z1 = conv3_fwd(cat, P[f"C{l}"], P[f"c{l}"])
-        a1 = np.maximum(z1, 0.0)
+        a1 = r(np.maximum(z1, 0.0))
         z2 = conv3_fwd(a1, P[f"D{l}"], P[f"d{l}"])
-        d = np.maximum(z2, 0.0)
+        d = r(np.maximum(z2, 0.0))
         cache[f"cat{l}"], cache[f"dz1{l}"], cache[f"da1{l}"], cache[f"dz2{l}"] = cat, z1, a1, z2
     cache["enc"] = enc
     cache["d0"] = d
@@ -165,3 +168,29 @@ def mse_loss(y, t):
     """mean((y - t)^2) and its gradient w.r.t. y."""
     d = y - t
     return float(np.mean(d * d)), 2.0 * d / d.size
+
+
+def features(v, rho, ct, hz):
+    """Network input of a 2D field (rows z, columns x) and the output scale:
+    ch0 = v/rms(v), ch1 = log(rho/mean rho), ch2 = log(1/(c~ rho hz^2))/10;
+    s = rms(v) / (mean c~ + pi^2 mean(1/rho)).  Returns ([1, H, W, 3], s)."""
+    v = np.asarray(v, dtype=np.float64)
+    rho = np.asarray(rho, dtype=np.float64)
+    ct = np.asarray(ct, dtype=np.float64)
+    rms = np.sqrt(np.mean(v * v))
+    x = np.stack([v / rms, np.log(rho / rho.mean()), np.log(1.0 / (ct * rho * hz * hz)) / 10.0], axis=-1)
+    s = rms / (ct.mean() + np.pi ** 2 * np.mean(1.0 / rho))
+    return x[None], s
+
+
+def flat_params(P, cin=3, ch=(16, 32, 48, 64)):
+    return np.concatenate([P[n].ravel() for n, _ in param_shapes(cin, ch)])
+
+
+def unflat_params(a, cin=3, ch=(16, 32, 48, 64)):
+    P, o = {}, 0
+    for n, shp in param_shapes(cin, ch):
+        k = int(np.prod(shp))
+        P[n] = np.asarray(a[o:o + k], dtype=np.float64).reshape(shp)
+        o += k
+    return P

@@ -332,8 +332,12 @@ int solve_mg_pcg(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
     return g->st_host->rel <= o->rtol ? LM_OK : LM_ERR_NO_CONVERGENCE;
 }
 
-// Inner float32 flexible CG on A32 e = r (r overwritten), V-cycle preconditioner.
-int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, int* vcycles) {
+// Inner float32 flexible CG on A32 e = r (r overwritten).  Preconditioner:
+// the V-cycle, or (*use_net) the learned network z = s NN(features(r)); a
+// network step that leaves the inner residual above `stall` after 4
+// iterations, or returns a non-finite value, switches the rest of the solve
+// to the V-cycle (*use_net = false).
+int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, int* vcycles, bool* use_net) {
     int rc;
     MgLevel& M = g->mg[0];
     const Red red{g->part, g->scal, g->ctr};
@@ -342,8 +346,12 @@ int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, in
     // the inner problem's reference norm: ||r|| of its right-hand side
     launch_dot32(g->N, g->G, s, g->r32, g->r32, red, 4, g->st_in);
     for (int it = 0; it < o->inner_max_iter; ++it) {
-        vcycle(g, 0, g->z32, g->r32, o->nu1, o->nu2, s);
-        ++*vcycles;
+        if (use_net && *use_net) {
+            if ((rc = lm::net_apply<float, float>(g, g->r32, g->z32, s))) return rc;
+        } else {
+            vcycle(g, 0, g->z32, g->r32, o->nu1, o->nu2, s);
+            ++*vcycles;
+        }
         if (it > 0) launch_dot32(g->N, g->G, s, g->z32, g->q32, red, 3, nullptr);
         launch_fcg_beta_p(g->N, g->G, s, g->z32, g->p32, g->scal, it == 0);
         launch_apply32(M.L, s, g->p32, g->q32, g->r32, red, 0, 2);
@@ -351,23 +359,41 @@ int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, in
         CK(cudaGetLastError());
         ++*iters;
         if ((rc = sync_state(g, g->st_in, s))) return rc;
+        const double rel = g->st_host->rel;
+        if (use_net && *use_net && (!std::isfinite(rel) || g->st_host->status || (it >= 3 && rel > 0.5))) {
+            *use_net = false;                     // the network does not help here: V-cycle from now on
+            if (!std::isfinite(rel) || g->st_host->status) return LM_OK;   // restart from the outer residual
+        }
         if (g->st_host->status) return LM_OK;     // breakdown: keep e so far
-        if (g->st_host->rel <= o->inner_rtol) break;
+        if (rel <= o->inner_rtol) break;
     }
     return LM_OK;
 }
 
 // ---- mixed precision: float64 iterative refinement around float32 FCG+MG ----
-int solve_mixed_ir(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
+// learned = true: warm start x0 = s NN(features(f)) (kept only if it beats
+// x0 = 0) and the network as the inner preconditioner, with the V-cycle as
+// fallback.
+int solve_mixed_ir(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res, bool learned) {
     cudaStream_t s = S(o->cuda_stream);
     int rc;
     if ((rc = build_mg(g, s))) return rc;
     if ((rc = init_state(g, g->st, o->rtol, s))) return rc;
+    bool use_net = learned && lm::net_usable(g);
     const bool x0 = o->use_x0 && g->have_x0;
     if (x0) CK(cudaMemcpyAsync(g->x, g->x0, sizeof(double) * g->N, cudaMemcpyDeviceToDevice, s));
-    launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, !x0, g->st, 1, nullptr);
+    bool warm = false;
+    if (use_net && !x0) {
+        if ((rc = lm::net_apply<double, double>(g, g->f, g->x, s))) return rc;
+        warm = true;
+    }
+    launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, !(x0 || warm), g->st, 1, nullptr);
     CK(cudaGetLastError());
     if ((rc = sync_state(g, g->st, s))) return rc;
+    if (warm && !(g->st_host->rel < 1.0)) {          // the warm start is worse than zero: drop it
+        launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, 1, g->st, 1, nullptr);
+        if ((rc = sync_state(g, g->st, s))) return rc;
+    }
     g->history.assign(1, g->st_host->rel);
     if (!(g->st_host->fnorm > 0.0)) {
         res->rel_residual = 0.0;
@@ -377,7 +403,7 @@ int solve_mixed_ir(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
     int outer = 0, iters = 0, vc = 0;
     int status = LM_OK;
     while (rel > o->rtol && outer < o->max_outer && iters < o->max_iter) {
-        if ((rc = inner_fcg(g, o, s, &iters, &vc))) return rc;
+        if ((rc = inner_fcg(g, o, s, &iters, &vc, &use_net))) return rc;
         if (g->st_host->status) status = g->st_host->status;
         launch_ir_correct(g->N, g->G, s, g->x, g->e32);
         launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, 0, g->st, 0, nullptr);
@@ -538,6 +564,9 @@ void lm_grid_destroy(lm_grid* g) {
     if (!g) return;
     cudaDeviceSynchronize();
     lm::batch_forget_grid(g);
+    if (g->net) lm_net_destroy(g->net);
+    cudaFree(g->feat);
+    cudaFree(g->nny);
     free_mg(g);
     void* bufs[] = {g->ct, g->gx, g->gy, g->gz, g->dinv, g->f, g->x, g->x0, g->r, g->p, g->q,
                     g->ct32, g->rho32, g->r32, g->e32, g->z32, g->p32, g->q32, g->tmp_a, g->tmp_b,
@@ -584,9 +613,15 @@ int lm_set_initial_guess(lm_grid* g, const double* x0, int on_device, void* stre
 }
 
 int lm_load_network(lm_grid* g, const char* path) {
-    (void)g;
-    (void)path;
-    return LM_ERR_NETWORK;
+    if (!g || !path) return LM_ERR_INVALID_ARG;
+    lm_net* N = nullptr;
+    int rc = lm_net_load(path, &N);
+    if (rc) return rc;
+    if (g->net) lm_net_destroy(g->net);
+    g->net = N;
+    if (!g->feat && (rc = dalloc(&g->feat, (size_t)3 * g->N))) return rc;
+    if (!g->nny && (rc = dalloc(&g->nny, g->N))) return rc;
+    return LM_OK;
 }
 
 int lm_solve(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
@@ -606,7 +641,8 @@ int lm_solve(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
     switch (o->mode) {
         case LM_FP64_JACOBI_PCG: rc = solve_jacobi_pcg(g, o, res); break;
         case LM_FP64_MG_PCG: rc = solve_mg_pcg(g, o, res); break;
-        default: rc = solve_mixed_ir(g, o, res); break;
+        case LM_MIXED_MG_IR: rc = solve_mixed_ir(g, o, res, false); break;
+        default: rc = solve_mixed_ir(g, o, res, true); break;
     }
     cudaEventRecord(g->ev1, s);
     cudaEventSynchronize(g->ev1);

@@ -30,6 +30,7 @@ struct MgLevel {
 
 }  // namespace lm
 
+struct lm_net;
 using lm::Geo;
 using lm::Op64;
 using lm::SolveState;
@@ -67,6 +68,9 @@ struct lm_grid {
     bool have_dinv = false;         // inverse Jacobi diagonal (formed on the first Jacobi solve)
     bool mg_built = false;
     unsigned version = 0;           // bumped when the hierarchy buffers are (re)allocated
+    lm_net* net = nullptr;          // learned warm start / preconditioner (2D grids)
+    float* feat = nullptr;          // network input (N x 3)
+    float* nny = nullptr;           // network output (N)
     std::vector<lm::MgLevel> mg;
     std::vector<double> history;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -76,5 +80,13 @@ struct lm_grid {
 namespace lm {
 int grid_build_mg(lm_grid* g, cudaStream_t s);      // multigrid hierarchy (idempotent)
 void batch_forget_grid(const lm_grid* g);            // drop cached batch plans that use g
+int net_forward(lm_net* N, const float* x, float* y, int B, int H, int W, cudaStream_t s);
+int net_backward(lm_net* N, const float* gy, cudaStream_t s);
+int net_create(const int ch[4], lm_net** out);
+void net_destroy(lm_net* N);
+int net_set_params(lm_net* N, const float* host, int n);
+bool net_usable(const lm_grid* g);
+template <typename TV, typename TO>
+int net_apply(lm_grid* g, const TV* v, TO* dst, cudaStream_t s);
 Lev32 make_level(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho);
 }  // namespace lm

@@ -58,6 +58,7 @@ _P = ctypes.c_void_p
 _I64_3 = ctypes.c_int64 * 3
 _D3 = ctypes.c_double * 3
 _I3 = ctypes.c_int * 3
+_I4 = ctypes.c_int * 4
 
 _SIGNATURES = {
     "lm_default_opts": (None, [ctypes.POINTER(SolveOpts)]),
@@ -79,6 +80,19 @@ _SIGNATURES = {
     "lm_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "lm_mg_vcycle": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
     "lm_mg_level_shape": (ctypes.c_int, [_P, ctypes.c_int, _I64_3, ctypes.POINTER(ctypes.c_int)]),
+    "lm_net_create": (ctypes.c_int, [_I4, ctypes.POINTER(_P)]),
+    "lm_net_destroy": (None, [_P]),
+    "lm_net_num_params": (ctypes.c_int, [_P]),
+    "lm_net_set_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+    "lm_net_get_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+    "lm_net_get_grads": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+    "lm_net_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "lm_net_backward": (ctypes.c_int, [_P, _P, _P]),
+    "lm_net_mse": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double), _P]),
+    "lm_net_adam": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
+    "lm_net_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "lm_net_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_P)]),
+    "lm_net_features": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "lm_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(SolveOpts),
                                        ctypes.POINTER(SolveResult)]),
     "lm_autotune_set_cache": (ctypes.c_int, [ctypes.c_char_p]),
@@ -280,6 +294,19 @@ class Grid:
             raise ValueError("lm_mg_vcycle takes device tensors")
         _check(lib().lm_mg_vcycle(self._g, rp, zp, nu1, nu2, _stream_ptr(stream)), "lm_mg_vcycle")
 
+    def load_network(self, path):
+        return _check(lib().lm_load_network(self._g, str(path).encode()), "lm_load_network")
+
+    def features(self, v, feat, stream=None):
+        """Network input of this (2D) grid from device float64 v into device float32 feat (N*3)."""
+        vp, dv, kv = _field(v, self.N)
+        fp, df, kf = _field(feat, 3 * self.N, np.float32)
+        if not (dv and df):
+            raise ValueError("lm_net_features takes device tensors")
+        sc = ctypes.c_double(0.0)
+        _check(lib().lm_net_features(self._g, vp, fp, ctypes.byref(sc), _stream_ptr(stream)), "lm_net_features")
+        return sc.value
+
     def mg_levels(self):
         shapes = []
         nl = ctypes.c_int(0)
@@ -289,6 +316,73 @@ class Grid:
             _check(lib().lm_mg_level_shape(self._g, l, out, ctypes.byref(nl)), "lm_mg_level_shape")
             shapes.append(tuple(out))
         return shapes
+
+
+class Net:
+    """The learned U-Net (lm_net_*): forward/backward/Adam on device float32 tensors."""
+
+    def __init__(self, ch=(16, 32, 48, 64), _handle=None):
+        if _handle is not None:
+            self._n = _handle
+        else:
+            h = _P()
+            _check(lib().lm_net_create(_I4(*ch), ctypes.byref(h)), "lm_net_create")
+            self._n = h
+        self.nparams = lib().lm_net_num_params(self._n)
+
+    @classmethod
+    def load(cls, path):
+        h = _P()
+        _check(lib().lm_net_load(str(path).encode(), ctypes.byref(h)), "lm_net_load")
+        return cls(_handle=h)
+
+    def close(self):
+        if getattr(self, "_n", None):
+            lib().lm_net_destroy(self._n)
+            self._n = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().lm_net_set_params(self._n, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size),
+               "lm_net_set_params")
+
+    def params(self):
+        a = np.empty(self.nparams, dtype=np.float32)
+        _check(lib().lm_net_get_params(self._n, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size),
+               "lm_net_get_params")
+        return a
+
+    def grads(self):
+        a = np.empty(self.nparams, dtype=np.float32)
+        _check(lib().lm_net_get_grads(self._n, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size),
+               "lm_net_get_grads")
+        return a
+
+    def forward(self, x, y, B, H, W, stream=None):
+        _check(lib().lm_net_forward(self._n, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), B, H, W,
+                                    _stream_ptr(stream)), "lm_net_forward")
+
+    def backward(self, gy, stream=None):
+        _check(lib().lm_net_backward(self._n, ctypes.c_void_p(gy.data_ptr()), _stream_ptr(stream)), "lm_net_backward")
+
+    def mse(self, y, t, gy, want_loss=True, stream=None):
+        loss = ctypes.c_double(0.0)
+        _check(lib().lm_net_mse(self._n, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                ctypes.c_void_p(gy.data_ptr()), y.numel(), ctypes.byref(loss) if want_loss else None,
+                                _stream_ptr(stream)), "lm_net_mse")
+        return loss.value
+
+    def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+        _check(lib().lm_net_adam(self._n, lr, b1, b2, eps, _stream_ptr(stream)), "lm_net_adam")
+
+    def save(self, path):
+        _check(lib().lm_net_save(self._n, str(path).encode()), "lm_net_save")
 
 
 def autotune_set_cache(path=None):
