@@ -42,7 +42,17 @@ WORKLOADS = {
     "plain64": dict(kind="plain2d", n=64, desc="2D 64^2 polytrope, Ma=0.1, rtol 1e-10"),
     "batch64": dict(kind="batch", n=64, desc="64 uneven 2D solves, sides from {128,256,512,1024}^2, Ma log-uniform "
                                              "[1e-3,1e-1], density contrast U[5,30], rtol 1e-8, one batched graph"),
+    "learned256": dict(kind="train2d", n=256, desc="2D 256^2 held-out problems of the learned-part family (seeds "
+                                                   "30000+, contrast U[5,30], Ma log-uniform [1e-3,1e-1]), "
+                                                   "rtol 1e-8, learned warm start + preconditioner"),
+    "semiconvection512": dict(kind="semi3d", n=512, desc="3D 512^3 two-component semiconvection (R_rho 1.1, "
+                                                         "1% T and helium perturbations), Ma=0.001, rtol 1e-8"),
 }
+DEFAULT_MODE = {"train2d": "learned"}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from an ncu
+# capture of the same kernel build on this workload, keyed (workload, kernel)
+NCU_TRAFFIC: dict = {}
+WEIGHTS = os.path.join(ROOT, "paper_1112_3507_gb300", "weights", "unet_16_32_48_64.bin")
 
 
 def make_problem(name: str, seed: int = 1):
@@ -50,7 +60,38 @@ def make_problem(name: str, seed: int = 1):
     w = WORKLOADS[name]
     if w["kind"] == "conv3d":
         return I.config_convection_3d(w["n"], seed=seed)
+    if w["kind"] == "semi3d":
+        return I.config_semiconvection_3d(w["n"], seed=7)
+    if w["kind"] == "train2d":
+        return I.config_training_2d(30000 + seed - 1, n=w["n"])
     return I.config_plain_2d(w["n"], seed=seed)
+
+
+def downsized(name: str, m: int, seed: int = 1):
+    """The workload's recipe on an m-cell-per-axis grid (oracle iteration counts)."""
+    from paper_1112_3507_gb300 import inputs as I
+    kind = WORKLOADS[name]["kind"]
+    if kind == "conv3d":
+        return I.config_convection_3d(m, seed=seed)
+    if kind == "semi3d":
+        return I.config_semiconvection_3d(m, seed=7)
+    return make_problem(name, seed)
+
+
+def job_time(elapsed_s: float, world: int, device=None) -> float:
+    """The job's time: the maximum over ranks of each rank's elapsed seconds."""
+    if world <= 1:
+        return elapsed_s
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cells_per_step: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput in GDOF/s: every rank solves its own replica."""
+    return world * cells_per_step * steps / seconds / 1e9
 
 
 # ---------------------------------------------------------------- clocks
@@ -124,14 +165,15 @@ def oracle_sample(name: str, iters: int = 2, seed: int = 1) -> dict:
     t_setup = max((t1 - t0) - t_iter, 0.0)
     counts = []
     n = w["n"]
-    sizes = [n // 16, n // 8, n // 4] if w["kind"] == "conv3d" else [n]
+    big = n // 8 if n > 256 else n // 4               # largest downsized grid the oracle solves in seconds
+    sizes = [big // 4, big // 2, big] if w["kind"] in ("conv3d", "semi3d") else [n]
     for m in sizes:
-        q = I.config_convection_3d(m, seed=seed) if w["kind"] == "conv3d" else p
-        _, c, _ = P.solve_pcg_jacobi(P.operator_from_problem(q), q.f, rtol=p.rtol)
+        q = downsized(name, m, seed) if len(sizes) > 1 else p
+        _, c, _ = P.solve_pcg_jacobi(P.operator_from_problem(q), q.f, rtol=p.rtol, maxiter=200000)
         counts.append(c)
     if len(counts) > 1:
         growth = (counts[-1] / counts[0]) ** (1.0 / (len(counts) - 1))
-        est_iters = counts[-1] * growth ** 2          # n/4 -> n is two doublings
+        est_iters = counts[-1] * growth ** round(np.log2(n / big))
     else:
         est_iters = counts[0]
     est_s = t_setup + t_iter * est_iters
@@ -278,19 +320,28 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    p = make_problem(args.workload, seed=1)
+    kind = WORKLOADS[args.workload]["kind"]
+    mode = args.mode or DEFAULT_MODE.get(kind, "mixed")
+    # the learned workload cycles through 8 held-out problems; the others solve one
+    probs = [make_problem(args.workload, seed=1 + k) for k in range(8 if kind == "train2d" else 1)]
+    p = probs[0]
     N = p.size
-    ro, rn, c2, f = (torch.as_tensor(a.ravel(), device=dev) for a in (p.rho_old, p.rho_new, p.cs2, p.f))
+    dev_in = [[torch.as_tensor(a.ravel(), device=dev) for a in (q.rho_old, q.rho_new, q.cs2, q.f)] for q in probs]
     g = lm.Grid.for_problem(p)
-    solve_kw = dict(mode=args.mode, rtol=p.rtol, max_iter=args.max_iter)
+    if mode == "learned":
+        g.load_network(WEIGHTS)
+    solve_kw = dict(mode=mode, rtol=p.rtol, max_iter=args.max_iter)
+    small = 4 * 8 * N < 2 * 129e6           # inputs that fit in L2 get it flushed between steps
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev) if small else None
 
-    def step():
-        g.set_coefficients(ro, rn, c2, p.dt, stream)
+    def step(k):
+        ro, rn, c2, f = dev_in[k % len(probs)]
+        g.set_coefficients(ro, rn, c2, probs[k % len(probs)].dt, stream)
         g.set_rhs(f, stream)
         return g.solve(stream=stream, **solve_kw)
 
-    for _ in range(args.warmup):
-        res = step()
+    for k in range(args.warmup):
+        step(k)
     torch.cuda.synchronize()
 
     def barrier():
@@ -302,85 +353,94 @@ def run_ours(args):
     barrier()
     clocks.start()
     launches0 = lm.kernel_launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    results = [step() for _ in range(args.steps)]
-    e1.record(stream)
-    e1.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    results = []
+    for k in range(args.steps):
+        if flush is not None:
+            flush.fill_(float(k))
+        ev[k][0].record(stream)
+        results.append(step(k))
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
     launches = lm.kernel_launches() - launches0
     barrier()
     clk = clocks.stop()
+    elapsed = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
     if args.only_steps:                 # profiling runs: the timed solves and nothing else
         if rank == 0:
-            print(json.dumps({"only_steps": True, "ms_per_step": e0.elapsed_time(e1) / args.steps,
+            print(json.dumps({"only_steps": True, "ms_per_step": elapsed * 1e3 / args.steps,
                               "gpu_launches": launches, "solve": results[-1]}), flush=True)
         g.close()
         return
-    elapsed = e0.elapsed_time(e1) * 1e-3
-    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed = float(t.item())
+    elapsed = job_time(elapsed, world, dev)
     res = results[-1]
     assert all(r["status"] == 0 and r["rel_residual"] <= p.rtol for r in results), results
-    value = world * N * args.steps / elapsed / 1e9
+    value = job_value(N, args.steps, world, elapsed)
     t_solve = elapsed / args.steps
 
     # ---- end to end through the C ABI with host buffers (pinned)
-    host = [torch.from_numpy(np.ascontiguousarray(a.ravel())).pin_memory() for a in (p.rho_old, p.rho_new, p.cs2, p.f)]
-    hn = [h.numpy() for h in host]
+    host = [[torch.from_numpy(np.ascontiguousarray(a.ravel())).pin_memory().numpy()
+             for a in (q.rho_old, q.rho_new, q.cs2, q.f)] for q in probs]
     xout = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
 
-    def e2e_step():
-        g.set_coefficients(hn[0], hn[1], hn[2], p.dt, stream)
+    def e2e_step(k):
+        hn = host[k % len(probs)]
+        g.set_coefficients(hn[0], hn[1], hn[2], probs[k % len(probs)].dt, stream)
         g.set_rhs(hn[3], stream)
         r = g.solve(stream=stream, **solve_kw)
         g.solution(xout, stream)
         return r
 
-    e2e_step()
+    e2e_step(0)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
+    for k in range(args.steps):
+        e2e_step(k)
     torch.cuda.synchronize()
-    e2e_t = time.perf_counter() - t0
-    t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_t = float(t.item())
+    e2e_t = job_time(time.perf_counter() - t0, world, dev)
 
-    # ---- the float64 Jacobi-PCG baseline and the float64 multigrid mode, same GPU
+    # ---- the float64 Jacobi-PCG baseline, the float64 multigrid mode and the
+    # mixed mode without the network, same GPU, same problems
     base = {}
-    for mode in ("jacobi", "fp64-mg"):
-        step_b = lambda: (g.set_coefficients(ro, rn, c2, p.dt, stream), g.set_rhs(f, stream),
-                          g.solve(stream=stream, mode=mode, rtol=p.rtol, max_iter=args.max_iter))[-1]
-        step_b()
+    others = ["jacobi", "fp64-mg"] + (["mixed"] if mode != "mixed" else [])
+    for bmode in others:
+        def step_b(k):
+            ro, rn, c2, f = dev_in[k % len(probs)]
+            g.set_coefficients(ro, rn, c2, probs[k % len(probs)].dt, stream)
+            g.set_rhs(f, stream)
+            return g.solve(stream=stream, mode=bmode, rtol=p.rtol, max_iter=args.max_iter, allow=(0, -3))
+        step_b(0)
+        reps = len(probs) if kind == "train2d" else 1
         torch.cuda.synchronize()
         b0 = time.perf_counter()
-        rb = step_b()
+        rb = [step_b(k) for k in range(reps)]
         torch.cuda.synchronize()
-        tb = time.perf_counter() - b0
-        base[mode] = {"time_to_tol_ms": tb * 1e3, "iters": rb["iters"], "rel_residual": rb["rel_residual"],
-                      "gdof_iter_per_s": N * rb["iters"] / tb / 1e9}
+        tb = (time.perf_counter() - b0) / reps
+        base[bmode] = {"time_to_tol_ms": tb * 1e3, "iters": rb[-1]["iters"], "status": rb[-1]["status"],
+                       "rel_residual": rb[-1]["rel_residual"],
+                       "gdof_iter_per_s": N * float(np.mean([r["iters"] for r in rb])) / tb / 1e9}
 
-    # ---- roofline of the dominant kernel, timed alone via its row-level entry point
-    g.set_coefficients(ro, rn, c2, p.dt, stream)
+    # ---- roofline of the dominant kernel (the red-black sweep of the V-cycle),
+    # timed alone through its row-level entry point, on the launching stream
+    step(0)
     x32 = torch.randn(N, dtype=torch.float32, device=dev)
+    f32 = torch.randn(N, dtype=torch.float32, device=dev)
     y32 = torch.empty_like(x32)
     reps = 20
-    t_k = time_kernel(torch, lambda: g.apply(x32, y32, prec=lm.PREC_FP32, stream=stream), reps, stream)
-    bytes_per_cell = 16          # read x, rho, c~; write y (float32), faces formed on the fly
+    t_sw = time_kernel(torch, lambda: g.mg_sweep(x32, f32, y32, 0, stream=stream), reps, stream)
+    t_ap = time_kernel(torch, lambda: g.apply(x32, y32, prec=lm.PREC_FP32, stream=stream), reps, stream)
+    x64 = torch.randn(N, dtype=torch.float64, device=dev)
+    y64 = torch.empty_like(x64)
+    t_k64 = time_kernel(torch, lambda: g.apply(x64, y64, prec=lm.PREC_FP64, stream=stream), reps, stream)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = bytes_per_cell * N / t_k / 1e9
-    x64 = torch.randn(N, dtype=torch.float64, device=dev)
-    y64 = torch.empty_like(x64)
-    t_k64 = time_kernel(torch, lambda: g.apply(x64, y64, prec=lm.PREC_FP64, stream=stream), reps, stream)
+    sweep_bytes = 20              # read x, f, rho, c~; write x (float32); faces formed on the fly
+    achieved = sweep_bytes * N / t_sw / 1e9
+    traffic = NCU_TRAFFIC.get((args.workload, "k_rbgs"))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -390,28 +450,38 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64 (float32 multigrid/Krylov, float64 residual/refinement)",
+            "vs_baseline": None, "dtype": "f32+f64 (float32 multigrid/Krylov, float64 residual/refinement)"
+            + (", bf16 network" if mode == "learned" else ""),
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]["desc"], "cells": N, "mode": args.mode,
-                       "rtol": p.rtol, "l2": "inputs exceed L2 (4 x %.0f MB)" % (N * 8 / 1e6),
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "cells": N, "mode": mode,
+                       "problems": len(probs), "rtol": p.rtol,
+                       "l2": ("flushed between steps (256 MB write)" if small else
+                              "inputs exceed L2 (4 x %.0f MB)" % (N * 8 / 1e6)),
                        "parallelism": f"replicas x{world}"},
             "time_to_tol_ms": t_solve * 1e3,
             "solve": {"iters": res["iters"], "outer_iters": res["outer_iters"], "vcycles": res["vcycles"],
                       "rel_residual": res["rel_residual"],
-                      "gdof_iter_per_s": N * res["iters"] / t_solve / 1e9},
+                      "gdof_iter_per_s": N * float(np.mean([r["iters"] for r in results])) / t_solve / 1e9},
             "fp64_jacobi_pcg": base["jacobi"], "fp64_mg_fcg": base["fp64-mg"],
             "speedup_vs_fp64_pcg": base["jacobi"]["time_to_tol_ms"] / (t_solve * 1e3),
-            "e2e": {"value": world * N * args.steps / e2e_t / 1e9, "unit": UNIT,
+            "e2e": {"value": job_value(N, args.steps, world, e2e_t), "unit": UNIT,
                     "h2d_bytes_per_step": 4 * 8 * N, "d2h_bytes_per_step": 8 * N},
-            "roofline": {"kernel": "k_apply32 (float32 stencil apply, row a2)", "bound": "hbm",
+            "roofline": {"kernel": "k_rbgs (float32 red-black Gauss-Seidel sweep, row a4)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "bytes_per_cell": bytes_per_cell, "launch_us": t_k * 1e6,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
-                         "fp64_apply_launch_us": t_k64 * 1e6},
+                         "traffic": traffic, "bytes_per_cell": sweep_bytes, "launch_us": t_sw * 1e6,
+                         "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
+                                         else "fallback 6800 GB/s (of fallback)"),
+                         "also": {"k_apply32z": {"bytes_per_cell": 16, "launch_us": t_ap * 1e6,
+                                                 "achieved": 16 * N / t_ap / 1e9,
+                                                 "frac": 16 * N / t_ap / 1e9 / peak},
+                                  "k_apply64": {"launch_us": t_k64 * 1e6,
+                                                "note": "float64 ALU-bound on GB300, not HBM-bound"}}},
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,
         }
+        if mode != "mixed":
+            line["mixed_no_network"] = base["mixed"]
         print(json.dumps(line), flush=True)
     g.close()
     if world > 1:
@@ -425,7 +495,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="convection256")
-    ap.add_argument("--mode", default="mixed")
+    ap.add_argument("--mode", default=None, help="solve mode (default: learned for learned256, else mixed)")
     ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--oracle-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -106,6 +106,10 @@ typedef struct {
     double inner_rtol;      /* relative reduction asked of each inner solve      */
     int    inner_max_iter;  /* inner iterations per refinement step               */
     int    check_every;     /* Krylov iterations between host convergence checks */
+    int    net_fallback;    /* LM_MIXED_LEARNED_FCG_IR: 1 = switch to the V-cycle
+                               when the network preconditioner stalls (inner
+                               residual above 1/2 after 4 iterations, or not
+                               finite); 0 = keep the network throughout        */
     void*  cuda_stream;     /* cudaStream_t for every kernel of the solve         */
 } lm_solve_opts;
 
@@ -118,8 +122,9 @@ typedef struct {
     double seconds;         /* device time of the solve (CUDA events)             */
 } lm_solve_result;
 
-/* Defaults: mode LM_MIXED_MG_IR, rtol 1e-8, max_iter 10000, nu1 = nu2 = 1,
- * inner_rtol 1e-3, inner_max_iter 30, max_outer 12, check_every 8. */
+/* Defaults: mode LM_MIXED_MG_IR, rtol 1e-8, max_iter 10000, nu1 = nu2 = 2,
+ * inner_rtol 1e-4, inner_max_iter 30, max_outer 12, check_every 8,
+ * net_fallback 1. */
 void lm_default_opts(lm_solve_opts* opts);
 
 /* ---- grid lifecycle ---------------------------------------------------- */
@@ -205,6 +210,16 @@ int  lm_apply(lm_grid* g, int prec, const void* x, void* y, double* dot_out, voi
  * the hierarchy from the current coefficients if needed. */
 int  lm_mg_vcycle(lm_grid* g, const float* r, float* z, int nu1, int nu2, void* stream);
 
+/* One red-black Gauss-Seidel sweep of the V-cycle's smoother on the finest
+ * level, float32: every cell of the first colour takes the value that
+ * solves its row of A x = f with its neighbours' values from x_in, then
+ * every cell of the second colour does the same with the updated values.
+ * order 0: red (i+j+k even) first, 1: black first.  x_in == NULL means
+ * x_in = 0.  x_in, f, x_out: float32 device vectors of N values; x_out
+ * must not overlap x_in or f.  LM_ERR_INVALID_ARG for an order other than
+ * 0/1 or a grid the hierarchy does not support (odd periodic extent). */
+int  lm_mg_sweep(lm_grid* g, const float* x_in, const float* f, float* x_out, int order, void* stream);
+
 /* Number of multigrid levels and the cell counts of level `level`
  * (n_out[3]); LM_ERR_INVALID_ARG past the coarsest level. */
 int  lm_mg_level_shape(lm_grid* g, int level, int64_t n_out[3], int* num_levels);
@@ -257,7 +272,8 @@ int  lm_net_features(lm_grid* g, const double* v, float* feat, double* scale, vo
  * z-chunk of every level shape is chosen by the autotuner (see
  * lm_autotune_set_cache).  The captured plan is cached per (grids,
  * coefficient versions, inner_max_iter, use_x0) and reused by later calls.
- * Requirements: 2D grids (ndim 2), nu1 = nu2 = 1, an exactly solved coarsest
+ * Requirements: 2D grids (ndim 2), nu1 = nu2 = 1 (lm_default_opts sets 2:
+ * set both to 1 for a batch), an exactly solved coarsest
  * level (grids whose halvings reach <= 64 cells), even periodic extents.
  * results[i] receives grid i's status, inner iterations (iters = vcycles),
  * refinement steps and final float64 relative residual; `seconds` is the

@@ -332,9 +332,33 @@ int solve_mg_pcg(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
     return g->st_host->rel <= o->rtol ? LM_OK : LM_ERR_NO_CONVERGENCE;
 }
 
+// Learned two-level preconditioner z = M_net r: a two-grid cycle whose
+// coarse-grid correction is replaced by the network,
+//   x1 = one red-black sweep on A x = r from x = 0,
+//   x2 = x1 + s NN(features(r - A x1)),
+//   z  = one black-red sweep from x2,
+// so the smoother removes the oscillatory error the network leaves and the
+// network supplies the smooth part a sweep cannot reach.  Uses the level-0
+// sweep buffers only (q32 holds A p of the flexible CG between iterations).
+int learned_precond(lm_grid* g, float* z, const float* r, cudaStream_t s) {
+    MgLevel& M = g->mg[0];
+    const Red red{g->part, g->scal, g->ctr};
+    const int rb = 0, br = 1;
+    float* x1 = sweep_chain(M, s, 1, &rb, nullptr, true, nullptr, nullptr, r, nullptr);
+    float* r1 = (x1 == M.xa) ? M.xb : M.xa;
+    launch_apply32(M.L, s, x1, r1, nullptr, red, -1, -1);
+    launch_axpy32(g->N, g->G, s, -1.f, r1, r, r1);                 // r1 = r - A x1
+    int rc = lm::net_apply<float, float>(g, r1, z, s);
+    if (rc) return rc;
+    launch_axpy32(g->N, g->G, s, 1.f, z, x1, r1);                  // x2 = x1 + net (into r1's buffer)
+    sweep_chain(M, s, 1, &br, r1, false, nullptr, nullptr, r, z);
+    CK(cudaGetLastError());
+    return LM_OK;
+}
+
 // Inner float32 flexible CG on A32 e = r (r overwritten).  Preconditioner:
-// the V-cycle, or (*use_net) the learned network z = s NN(features(r)); a
-// network step that leaves the inner residual above `stall` after 4
+// the V-cycle, or (*use_net) the learned two-level cycle above; a network
+// preconditioner that leaves the inner residual above 1/2 after 4
 // iterations, or returns a non-finite value, switches the rest of the solve
 // to the V-cycle (*use_net = false).
 int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, int* vcycles, bool* use_net) {
@@ -347,7 +371,7 @@ int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, in
     launch_dot32(g->N, g->G, s, g->r32, g->r32, red, 4, g->st_in);
     for (int it = 0; it < o->inner_max_iter; ++it) {
         if (use_net && *use_net) {
-            if ((rc = lm::net_apply<float, float>(g, g->r32, g->z32, s))) return rc;
+            if ((rc = learned_precond(g, g->z32, g->r32, s))) return rc;
         } else {
             vcycle(g, 0, g->z32, g->r32, o->nu1, o->nu2, s);
             ++*vcycles;
@@ -360,7 +384,8 @@ int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, in
         ++*iters;
         if ((rc = sync_state(g, g->st_in, s))) return rc;
         const double rel = g->st_host->rel;
-        if (use_net && *use_net && (!std::isfinite(rel) || g->st_host->status || (it >= 3 && rel > 0.5))) {
+        if (use_net && *use_net && (!std::isfinite(rel) || g->st_host->status ||
+                                    (o->net_fallback && it >= 3 && rel > 0.5))) {
             *use_net = false;                     // the network does not help here: V-cycle from now on
             if (!std::isfinite(rel) || g->st_host->status) return LM_OK;   // restart from the outer residual
         }
@@ -371,9 +396,11 @@ int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, in
 }
 
 // ---- mixed precision: float64 iterative refinement around float32 FCG+MG ----
-// learned = true: warm start x0 = s NN(features(f)) (kept only if it beats
-// x0 = 0) and the network as the inner preconditioner, with the V-cycle as
-// fallback.
+// learned = true: warm start x0 = alpha s NN(features(f)) with the
+// energy-optimal alpha (x0 = 0 when alpha <= 0; a warm start whose residual
+// exceeds ||f|| is kept, since its excess is oscillatory error the first
+// smoothing sweep removes) and the learned two-level preconditioner in the
+// inner flexible CG, with the V-cycle as fallback.
 int solve_mixed_ir(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res, bool learned) {
     cudaStream_t s = S(o->cuda_stream);
     int rc;
@@ -385,12 +412,13 @@ int solve_mixed_ir(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res, boo
     bool warm = false;
     if (use_net && !x0) {
         if ((rc = lm::net_apply<double, double>(g, g->f, g->x, s))) return rc;
+        launch_warm_scale(g->geo, g->G, s, op64(g), g->f, g->x, g->part);
         warm = true;
     }
     launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, !(x0 || warm), g->st, 1, nullptr);
     CK(cudaGetLastError());
     if ((rc = sync_state(g, g->st, s))) return rc;
-    if (warm && !(g->st_host->rel < 1.0)) {          // the warm start is worse than zero: drop it
+    if (warm && !std::isfinite(g->st_host->rel)) {   // a non-finite warm start: start from zero
         launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, 1, g->st, 1, nullptr);
         if ((rc = sync_state(g, g->st, s))) return rc;
     }
@@ -483,11 +511,12 @@ void lm_default_opts(lm_solve_opts* o) {
     o->max_iter = 10000;
     o->use_x0 = 0;
     o->max_outer = 12;
-    o->nu1 = 1;
-    o->nu2 = 1;
-    o->inner_rtol = 1e-3;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->inner_rtol = 1e-4;
     o->inner_max_iter = 30;
     o->check_every = 8;
+    o->net_fallback = 1;
     o->cuda_stream = nullptr;
 }
 
@@ -713,6 +742,18 @@ int lm_mg_vcycle(lm_grid* g, const float* r, float* z, int nu1, int nu2, void* s
     int rc = build_mg(g, s);
     if (rc) return rc;
     vcycle(g, 0, z, r, nu1, nu2, s);
+    CK(cudaGetLastError());
+    return LM_OK;
+}
+
+int lm_mg_sweep(lm_grid* g, const float* x_in, const float* f, float* x_out, int order, void* stream) {
+    if (!g || !f || !x_out || (order != 0 && order != 1) || x_out == x_in || x_out == f) return LM_ERR_INVALID_ARG;
+    if (!g->have_coefs) return LM_ERR_STATE;
+    if (!mg_supported(g)) return LM_ERR_INVALID_ARG;
+    cudaStream_t s = S(stream);
+    int rc = build_mg(g, s);
+    if (rc) return rc;
+    launch_rbgs(g->mg[0].L, s, x_in, nullptr, nullptr, 0, 0, 0, f, x_out, order, x_in == nullptr, false);
     CK(cudaGetLastError());
     return LM_OK;
 }

@@ -66,6 +66,13 @@ __global__ void __launch_bounds__(NT) k_fcg_update(int N, float* __restrict__ e,
     }
 }
 
+// out = y + alpha x (out may alias y)
+__global__ void __launch_bounds__(NT) k_axpy32(int N, float alpha, const float* __restrict__ x, const float* y,
+                                               float* out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        out[i] = __fmaf_rn(alpha, x[i], y[i]);
+}
+
 // Mean of the children's c~ and rho (coarse coefficients); one thread per coarse cell.
 __global__ void __launch_bounds__(256) k_coarsen(Lev32 F, Geo C, int hx, int hy, int hz, float* __restrict__ ct_c,
                                                  float* __restrict__ rho_c) {
@@ -196,6 +203,10 @@ void launch_dot32(int N, int G, cudaStream_t s, const float* a, const float* b, 
                   SolveState* fnorm_st) {
     count_launches(1);
     k_dot32<<<G, NT, 0, s>>>(N, a, b, red, slot, fnorm_st);
+}
+void launch_axpy32(int N, int G, cudaStream_t s, float alpha, const float* x, const float* y, float* out) {
+    count_launches(1);
+    k_axpy32<<<G, NT, 0, s>>>(N, alpha, x, y, out);
 }
 void launch_fcg_beta_p(int N, int G, cudaStream_t s, const float* z, float* p, const double* scal, int first) {
     count_launches(1);

@@ -268,6 +268,36 @@ __global__ void __launch_bounds__(NT) k_ir_residual(Geo g, Op64 op, const double
     }
 }
 
+// Warm-start scaling.  Along a direction x the A-norm error of alpha x is
+// least at alpha = f.x / x^T A x (then J(alpha x) = -(f.x)^2 / (2 x^T A x) <= J(0)
+// for the energy J(x) = x^T A x / 2 - f.x of the SPD system).  Pass 1: partial
+// x^T A x (slot 0) and f.x (slot 1).
+__global__ void __launch_bounds__(NT) k_warm_dots(Geo g, Op64 op, const double* __restrict__ f,
+                                                  const double* __restrict__ x, double* __restrict__ part) {
+    __shared__ double sm[64];
+    double acc[2] = {0.0, 0.0};
+    const int stride = gridDim.x * blockDim.x;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
+        const double xi = x[idx];
+        acc[0] += xi * apply64_at(idx, g, op, x);
+        acc[1] += f[idx] * xi;
+    }
+    write_partials<2>(acc, part, sm);
+}
+
+// Pass 2: x *= alpha, with alpha = 0 (drop the warm start) unless f.x > 0
+// and x^T A x > 0 are finite.  Every block forms alpha from the partials in
+// the same order.
+__global__ void __launch_bounds__(NT) k_warm_scale(int N, double* __restrict__ x, const double* part, int G) {
+    __shared__ double sm[32];
+    const double xax = reduce_partials(part, G, sm);
+    const double fx = reduce_partials(part + MAX_PARTIALS, G, sm);
+    const double alpha = (fx > 0.0 && xax > 0.0 && isfinite(fx) && isfinite(xax)) ? fx / xax : 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride)
+        x[idx] = alpha > 0.0 ? alpha * x[idx] : 0.0;
+}
+
 // x += e (float32 correction accumulated in float64)
 __global__ void __launch_bounds__(NT) k_ir_correct(int N, double* __restrict__ x, const float* __restrict__ e) {
     const int stride = gridDim.x * blockDim.x;
@@ -427,6 +457,12 @@ void launch_ir_residual(const Geo& g, int G, cudaStream_t s, const Op64& op, con
     k_ir_residual<<<G, NT, 0, s>>>(g, op, f, x, r32, part, zero_x);
     count_launches(1);
     k_finish_rel<<<1, NT, 0, s>>>(part, G, st, set_fnorm, hist_entry);
+}
+void launch_warm_scale(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* f, double* x,
+                       double* part) {
+    count_launches(2);
+    k_warm_dots<<<G, NT, 0, s>>>(g, op, f, x, part);
+    k_warm_scale<<<G, NT, 0, s>>>(g.N, x, part, G);
 }
 void launch_ir_correct(int N, int G, cudaStream_t s, double* x, const float* e) {
     count_launches(1);

@@ -63,6 +63,8 @@ void launch_pcg_iter(const PcgArgs& a, int G, cudaStream_t s, int k);
 void launch_true_residual(const PcgArgs& a, int G, cudaStream_t s);
 void launch_ir_residual(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* f, double* x,
                         float* r32, double* part, int zero_x, SolveState* st, int set_fnorm, double* hist_entry);
+void launch_warm_scale(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* f, double* x,
+                       double* part);
 void launch_ir_correct(int N, int G, cudaStream_t s, double* x, const float* e);
 void launch_reduce_rel(double* part, int G, cudaStream_t s, SolveState* st, double* hist_entry);
 void launch_reduce_slot(const double* part, int slot, int G, cudaStream_t s, double* out);
@@ -78,6 +80,7 @@ void launch_apply32(const Lev32& L, cudaStream_t s, const float* x, float* y, co
                     int slot_xy, int slot_xr);
 void launch_dot32(int N, int G, cudaStream_t s, const float* a, const float* b, const Red& red, int slot,
                   SolveState* fnorm_st);
+void launch_axpy32(int N, int G, cudaStream_t s, float alpha, const float* x, const float* y, float* out);
 void launch_fcg_beta_p(int N, int G, cudaStream_t s, const float* z, float* p, const double* scal, int first);
 void launch_fcg_update(int N, int G, cudaStream_t s, float* e, float* r, const float* p, const float* q,
                        const Red& red, SolveState* st);

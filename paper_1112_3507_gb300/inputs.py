@@ -91,12 +91,16 @@ class Problem:
 
 
 def smoothed_noise(shape3, bc, seed: int, sigma: float = 2.0, field: int = 1) -> np.ndarray:
-    """White N(0,1) noise, Gaussian-smoothed (sigma in cells, radius 4 sigma),
+    """White N(0,1) noise, Gaussian-smoothed (sigma in cells, radius 4 sigma;
+    sigma = 0 leaves it white),
     wrapped on periodic axes and mirrored on walled axes, minus its mean and
     scaled to unit 2-norm."""
     from scipy import ndimage
     nz, ny, nx = shape3
     w = normal(_stream(seed, field), nz * ny * nx).reshape(shape3)
+    if sigma <= 0.0:                       # white noise
+        w -= w.mean()
+        return w / np.linalg.norm(w)
     r = int(math.ceil(4 * sigma))
     t = np.arange(-r, r + 1, dtype=np.float64)
     g = np.exp(-0.5 * (t / sigma) ** 2)
@@ -194,14 +198,96 @@ def config_batch(count: int = 64, seed: int = 42, scale: int = 1):
             for b, s in enumerate(batch_specs(count, seed, scale=scale))]
 
 
+TRAIN_SIGMAS = (0.0, 0.5, 1.0, 2.0, 4.0)
+
+
 def config_training_2d(index: int, n: int = 256) -> Problem:
     """Member `index` of the learned-part family: n^2, contrast U[5,30],
-    Ma log-uniform [1e-3, 1e-1], 1% density noise."""
-    u = uniform01(_stream(index, 13), 2)
+    Ma log-uniform [1e-3, 1e-1], 1% density noise; the rhs smoothing width
+    is drawn from TRAIN_SIGMAS (0 = white noise), because the network also
+    preconditions inner residuals, which are rougher than the workloads'
+    sigma = 2 right-hand sides."""
+    u = uniform01(_stream(index, 13), 3)
     ma = 10.0 ** (-3.0 + 2.0 * u[0])
     contrast = 5.0 + 25.0 * u[1]
-    return make_problem(n, n, ma=ma, contrast=contrast, noise=0.01, seed=index, rtol=1e-8,
-                        name=f"train2d-{index}")
+    sigma = TRAIN_SIGMAS[min(int(u[2] * len(TRAIN_SIGMAS)), len(TRAIN_SIGMAS) - 1)]
+    p = make_problem(n, n, ma=ma, contrast=contrast, noise=0.01, seed=index, rtol=1e-8,
+                     name=f"train2d-{index}-sigma{sigma}")
+    p.f = smoothed_noise(p.shape3, p.bc, index, sigma=sigma).reshape(p.f.shape)
+    return p
+
+
+def semiconvection_profile(nz: int, a: float = 1.2, r_rho: float = 1.1, c_top: float = 0.2, g: float = 1.0,
+                           R: float = 1.0, substeps: int = 64):
+    """Two-component stratification over z in [0, 1] (Sec. 3.1): ideal gas
+    P = R rho T / mu (Eq. idealEOS) with mu = 1/(c/4 + (1-c)/1), a linear
+    temperature profile whose gradient is a times the adiabatic one of the
+    top layer (b(x) = a, Eq. bfac; c_P = 2.5 R / mu), and a stabilising
+    helium gradient with d ln mu / d ln P = R_rho (nabla - nabla_ad),
+    nabla_ad = 1 - 1/gamma.  Hydrostatic equilibrium d ln P/dz = -g mu/(R T)
+    is integrated downward from the top (P = 1, c = c_top) by classical RK4
+    with `substeps` steps per cell.  Returns cell-centre (T, mu, P)."""
+    mu_of = lambda c: 1.0 / (c / 4.0 + (1.0 - c))
+    mu_top = mu_of(c_top)
+    T_top = 1.0
+    dTdz = -a * g * mu_top / (2.5 * R)          # T rises downward
+    nabla_ad = 1.0 - 1.0 / GAMMA
+
+    def rhs(z, y):
+        lnP, lnmu = y
+        T = T_top + dTdz * (z - 1.0)
+        mu = math.exp(lnmu)
+        dlnP = -g * mu / (R * T)
+        nabla = (dTdz / T) / dlnP
+        return np.array([dlnP, r_rho * (nabla - nabla_ad) * dlnP])
+
+    h = 1.0 / nz
+    zc = (np.arange(nz) + 0.5) * h
+    out = np.zeros((nz, 2))
+    y = np.array([0.0, math.log(mu_top)])
+    z = 1.0
+    k = nz - 1
+    targets = list(zc[::-1])
+    dz = -h / substeps
+    # integrate from z = 1 down to each cell centre in turn
+    for zt in targets:
+        while z - zt > 1e-15:
+            step = max(dz, zt - z)
+            k1 = rhs(z, y)
+            k2 = rhs(z + step / 2, y + step / 2 * k1)
+            k3 = rhs(z + step / 2, y + step / 2 * k2)
+            k4 = rhs(z + step, y + step * k3)
+            y = y + step / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+            z += step
+        out[k] = y
+        k -= 1
+    T = T_top + dTdz * (zc - 1.0)
+    return T, np.exp(out[:, 1]), np.exp(out[:, 0])
+
+
+def config_semiconvection_3d(n: int = 512, seed: int = 7, perturb: float = 0.01, ma: float = 0.001) -> Problem:
+    """3D n^3 two-component semiconvection (Sec. 3.1, 3.3): the profile of
+    semiconvection_profile, seeded relative perturbations U(-1,1)*perturb of
+    T and of the helium fraction, rho = P mu / (R T), c_s^2 = gamma P / rho,
+    dt at Ma = 0.001, x,y periodic, z walls, rtol 1e-8."""
+    T0, mu0, P0 = semiconvection_profile(n)
+    shape = (n, n, n)
+    xiT = 2.0 * uniform01(_stream(seed, 21), n ** 3).reshape(shape) - 1.0
+    xic = 2.0 * uniform01(_stream(seed, 22), n ** 3).reshape(shape) - 1.0
+    T = T0[:, None, None] * (1.0 + perturb * xiT)
+    c0 = (1.0 - 1.0 / mu0) / 0.75                  # helium fraction of the profile
+    c = np.clip(c0[:, None, None] * (1.0 + perturb * xic), 0.0, 1.0)
+    mu = 1.0 / (c / 4.0 + (1.0 - c))
+    P = np.broadcast_to(P0[:, None, None], shape)
+    rho = P * mu / T
+    cs2 = GAMMA * P / rho
+    del xiT, xic, T, c, mu
+    h = 1.0 / n
+    bc = (BC_PERIODIC, BC_PERIODIC, BC_NEUMANN)
+    dt = dt_from_mach(h, cs2, ma)
+    f = smoothed_noise(shape, bc, seed)
+    return Problem(n=(n, n, n), ndim=3, h=(h, h, h), bc=bc, rho_old=rho, rho_new=rho.copy(), cs2=cs2, dt=dt,
+                   f=f, rtol=1e-8, name=f"semiconvection3d-{n}^3-Ma{ma}", ma=ma)
 
 
 def analytic_exp_problem(n: int, perturb: str | None = None, seed: int = 5, eps: float = 1e-2):

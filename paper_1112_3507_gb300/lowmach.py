@@ -39,7 +39,8 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("use_x0", ctypes.c_int), ("max_outer", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("inner_max_iter", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("check_every", ctypes.c_int), ("net_fallback", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class SolveResult(ctypes.Structure):
@@ -79,6 +80,7 @@ _SIGNATURES = {
     "lm_get_coefficients": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "lm_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "lm_mg_vcycle": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
+    "lm_mg_sweep": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P]),
     "lm_mg_level_shape": (ctypes.c_int, [_P, ctypes.c_int, _I64_3, ctypes.POINTER(ctypes.c_int)]),
     "lm_net_create": (ctypes.c_int, [_I4, ctypes.POINTER(_P)]),
     "lm_net_destroy": (None, [_P]),
@@ -294,6 +296,17 @@ class Grid:
             raise ValueError("lm_mg_vcycle takes device tensors")
         _check(lib().lm_mg_vcycle(self._g, rp, zp, nu1, nu2, _stream_ptr(stream)), "lm_mg_vcycle")
 
+    def mg_sweep(self, x_in, f, x_out, order=0, stream=None):
+        """One float32 red-black (order 0) or black-red (1) sweep on the finest level; x_in None = 0."""
+        fp, df, kf = _field(f, self.N, np.float32)
+        op, do, ko = _field(x_out, self.N, np.float32)
+        xp, dx = None, 1
+        if x_in is not None:
+            xp, dx, kx = _field(x_in, self.N, np.float32)
+        if not (df and do and dx):
+            raise ValueError("lm_mg_sweep takes device tensors")
+        _check(lib().lm_mg_sweep(self._g, xp, fp, op, int(order), _stream_ptr(stream)), "lm_mg_sweep")
+
     def load_network(self, path):
         return _check(lib().lm_load_network(self._g, str(path).encode()), "lm_load_network")
 
@@ -395,6 +408,8 @@ def batch_solve(grids, rtol=1e-8, stream=None, allow=(LM_OK,), **kw):
     lib().lm_default_opts(ctypes.byref(o))
     o.mode = MIXED_MG_IR
     o.rtol = float(rtol)
+    o.nu1 = o.nu2 = 1          # the batched schedule runs one sweep before and after each coarse correction
+    o.inner_rtol = 1e-3
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError(f"unknown solve option {k}")

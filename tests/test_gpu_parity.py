@@ -132,6 +132,34 @@ def test_vcycle_matches_oracle(name, nu):
     assert np.linalg.norm(z - z_ref) <= 1e-4 * np.linalg.norm(z_ref)
 
 
+@pytest.mark.parametrize("name", ["plain2d-64", "conv3d-16", "ragged3d-12x6x10", "ragged2d-37x50-walls",
+                                  "column-1x1x40"])
+@pytest.mark.parametrize("order", [0, 1])
+def test_sweep_matches_oracle(name, order):
+    """Row a4 smoother: one float32 red-black (or black-red) Gauss-Seidel
+    sweep, from zero and from a random x, vs the oracle's float64 sweep on
+    the float32-rounded coefficients."""
+    p = PROBLEMS[name]()
+    op = P.operator_from_problem(p)
+    ct32 = op.ct.astype(np.float32).astype(np.float64)
+    rho32 = p.rho_new.astype(np.float32).astype(np.float64)
+    level = OM.build_hierarchy(ct32, rho32, p.h, p.bc)[0]
+    rng = np.random.default_rng(10 + order)
+    f = rng.standard_normal(p.size).astype(np.float32)
+    x0 = rng.standard_normal(p.size).astype(np.float32)
+    tag = "RB" if order == 0 else "BR"
+    with _grid(p) as g:
+        fd, out = _dev(f, torch.float32), torch.empty(p.size, dtype=torch.float32, device="cuda")
+        for x in (None, x0):
+            xin = np.zeros(p.size) if x is None else x.astype(np.float64)
+            ref = OM.sweep(level, xin.reshape(p.shape3), f.astype(np.float64).reshape(p.shape3), tag).ravel()
+            g.mg_sweep(None if x is None else _dev(x, torch.float32), fd, out, order)
+            got = out.cpu().numpy().astype(np.float64)
+            assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+        with pytest.raises(lm().LowMachError):
+            g.mg_sweep(fd, fd, fd, order)
+
+
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_jacobi_pcg_parity(name):
     """Row a3: float64 Jacobi-PCG solution vs the oracle's direct solve."""

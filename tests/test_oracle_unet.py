@@ -87,3 +87,24 @@ def test_network_gradients_match_finite_differences():
 def test_param_count_of_the_default_network():
     n = sum(int(np.prod(s)) for _, s in U.param_shapes())
     assert 200_000 < n < 260_000
+
+
+def test_features_invariances():
+    """The network input is invariant to the scale of v (ch0 and s scale
+    out), the log-density channel vanishes for constant rho, and s is
+    linear in rms(v)."""
+    rng = np.random.default_rng(5)
+    H, W = 8, 12
+    v = rng.standard_normal((H, W))
+    rho = 1.0 + rng.random((H, W))
+    ct = 0.1 + rng.random((H, W))
+    x1, s1 = U.features(v, rho, ct, 0.125)
+    x2, s2 = U.features(3.0 * v, rho, ct, 0.125)
+    assert np.allclose(x1, x2) and s2 == pytest.approx(3.0 * s1)
+    assert np.sqrt(np.mean(x1[0, :, :, 0] ** 2)) == pytest.approx(1.0)
+    x3, _ = U.features(v, np.full((H, W), 2.5), ct, 0.125)
+    assert np.all(x3[0, :, :, 1] == 0.0)
+    # constant c~ rho h^2 = 1 gives a zero third channel
+    x4, s4 = U.features(v, np.full((H, W), 2.0), np.full((H, W), 0.5 * 64.0), 0.125)
+    assert np.allclose(x4[0, :, :, 2], 0.0)
+    assert s4 == pytest.approx(np.sqrt(np.mean(v * v)) / (32.0 + np.pi ** 2 / 2.0))
