@@ -106,10 +106,13 @@ typedef struct {
     double inner_rtol;      /* relative reduction asked of each inner solve      */
     int    inner_max_iter;  /* inner iterations per refinement step               */
     int    check_every;     /* Krylov iterations between host convergence checks */
-    int    net_fallback;    /* LM_MIXED_LEARNED_FCG_IR: 1 = switch to the V-cycle
-                               when the network preconditioner stalls (inner
+    int    net_precond;     /* LM_MIXED_LEARNED_FCG_IR, the inner preconditioner:
+                               0 = the V-cycle (the network gives the warm
+                               start only); 1 = the learned two-level cycle,
+                               replaced by the V-cycle when it stalls (inner
                                residual above 1/2 after 4 iterations, or not
-                               finite); 0 = keep the network throughout        */
+                               finite); 2 = the learned two-level cycle
+                               throughout                                      */
     void*  cuda_stream;     /* cudaStream_t for every kernel of the solve         */
 } lm_solve_opts;
 
@@ -124,7 +127,7 @@ typedef struct {
 
 /* Defaults: mode LM_MIXED_MG_IR, rtol 1e-8, max_iter 10000, nu1 = nu2 = 2,
  * inner_rtol 1e-4, inner_max_iter 30, max_outer 12, check_every 8,
- * net_fallback 1. */
+ * net_precond 0. */
 void lm_default_opts(lm_solve_opts* opts);
 
 /* ---- grid lifecycle ---------------------------------------------------- */

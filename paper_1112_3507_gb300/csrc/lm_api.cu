@@ -335,22 +335,27 @@ int solve_mg_pcg(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res) {
 // Learned two-level preconditioner z = M_net r: a two-grid cycle whose
 // coarse-grid correction is replaced by the network,
 //   x1 = one red-black sweep on A x = r from x = 0,
-//   x2 = x1 + s NN(features(r - A x1)),
-//   z  = one black-red sweep from x2,
-// so the smoother removes the oscillatory error the network leaves and the
-// network supplies the smooth part a sweep cannot reach.  Uses the level-0
-// sweep buffers only (q32 holds A p of the flexible CG between iterations).
+//   n  = s NN(features(r1)),  r1 = r - A x1,
+//   x2 = x1 + alpha n,  alpha = n.r1 / n^T A n  (0 unless both are positive),
+//   z  = one black-red sweep from x2.
+// alpha is the step along n that minimises the A-norm error of x2, so the
+// network correction never makes x2 worse than x1 in that norm; the sweeps
+// remove the oscillatory error the network leaves.  Buffers: the level-0
+// sweep buffers and the network's own output buffer (q32 holds A p of the
+// flexible CG between iterations).
 int learned_precond(lm_grid* g, float* z, const float* r, cudaStream_t s) {
     MgLevel& M = g->mg[0];
     const Red red{g->part, g->scal, g->ctr};
     const int rb = 0, br = 1;
+    constexpr int S_NAN = 5, S_NR = 6;              // scal slots: n^T A n, n.r1
     float* x1 = sweep_chain(M, s, 1, &rb, nullptr, true, nullptr, nullptr, r, nullptr);
     float* r1 = (x1 == M.xa) ? M.xb : M.xa;
     launch_apply32(M.L, s, x1, r1, nullptr, red, -1, -1);
     launch_axpy32(g->N, g->G, s, -1.f, r1, r, r1);                 // r1 = r - A x1
-    int rc = lm::net_apply<float, float>(g, r1, z, s);
+    int rc = lm::net_apply<float, float>(g, r1, z, s);              // n (into z)
     if (rc) return rc;
-    launch_axpy32(g->N, g->G, s, 1.f, z, x1, r1);                  // x2 = x1 + net (into r1's buffer)
+    launch_apply32(M.L, s, z, g->nny, r1, red, S_NAN, S_NR);        // n^T A n, n.r1
+    launch_axpy_ratio32(g->N, g->G, s, g->scal, S_NR, S_NAN, z, x1, r1);   // x2 (into r1's buffer)
     sweep_chain(M, s, 1, &br, r1, false, nullptr, nullptr, r, z);
     CK(cudaGetLastError());
     return LM_OK;
@@ -385,7 +390,7 @@ int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, in
         if ((rc = sync_state(g, g->st_in, s))) return rc;
         const double rel = g->st_host->rel;
         if (use_net && *use_net && (!std::isfinite(rel) || g->st_host->status ||
-                                    (o->net_fallback && it >= 3 && rel > 0.5))) {
+                                    (o->net_precond == 1 && it >= 3 && rel > 0.5))) {
             *use_net = false;                     // the network does not help here: V-cycle from now on
             if (!std::isfinite(rel) || g->st_host->status) return LM_OK;   // restart from the outer residual
         }
@@ -397,22 +402,29 @@ int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, in
 
 // ---- mixed precision: float64 iterative refinement around float32 FCG+MG ----
 // learned = true: warm start x0 = alpha s NN(features(f)) with the
-// energy-optimal alpha (x0 = 0 when alpha <= 0; a warm start whose residual
-// exceeds ||f|| is kept, since its excess is oscillatory error the first
-// smoothing sweep removes) and the learned two-level preconditioner in the
-// inner flexible CG, with the V-cycle as fallback.
+// energy-optimal alpha (x0 = 0 when alpha <= 0), smoothed by one symmetric
+// sweep pair; the inner preconditioner is the V-cycle, or (net_precond 1/2)
+// the learned two-level cycle.
 int solve_mixed_ir(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res, bool learned) {
     cudaStream_t s = S(o->cuda_stream);
     int rc;
     if ((rc = build_mg(g, s))) return rc;
     if ((rc = init_state(g, g->st, o->rtol, s))) return rc;
-    bool use_net = learned && lm::net_usable(g);
+    const bool have_net = learned && lm::net_usable(g);
+    bool use_net = have_net && o->net_precond != 0;     // network as the inner preconditioner
     const bool x0 = o->use_x0 && g->have_x0;
     if (x0) CK(cudaMemcpyAsync(g->x, g->x0, sizeof(double) * g->N, cudaMemcpyDeviceToDevice, s));
     bool warm = false;
-    if (use_net && !x0) {
+    if (have_net && !x0) {
+        // warm start: the scaled network guess, then one symmetric sweep pair
+        // on its residual, x += S(f - A x), which removes the oscillatory
+        // error a network leaves (large in the residual, small in the energy)
         if ((rc = lm::net_apply<double, double>(g, g->f, g->x, s))) return rc;
         launch_warm_scale(g->geo, g->G, s, op64(g), g->f, g->x, g->part);
+        launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, 0, g->st, 1, nullptr);
+        const int order[2] = {0, 1};
+        sweep_chain(g->mg[0], s, 2, order, nullptr, true, nullptr, nullptr, g->r32, g->e32);
+        launch_ir_correct(g->N, g->G, s, g->x, g->e32);
         warm = true;
     }
     launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, !(x0 || warm), g->st, 1, nullptr);
@@ -516,7 +528,7 @@ void lm_default_opts(lm_solve_opts* o) {
     o->inner_rtol = 1e-4;
     o->inner_max_iter = 30;
     o->check_every = 8;
-    o->net_fallback = 1;
+    o->net_precond = 0;
     o->cuda_stream = nullptr;
 }
 

@@ -73,6 +73,17 @@ __global__ void __launch_bounds__(NT) k_axpy32(int N, float alpha, const float* 
         out[i] = __fmaf_rn(alpha, x[i], y[i]);
 }
 
+// out = y + alpha x with alpha = scal[num] / scal[den] when both are positive
+// and finite, else alpha = 0 (the energy-optimal step along x, dropped when
+// x is not a descent direction)
+__global__ void __launch_bounds__(NT) k_axpy_ratio32(int N, const double* __restrict__ scal, int num, int den,
+                                                     const float* __restrict__ x, const float* y, float* out) {
+    const double a = scal[num], b = scal[den];
+    const float alpha = (a > 0.0 && b > 0.0 && isfinite(a) && isfinite(b)) ? (float)(a / b) : 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        out[i] = __fmaf_rn(alpha, x[i], y[i]);
+}
+
 // Mean of the children's c~ and rho (coarse coefficients); one thread per coarse cell.
 __global__ void __launch_bounds__(256) k_coarsen(Lev32 F, Geo C, int hx, int hy, int hz, float* __restrict__ ct_c,
                                                  float* __restrict__ rho_c) {
@@ -207,6 +218,11 @@ void launch_dot32(int N, int G, cudaStream_t s, const float* a, const float* b, 
 void launch_axpy32(int N, int G, cudaStream_t s, float alpha, const float* x, const float* y, float* out) {
     count_launches(1);
     k_axpy32<<<G, NT, 0, s>>>(N, alpha, x, y, out);
+}
+void launch_axpy_ratio32(int N, int G, cudaStream_t s, const double* scal, int num, int den, const float* x,
+                         const float* y, float* out) {
+    count_launches(1);
+    k_axpy_ratio32<<<G, NT, 0, s>>>(N, scal, num, den, x, y, out);
 }
 void launch_fcg_beta_p(int N, int G, cudaStream_t s, const float* z, float* p, const double* scal, int first) {
     count_launches(1);

@@ -81,6 +81,8 @@ void launch_apply32(const Lev32& L, cudaStream_t s, const float* x, float* y, co
 void launch_dot32(int N, int G, cudaStream_t s, const float* a, const float* b, const Red& red, int slot,
                   SolveState* fnorm_st);
 void launch_axpy32(int N, int G, cudaStream_t s, float alpha, const float* x, const float* y, float* out);
+void launch_axpy_ratio32(int N, int G, cudaStream_t s, const double* scal, int num, int den, const float* x,
+                         const float* y, float* out);
 void launch_fcg_beta_p(int N, int G, cudaStream_t s, const float* z, float* p, const double* scal, int first);
 void launch_fcg_update(int N, int G, cudaStream_t s, float* e, float* r, const float* p, const float* q,
                        const Red& red, SolveState* st);

@@ -39,7 +39,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("use_x0", ctypes.c_int), ("max_outer", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("inner_max_iter", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("net_fallback", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("net_precond", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p)]
 
 
