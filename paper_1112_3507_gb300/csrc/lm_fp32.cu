@@ -109,6 +109,151 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Lev32 F, Geo C, int hx, 
     resid_restrict_tile(F, C, hx, hy, hz, x, f, fc, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// ---- 3D red-black sweep on whole tiles: a staged, recomputed halo box -----
+//
+// For 3D levels whose extents are multiples of the 32 x 8 x KZ tile.  The
+// block owning the tile stages x_old and rho on the tile plus two cells in
+// every direction in shared memory (periodic axes wrapped; past a Neumann
+// wall x = 0 and rho = +inf, so that face's weight c2 / (rho_c + inf) is 0
+// and no wall test is needed later).  Phase 1 updates the FIRST colour on the
+// tile plus a one-cell halo in place -- a first-colour update reads only
+// second-colour neighbours, so in-place is the red-black sweep -- and the
+// halo values equal those the neighbouring blocks compute for their own
+// cells; phase 2 updates the second colour of the tile from them; phase 3
+// writes the tile in whole rows.  Work items enumerate only cells of the
+// colour being updated, so no lane idles on a colour test.  Wrapped global
+// offsets come from small per-block tables, so the staging and the f, c~
+// loads need no per-cell wrap logic.  Same operations in the same order as
+// rbgs_tile, so both kernels produce the same bits.
+template <int KZ, int FIRST, bool ZERO, bool PROLONG>
+__global__ void __launch_bounds__(256) k_rbgs_box(Lev32 L, const float* __restrict__ xin,
+                                                 const float* __restrict__ ec, Geo C, int hx, int hy, int hz,
+                                                 const float* __restrict__ f, float* __restrict__ xout) {
+    constexpr int TX = 32, TY = 8, SX = TX + 4, SY = TY + 4, SZ = KZ + 4, PL = SX * SY;
+    __shared__ float X[SZ * PL];
+    __shared__ float R[SZ * PL];
+    __shared__ int ox[SX], oy[SY], oz[SZ];       // wrapped offsets of staged coordinates, -1 past a wall
+    __shared__ int px[SX], py[SY], pz[SZ];       // parent offsets (PROLONG)
+    const Geo& g = L.g;
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int k0 = blockIdx.x * KZ, i0 = blockIdx.y * TX, j0 = blockIdx.z * TY;
+    const int sy = g.nx, sz = g.nx * g.ny;
+    auto wrap = [](int c, int n, int bc) -> int {     // c within two cells of [0, n), n >= 2
+        if (c < 0) return bc == LM_BC_PERIODIC ? c + n : -1;
+        if (c >= n) return bc == LM_BC_PERIODIC ? c - n : -1;
+        return c;
+    };
+    if (tid < SX) {
+        const int c = wrap(i0 - 2 + tid, g.nx, g.bcx);
+        ox[tid] = c;
+        px[tid] = c >> hx;
+    } else if (tid < SX + SY) {
+        const int c = wrap(j0 - 2 + tid - SX, g.ny, g.bcy);
+        oy[tid - SX] = c < 0 ? -1 : sy * c;
+        py[tid - SX] = C.nx * (c >> hy);
+    } else if (tid < SX + SY + SZ) {
+        const int c = wrap(k0 - 2 + tid - SX - SY, g.nz, g.bcz);
+        oz[tid - SX - SY] = c < 0 ? -1 : sz * c;
+        pz[tid - SX - SY] = C.nx * C.ny * (c >> hz);
+    }
+    __syncthreads();
+    // staging: each thread owns in-plane positions tid and tid + 256 of every
+    // staged plane, so its wrapped (i, j) offsets are computed once
+    {
+        int pos[2], base[2], pbase[2];
+        bool ok[2], use[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            pos[q] = tid + q * TX * TY;
+            use[q] = pos[q] < PL;
+            const int sj = use[q] ? pos[q] / SX : 0, si = use[q] ? pos[q] - sj * SX : 0;
+            const int a = ox[si], b = oy[sj];
+            ok[q] = use[q] && (a | b) >= 0;
+            base[q] = a + b;
+            pbase[q] = px[si] + py[sj];
+        }
+#pragma unroll 4
+        for (int sk = 0; sk < SZ; ++sk) {
+            const int c = oz[sk], pc = pz[sk];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (!use[q]) continue;
+                float xv = 0.f, rv = __int_as_float(0x7f800000);      // +inf
+                if (ok[q] && c >= 0) {
+                    const int idx = base[q] + c;
+                    rv = L.rho[idx];
+                    if (!ZERO) {
+                        xv = xin[idx];
+                        if (PROLONG) xv += ec[pbase[q] + pc];
+                    }
+                }
+                X[sk * PL + pos[q]] = xv;
+                R[sk * PL + pos[q]] = rv;
+            }
+        }
+    }
+    __syncthreads();
+
+    // Gauss-Seidel value at staged position s of the in-domain cell with global index idx
+    auto gs = [&](int s, int idx) -> float {
+        const float rc = R[s];
+        const float wxm = face32(rc, R[s - 1], L.c2x);
+        const float wxp = face32(rc, R[s + 1], L.c2x);
+        const float wym = face32(rc, R[s - SX], L.c2y);
+        const float wyp = face32(rc, R[s + SX], L.c2y);
+        const float wzm = face32(rc, R[s - PL], L.c2z);
+        const float wzp = face32(rc, R[s + PL], L.c2z);
+        const float d = L.ct[idx] + ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
+        float num = f[idx];
+        num = fmaf(wxm, X[s - 1], num);
+        num = fmaf(wxp, X[s + 1], num);
+        num = fmaf(wym, X[s - SX], num);
+        num = fmaf(wyp, X[s + SX], num);
+        num = fmaf(wzm, X[s - PL], num);
+        num = fmaf(wzp, X[s + PL], num);
+        return __fdividef(num, d);
+    };
+
+    // phase 1: first colour on the tile + one-cell halo (staged coordinates
+    // 1 .. S - 2); thread t < 17 * 10 owns the t-th first-colour cell of
+    // every halo-box plane
+    constexpr int BXH = (TX + 2) / 2, BY = TY + 2, BZ = KZ + 2;
+    const int par0 = (i0 + j0 + k0 + 1) & 1;                      // parity of staged cell (1, 1, 1)
+    if (tid < BXH * BY) {
+        const int m = tid % BXH, bj = tid / BXH;
+        const int b = oy[bj + 1];
+        const int ae = ox[2 * m + 1], ao = ox[2 * m + 2];          // the two x positions of the pair
+#pragma unroll 2
+        for (int bk = 0; bk < BZ; ++bk) {
+            const int odd = (FIRST + par0 + bj + bk) & 1;
+            const int s = ((bk + 1) * SY + bj + 1) * SX + 2 * m + odd + 1;
+            const int a = odd ? ao : ae, c = oz[bk + 1];
+            if ((a | b | c) >= 0) X[s] = gs(s, a + b + c);
+        }
+    }
+    __syncthreads();
+    // phase 2: second colour on the tile (staged coordinates 2 .. S - 3);
+    // the two halves of the block take alternate planes
+    {
+        const int half = tid >> 7, t = tid & 127;
+        const int m = t % (TX / 2), tj = t / (TX / 2);
+        const int part = (i0 + j0 + k0) & 1;
+        const int gbase = i0 + 2 * m + sy * (j0 + tj);
+#pragma unroll 2
+        for (int tk = half; tk < KZ; tk += 2) {
+            const int odd = (1 - FIRST + part + tj + tk) & 1;
+            const int s = ((tk + 2) * SY + tj + 2) * SX + 2 * m + odd + 2;
+            X[s] = gs(s, gbase + odd + sz * (k0 + tk));
+        }
+    }
+    __syncthreads();
+    // phase 3: the tile, row by row
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll 4
+    for (int tk = 0; tk < KZ; ++tk)
+        xout[(i0 + tx) + sy * (j0 + ty) + sz * (k0 + tk)] = X[((tk + 2) * SY + ty + 2) * SX + tx + 2];
+}
+
 template <int BX, int TY, bool HAS_Y, int FIRST, bool ZERO, bool PROLONG>
 __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, const float* __restrict__ xin,
                                                                    const float* __restrict__ ec, Geo C, int hx,
@@ -120,15 +265,18 @@ __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, con
 
 // Inverse of the coarsest level's matrix (n <= 64) by in-place Gauss-Jordan
 // elimination in float64 (SPD: no pivoting needed); one block.
-__global__ void __launch_bounds__(NT) k_coarse_inverse(Lev32 L, float* __restrict__ ainv) {
+__global__ void __launch_bounds__(1024) k_coarse_inverse(Lev32 L, float* __restrict__ ainv) {
+    // Gauss-Jordan inversion of the dense coarsest operator (n <= 64) in
+    // float64; block (64, 16): thread (j, r) owns column j of rows r, r+16, ...
     __shared__ double A[64 * 64];
     __shared__ double colk[64], rowk[64];
     const Geo& g = L.g;
     const int n = g.N;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = 0.0;
+    const int lin = threadIdx.x + 64 * threadIdx.y;
+    for (int e = lin; e < n * n; e += 1024) A[e] = 0.0;
     __syncthreads();
-    if (threadIdx.x < n) {
-        const int idx = threadIdx.x;
+    if (lin < n) {
+        const int idx = lin;
         const int i = idx % g.nx, j = (idx / g.nx) % g.ny, k = idx / (g.nx * g.ny);
         const double rc = L.rho[idx];
         double d = L.ct[idx];
@@ -150,25 +298,28 @@ __global__ void __launch_bounds__(NT) k_coarse_inverse(Lev32 L, float* __restric
         A[idx * n + idx] += d;
     }
     __syncthreads();
+    const int jc = threadIdx.x;
     for (int kk = 0; kk < n; ++kk) {
-        if (threadIdx.x < n) {
-            colk[threadIdx.x] = A[threadIdx.x * n + kk];
-            rowk[threadIdx.x] = A[kk * n + threadIdx.x];
+        // pivot row scaled by the pivot's inverse, and the pivot column
+        if (lin < n) {
+            const double ipiv = 1.0 / A[kk * n + kk];
+            colk[lin] = A[lin * n + kk];
+            rowk[lin] = lin == kk ? ipiv : A[kk * n + lin] * ipiv;
         }
         __syncthreads();
-        const double ipiv = 1.0 / rowk[kk];
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            const int i = e / n, j = e % n;
-            double v;
-            if (i == kk && j == kk) v = ipiv;
-            else if (i == kk) v = rowk[j] * ipiv;
-            else if (j == kk) v = -colk[i] * ipiv;
-            else v = A[e] - colk[i] * (rowk[j] * ipiv);
-            A[e] = v;
+        if (jc < n) {
+            const double rj = rowk[jc];
+            for (int i = threadIdx.y; i < n; i += 16) {
+                double v;
+                if (i == kk) v = rj;
+                else if (jc == kk) v = -colk[i] * rj;
+                else v = A[i * n + jc] - colk[i] * rj;
+                A[i * n + jc] = v;
+            }
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) ainv[e] = (float)A[e];
+    for (int e = lin; e < n * n; e += 1024) ainv[e] = (float)A[e];
 }
 
 __global__ void k_coarse_solve(int n, const float* __restrict__ ainv, const float* __restrict__ f,
@@ -251,7 +402,26 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
     const Geo& g = L.g;
     const Geo Cg = C ? C->g : g;
     count_launches(1);
-    if (g.ny > 1) {
+    if (g.ny > 1 && g.nx % 32 == 0 && g.ny % 8 == 0 && g.nz % 2 == 0) {
+        // whole 32 x 8 x KZ tiles: the halo-box sweep; KZ the largest of
+        // 8, 4, 2 that divides nz and still gives two blocks per SM (KZ = 8
+        // keeps the staged box within 48 KB of static shared memory)
+        const long long tiles = (long long)(g.nx / 32) * (g.ny / 8);
+        int KZ = (kz == 2 || kz == 4 || kz == 8) && g.nz % kz == 0 ? kz : 0;
+        if (!KZ) {
+            KZ = 8;
+            while (KZ > 2 && (g.nz % KZ || tiles * (g.nz / KZ) < 2 * 152)) KZ /= 2;
+        }
+        const dim3 grd(g.nz / KZ, g.nx / 32, g.ny / 8), blk(32, 8);
+#define LM_RBB(K, F, Z, P) k_rbgs_box<K, F, Z, P><<<grd, blk, 0, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout)
+#define LM_RBK(K)                                                              \
+    if (zero) { if (first) LM_RBB(K, 1, true, false); else LM_RBB(K, 0, true, false); }          \
+    else if (prolong) { if (first) LM_RBB(K, 1, false, true); else LM_RBB(K, 0, false, true); }  \
+    else { if (first) LM_RBB(K, 1, false, false); else LM_RBB(K, 0, false, false); }
+        if (KZ == 8) { LM_RBK(8) } else if (KZ == 4) { LM_RBK(4) } else { LM_RBK(2) }
+#undef LM_RBK
+#undef LM_RBB
+    } else if (g.ny > 1) {
         constexpr int BX = 32, TY = 8;
         const int tiles = hdiv(g.nx, 2 * BX) * hdiv(g.ny, TY);
         int KZ = kz;
@@ -287,7 +457,7 @@ void launch_rbgs(const Lev32& L, cudaStream_t s, const float* xin, const float* 
 }
 void launch_coarse_inverse(const Lev32& L, cudaStream_t s, float* ainv) {
     count_launches(1);
-    k_coarse_inverse<<<1, NT, 0, s>>>(L, ainv);
+    k_coarse_inverse<<<1, dim3(64, 16), 0, s>>>(L, ainv);
 }
 void launch_coarse_solve(int n, cudaStream_t s, const float* ainv, const float* f, float* x) {
     count_launches(1);

@@ -39,6 +39,10 @@ PROBLEMS = {
                                                    bc=(NEU, PER, NEU)),
     "ragged3d-12x6x10": lambda: I.make_problem(12, 10, 6, ma=0.02, contrast=12.0, noise=0.01, seed=4),
     "column-1x1x40": lambda: I.make_problem(1, 40, ma=0.1, contrast=5.0, seed=5),
+    # whole 32 x 8 tiles on the two finest levels: the halo-box sweep kernel
+    "box3d-64x16x24": lambda: I.make_problem(64, 24, 16, ma=0.01, contrast=20.0, noise=0.01, seed=7),
+    "box3d-walls-32x8x16": lambda: I.make_problem(32, 16, 8, ma=0.02, contrast=10.0, noise=0.01, seed=8,
+                                                  bc=(NEU, NEU, NEU)),
 }
 
 
@@ -108,7 +112,8 @@ def test_apply_fp32(name):
 
 
 @pytest.mark.parametrize("name,nu", [("plain2d-64", 1), ("conv3d-16", 1), ("ragged3d-12x6x10", 1),
-                                     ("ragged2d-37x50-walls", 1), ("conv3d-16", 2), ("plain2d-64", 3)])
+                                     ("ragged2d-37x50-walls", 1), ("conv3d-16", 2), ("plain2d-64", 3),
+                                     ("box3d-64x16x24", 1), ("box3d-64x16x24", 2), ("box3d-walls-32x8x16", 2)])
 def test_vcycle_matches_oracle(name, nu):
     """Row a4: one float32 V-cycle z = M r vs the oracle's float64 V-cycle on
     the same (float32-rounded) coefficients; same hierarchy."""
@@ -133,7 +138,7 @@ def test_vcycle_matches_oracle(name, nu):
 
 
 @pytest.mark.parametrize("name", ["plain2d-64", "conv3d-16", "ragged3d-12x6x10", "ragged2d-37x50-walls",
-                                  "column-1x1x40"])
+                                  "column-1x1x40", "box3d-64x16x24", "box3d-walls-32x8x16"])
 @pytest.mark.parametrize("order", [0, 1])
 def test_sweep_matches_oracle(name, order):
     """Row a4 smoother: one float32 red-black (or black-red) Gauss-Seidel
