@@ -109,149 +109,218 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Lev32 F, Geo C, int hx, 
     resid_restrict_tile(F, C, hx, hy, hz, x, f, fc, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// ---- 3D red-black sweep on whole tiles: a staged, recomputed halo box -----
+// ---- 3D red-black sweep on whole tiles: in-place z-march ------------------
 //
-// For 3D levels whose extents are multiples of the 32 x 8 x KZ tile.  The
-// block owning the tile stages x_old and rho on the tile plus two cells in
-// every direction in shared memory (periodic axes wrapped; past a Neumann
-// wall x = 0 and rho = +inf, so that face's weight c2 / (rho_c + inf) is 0
-// and no wall test is needed later).  Phase 1 updates the FIRST colour on the
-// tile plus a one-cell halo in place -- a first-colour update reads only
-// second-colour neighbours, so in-place is the red-black sweep -- and the
-// halo values equal those the neighbouring blocks compute for their own
-// cells; phase 2 updates the second colour of the tile from them; phase 3
-// writes the tile in whole rows.  Work items enumerate only cells of the
-// colour being updated, so no lane idles on a colour test.  Wrapped global
-// offsets come from small per-block tables, so the staging and the f, c~
-// loads need no per-cell wrap logic.  Same operations in the same order as
-// rbgs_tile, so both kernels produce the same bits.
-template <int KZ, int FIRST, bool ZERO, bool PROLONG>
-__global__ void __launch_bounds__(256) k_rbgs_box(Lev32 L, const float* __restrict__ xin,
-                                                 const float* __restrict__ ec, Geo C, int hx, int hy, int hz,
-                                                 const float* __restrict__ f, float* __restrict__ xout) {
-    constexpr int TX = 32, TY = 8, SX = TX + 4, SY = TY + 4, SZ = KZ + 4, PL = SX * SY;
-    __shared__ float X[SZ * PL];
-    __shared__ float R[SZ * PL];
-    __shared__ int ox[SX], oy[SY], oz[SZ];       // wrapped offsets of staged coordinates, -1 past a wall
-    __shared__ int px[SX], py[SY], pz[SZ];       // parent offsets (PROLONG)
+// For 3D levels whose nx, ny are multiples of the 32 x 8 tile.  A block owns
+// the columns of one tile over a chunk of KZ planes and marches up z with a
+// five-plane ring of x and rho staged on the tile plus two cells in x and y
+// (periodic axes wrapped; past a Neumann wall x = 0 and rho = +inf, so that
+// face's weight c2 / (rho_c + inf) is 0 and no wall test is needed).  At
+// step s the block (1) stores the staged plane s + 1 and issues the loads of
+// plane s + 2, (2) updates the FIRST colour of plane s on the tile plus a
+// one-cell halo in place -- a first-colour update reads only second-colour
+// neighbours, and the halo values equal those the neighbouring blocks
+// compute for their own cells -- (3) updates the second colour of plane
+// s - 1 on the tile, whose first-colour neighbours (planes s - 2 .. s) are
+// final, and (4) writes plane s - 2, final since step s - 1.  One sweep is
+// thus one pass over memory with no grid-wide barrier.  Work items
+// enumerate only cells of the colour being updated; wrapped in-plane
+// offsets are per-thread constants from small tables; f and c~ of the next
+// step's cells are loaded a step ahead.  Same operations in the same order
+// as rbgs_tile, so both kernels produce the same bits.
+template <int FIRST, bool ZERO, bool PROLONG>
+__global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restrict__ xin,
+                                                const float* __restrict__ ec, Geo C, int hx, int hy, int hz,
+                                                const float* __restrict__ f, float* __restrict__ xout, int KZ) {
+    constexpr int TX = 32, TY = 8, SX = TX + 4, SY = TY + 4, PL = SX * SY, NR = 5;
+    constexpr int NA = (TX + 2) / 2 * (TY + 2);         // first-colour cells per halo-box plane (170)
+    constexpr int NB = TX / 2 * TY;                      // second-colour cells per tile plane (128)
+    __shared__ float X[NR * PL];
+    __shared__ float R[NR * PL];
+    __shared__ int ox[SX], oy[SY], pxy[SX + SY];
     const Geo& g = L.g;
     const int tid = threadIdx.x + TX * threadIdx.y;
-    const int k0 = blockIdx.x * KZ, i0 = blockIdx.y * TX, j0 = blockIdx.z * TY;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int k0 = blockIdx.z * KZ, k1 = min(k0 + KZ, g.nz);
     const int sy = g.nx, sz = g.nx * g.ny;
-    auto wrap = [](int c, int n, int bc) -> int {     // c within two cells of [0, n), n >= 2
-        if (c < 0) return bc == LM_BC_PERIODIC ? c + n : -1;
-        if (c >= n) return bc == LM_BC_PERIODIC ? c - n : -1;
-        return c;
-    };
     if (tid < SX) {
-        const int c = wrap(i0 - 2 + tid, g.nx, g.bcx);
+        int c = i0 - 2 + tid;
+        if (c < 0) c = g.bcx == LM_BC_PERIODIC ? c + g.nx : -1;
+        else if (c >= g.nx) c = g.bcx == LM_BC_PERIODIC ? c - g.nx : -1;
         ox[tid] = c;
-        px[tid] = c >> hx;
+        pxy[tid] = c >> hx;
     } else if (tid < SX + SY) {
-        const int c = wrap(j0 - 2 + tid - SX, g.ny, g.bcy);
+        int c = j0 - 2 + tid - SX;
+        if (c < 0) c = g.bcy == LM_BC_PERIODIC ? c + g.ny : -1;
+        else if (c >= g.ny) c = g.bcy == LM_BC_PERIODIC ? c - g.ny : -1;
         oy[tid - SX] = c < 0 ? -1 : sy * c;
-        py[tid - SX] = C.nx * (c >> hy);
-    } else if (tid < SX + SY + SZ) {
-        const int c = wrap(k0 - 2 + tid - SX - SY, g.nz, g.bcz);
-        oz[tid - SX - SY] = c < 0 ? -1 : sz * c;
-        pz[tid - SX - SY] = C.nx * C.ny * (c >> hz);
+        pxy[tid] = C.nx * (c >> hy);
     }
     __syncthreads();
-    // staging: each thread owns in-plane positions tid and tid + 256 of every
-    // staged plane, so its wrapped (i, j) offsets are computed once
-    {
-        int pos[2], base[2], pbase[2];
-        bool ok[2], use[2];
+    // plane p (unwrapped) -> wrapped plane offset, -1 past a wall; and the
+    // parent plane offset (PROLONG)
+    auto zwrap = [&](int p) -> int { return ((p % g.nz) + g.nz) % g.nz; };
+    auto zoff = [&](int p) -> int {
+        if (p >= 0 && p < g.nz) return sz * p;
+        return g.bcz == LM_BC_PERIODIC ? sz * zwrap(p) : -1;
+    };
+    auto zpar = [&](int p) -> int { return C.nx * C.ny * (zwrap(p) >> hz); };
+
+    // staging positions of this thread: tid and tid + 256 of the 432 in-plane positions
+    int spos[2], sbase[2], spar[2];
+    bool sok[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        spos[q] = tid + q * TX * TY;
+        const bool use = spos[q] < PL;
+        const int sj = use ? spos[q] / SX : 0, si = use ? spos[q] - sj * SX : 0;
+        sok[q] = use && (ox[si] | oy[sj]) >= 0;
+        sbase[q] = ox[si] + oy[sj];
+        spar[q] = pxy[si] + pxy[SX + sj];
+        if (!use) spos[q] = -1;
+    }
+    float vx[2], vr[2];
+    auto fetch = [&](int zo, int zp) {                   // plane with offset zo -> registers
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            pos[q] = tid + q * TX * TY;
-            use[q] = pos[q] < PL;
-            const int sj = use[q] ? pos[q] / SX : 0, si = use[q] ? pos[q] - sj * SX : 0;
-            const int a = ox[si], b = oy[sj];
-            ok[q] = use[q] && (a | b) >= 0;
-            base[q] = a + b;
-            pbase[q] = px[si] + py[sj];
-        }
-#pragma unroll 4
-        for (int sk = 0; sk < SZ; ++sk) {
-            const int c = oz[sk], pc = pz[sk];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (!use[q]) continue;
-                float xv = 0.f, rv = __int_as_float(0x7f800000);      // +inf
-                if (ok[q] && c >= 0) {
-                    const int idx = base[q] + c;
-                    rv = L.rho[idx];
-                    if (!ZERO) {
-                        xv = xin[idx];
-                        if (PROLONG) xv += ec[pbase[q] + pc];
-                    }
+            vx[q] = 0.f;
+            vr[q] = __int_as_float(0x7f800000);          // +inf
+            if (sok[q] && zo >= 0) {
+                const int idx = sbase[q] + zo;
+                vr[q] = L.rho[idx];
+                if (!ZERO) {
+                    vx[q] = xin[idx];
+                    if (PROLONG) vx[q] += ec[spar[q] + zp];
                 }
-                X[sk * PL + pos[q]] = xv;
-                R[sk * PL + pos[q]] = rv;
             }
         }
-    }
-    __syncthreads();
+    };
+    auto store = [&](int o) {                            // registers -> ring slot at offset o
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            if (spos[q] >= 0) {
+                X[o + spos[q]] = vx[q];
+                R[o + spos[q]] = vr[q];
+            }
+    };
 
-    // Gauss-Seidel value at staged position s of the in-domain cell with global index idx
-    auto gs = [&](int s, int idx) -> float {
-        const float rc = R[s];
-        const float wxm = face32(rc, R[s - 1], L.c2x);
-        const float wxp = face32(rc, R[s + 1], L.c2x);
-        const float wym = face32(rc, R[s - SX], L.c2y);
-        const float wyp = face32(rc, R[s + SX], L.c2y);
-        const float wzm = face32(rc, R[s - PL], L.c2z);
-        const float wzp = face32(rc, R[s + PL], L.c2z);
-        const float d = L.ct[idx] + ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
-        float num = f[idx];
-        num = fmaf(wxm, X[s - 1], num);
-        num = fmaf(wxp, X[s + 1], num);
-        num = fmaf(wym, X[s - SX], num);
-        num = fmaf(wyp, X[s + SX], num);
-        num = fmaf(wzm, X[s - PL], num);
-        num = fmaf(wzp, X[s + PL], num);
+    // Gauss-Seidel value at in-plane staged position e of the plane in ring
+    // slot s0 (slots sm, sp: the planes below and above)
+    auto gs = [&](int e, int sm, int s0, int sp, float fv, float cv) -> float {
+        const int c = s0 + e;
+        const float rc = R[c];
+        const float wxm = face32(rc, R[c - 1], L.c2x);
+        const float wxp = face32(rc, R[c + 1], L.c2x);
+        const float wym = face32(rc, R[c - SX], L.c2y);
+        const float wyp = face32(rc, R[c + SX], L.c2y);
+        const float wzm = face32(rc, R[sm + e], L.c2z);
+        const float wzp = face32(rc, R[sp + e], L.c2z);
+        const float d = cv + ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
+        float num = fv;
+        num = fmaf(wxm, X[c - 1], num);
+        num = fmaf(wxp, X[c + 1], num);
+        num = fmaf(wym, X[c - SX], num);
+        num = fmaf(wyp, X[c + SX], num);
+        num = fmaf(wzm, X[sm + e], num);
+        num = fmaf(wzp, X[sp + e], num);
         return __fdividef(num, d);
     };
 
-    // phase 1: first colour on the tile + one-cell halo (staged coordinates
-    // 1 .. S - 2); thread t < 17 * 10 owns the t-th first-colour cell of
-    // every halo-box plane
-    constexpr int BXH = (TX + 2) / 2, BY = TY + 2, BZ = KZ + 2;
-    const int par0 = (i0 + j0 + k0 + 1) & 1;                      // parity of staged cell (1, 1, 1)
-    if (tid < BXH * BY) {
-        const int m = tid % BXH, bj = tid / BXH;
-        const int b = oy[bj + 1];
-        const int ae = ox[2 * m + 1], ao = ox[2 * m + 2];          // the two x positions of the pair
-#pragma unroll 2
-        for (int bk = 0; bk < BZ; ++bk) {
-            const int odd = (FIRST + par0 + bj + bk) & 1;
-            const int s = ((bk + 1) * SY + bj + 1) * SX + 2 * m + odd + 1;
-            const int a = odd ? ao : ae, c = oz[bk + 1];
-            if ((a | b | c) >= 0) X[s] = gs(s, a + b + c);
-        }
-    }
-    __syncthreads();
-    // phase 2: second colour on the tile (staged coordinates 2 .. S - 3);
-    // the two halves of the block take alternate planes
+    // first-colour task of this thread (tid < 170): pair am of halo-box row
+    // abj; its cell alternates between the two x positions of the pair
+    const bool hasA = tid < NA;
+    const int am = hasA ? tid % ((TX + 2) / 2) : 0, abj = hasA ? tid / ((TX + 2) / 2) : 0;
+    const int aeE = (abj + 1) * SX + 2 * am + 1, aoy = oy[abj + 1];
+    const int aoE = ox[2 * am + 1], aoO = ox[2 * am + 2];
+    const int apar = (FIRST + i0 + j0 + abj) & 1;              // odd-x on plane p iff (apar + p) & 1
+    // second-colour task (tid < 128): pair bm of tile row btj
+    const bool hasB = tid < NB;
+    const int bm = tid % (TX / 2), btj = (tid / (TX / 2)) % TY;
+    const int beE = (btj + 2) * SX + 2 * bm + 2;
+    const int bidxE = i0 + 2 * bm + sy * (j0 + btj);
+    const int bpar = (1 - FIRST + i0 + j0 + btj) & 1;
+    const int wpos = (threadIdx.y + 2) * SX + threadIdx.x + 2;
+    const int wbase = (i0 + threadIdx.x) + sy * (j0 + threadIdx.y);
+
+    // ring slot offsets of planes p - 2 .. p + 2 at step p (rotated each step)
+    int om2 = 0 * PL, om1 = 1 * PL, o0 = 2 * PL, op1 = 3 * PL, op2 = 4 * PL;
+    // wrapped offsets of planes p, p + 1, p + 2 (shift register)
+    int z0 = zoff(k0 - 1), z1 = zoff(k0), z2 = zoff(k0 + 1);
+    // prologue: planes k0 - 2, k0 - 1 staged; plane k0 in registers
+    fetch(zoff(k0 - 2), PROLONG ? zpar(k0 - 2) : 0);
+    store(om1);                          // plane k0 - 2 = p - 1 at the first step p = k0 - 1
+    fetch(z0, PROLONG ? zpar(k0 - 1) : 0);
+    store(o0);
+    fetch(z1, PROLONG ? zpar(k0) : 0);
+    // f, c~ of the first-colour cell of plane p (loaded a step ahead)
+    float fa = 0.f, ca = 1.f, fb = 0.f, cb = 1.f;
+    bool okA = false;
+    int eA = 0;
     {
-        const int half = tid >> 7, t = tid & 127;
-        const int m = t % (TX / 2), tj = t / (TX / 2);
-        const int part = (i0 + j0 + k0) & 1;
-        const int gbase = i0 + 2 * m + sy * (j0 + tj);
-#pragma unroll 2
-        for (int tk = half; tk < KZ; tk += 2) {
-            const int odd = (1 - FIRST + part + tj + tk) & 1;
-            const int s = ((tk + 2) * SY + tj + 2) * SX + 2 * m + odd + 2;
-            X[s] = gs(s, gbase + odd + sz * (k0 + tk));
+        const int p = k0 - 1, odd = (apar + p) & 1;
+        const int a = odd ? aoO : aoE;
+        okA = hasA && (a | aoy | z0) >= 0;
+        eA = aeE + odd;
+        if (okA) {
+            fa = f[a + aoy + z0];
+            ca = L.ct[a + aoy + z0];
         }
     }
-    __syncthreads();
-    // phase 3: the tile, row by row
-    const int tx = threadIdx.x, ty = threadIdx.y;
-#pragma unroll 4
-    for (int tk = 0; tk < KZ; ++tk)
-        xout[(i0 + tx) + sy * (j0 + ty) + sz * (k0 + tk)] = X[((tk + 2) * SY + ty + 2) * SX + tx + 2];
+    bool okB = false;
+    int eB = 0;
+    for (int p = k0 - 1; p <= k1 + 1; ++p) {
+        // (1) stage plane p + 1, fetch plane p + 2
+        if (p <= k1) store(op1);
+        if (p + 1 <= k1) fetch(z2, PROLONG ? zpar(p + 2) : 0);
+        const float fA = fa, cA = ca, fB = fb, cB = cb;
+        const bool doA = okA && p <= k1, doB = okB;
+        const int eAc = eA, eBc = eB;
+        // f, c~ of the second-colour cell of plane p (used at step p + 1)
+        {
+            const int odd = (bpar + p) & 1;
+            okB = hasB && p >= k0 && p < k1;
+            eB = beE + odd;
+            if (okB) {
+                const int idx = bidxE + odd + sz * p;
+                fb = f[idx];
+                cb = L.ct[idx];
+            }
+        }
+        __syncthreads();
+        // (2) first colour on plane p (tile + halo)
+        if (doA) X[o0 + eAc] = gs(eAc, om1, o0, op1, fA, cA);
+        // f, c~ of the first-colour cell of plane p + 1
+        {
+            const int odd = (apar + p + 1) & 1;
+            const int a = odd ? aoO : aoE;
+            okA = hasA && p + 1 <= k1 && (a | aoy | z1) >= 0;
+            eA = aeE + odd;
+            if (okA) {
+                fa = f[a + aoy + z1];
+                ca = L.ct[a + aoy + z1];
+            }
+        }
+        __syncthreads();
+        // (3) second colour on plane p - 1 (tile)
+        if (doB) X[om1 + eBc] = gs(eBc, om2, om1, o0, fB, cB);
+        // (4) write plane p - 2
+        if (p - 2 >= k0) xout[wbase + sz * (p - 2)] = X[om2 + wpos];
+        // rotate to step p + 1
+        const int t = om2;
+        om2 = om1;
+        om1 = o0;
+        o0 = op1;
+        op1 = op2;
+        op2 = t;
+        z0 = z1;
+        z1 = z2;
+        {   // offset of plane p + 3 (p + 3 <= nz + 4: at most two wraps)
+            int c = p + 3;
+            if (c >= g.nz) c -= g.nz;
+            if (c >= g.nz) c -= g.nz;
+            z2 = (p + 3 < g.nz || g.bcz == LM_BC_PERIODIC) && c >= 0 && c < g.nz ? sz * c : -1;
+        }
+    }
 }
 
 template <int BX, int TY, bool HAS_Y, int FIRST, bool ZERO, bool PROLONG>
@@ -402,25 +471,19 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
     const Geo& g = L.g;
     const Geo Cg = C ? C->g : g;
     count_launches(1);
-    if (g.ny > 1 && g.nx % 32 == 0 && g.ny % 8 == 0 && g.nz % 2 == 0) {
-        // whole 32 x 8 x KZ tiles: the halo-box sweep; KZ the largest of
-        // 8, 4, 2 that divides nz and still gives two blocks per SM (KZ = 8
-        // keeps the staged box within 48 KB of static shared memory)
+    if (g.ny > 1 && g.nx % 32 == 0 && g.ny % 8 == 0 && g.nz >= 2) {
+        // whole 32 x 8 tiles: the in-place z-march; KZ planes per block, the
+        // largest of 64, 32, 16, 8 that still gives eight blocks per SM
         const long long tiles = (long long)(g.nx / 32) * (g.ny / 8);
-        int KZ = (kz == 2 || kz == 4 || kz == 8) && g.nz % kz == 0 ? kz : 0;
-        if (!KZ) {
-            KZ = 8;
-            while (KZ > 2 && (g.nz % KZ || tiles * (g.nz / KZ) < 2 * 152)) KZ /= 2;
-        }
-        const dim3 grd(g.nz / KZ, g.nx / 32, g.ny / 8), blk(32, 8);
-#define LM_RBB(K, F, Z, P) k_rbgs_box<K, F, Z, P><<<grd, blk, 0, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout)
-#define LM_RBK(K)                                                              \
-    if (zero) { if (first) LM_RBB(K, 1, true, false); else LM_RBB(K, 0, true, false); }          \
-    else if (prolong) { if (first) LM_RBB(K, 1, false, true); else LM_RBB(K, 0, false, true); }  \
-    else { if (first) LM_RBB(K, 1, false, false); else LM_RBB(K, 0, false, false); }
-        if (KZ == 8) { LM_RBK(8) } else if (KZ == 4) { LM_RBK(4) } else { LM_RBK(2) }
-#undef LM_RBK
-#undef LM_RBB
+        int KZ = kz > 0 ? kz : 64;
+        if (kz <= 0)
+            while (KZ > 8 && tiles * hdiv(g.nz, KZ) < 8 * 152) KZ /= 2;
+        const dim3 grd(g.nx / 32, g.ny / 8, hdiv(g.nz, KZ)), blk(32, 8);
+#define LM_RBZ(F, Z, P) k_rbgs_zm<F, Z, P><<<grd, blk, 0, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout, KZ)
+        if (zero) { if (first) LM_RBZ(1, true, false); else LM_RBZ(0, true, false); }
+        else if (prolong) { if (first) LM_RBZ(1, false, true); else LM_RBZ(0, false, true); }
+        else { if (first) LM_RBZ(1, false, false); else LM_RBZ(0, false, false); }
+#undef LM_RBZ
     } else if (g.ny > 1) {
         constexpr int BX = 32, TY = 8;
         const int tiles = hdiv(g.nx, 2 * BX) * hdiv(g.ny, TY);
