@@ -128,18 +128,23 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Lev32 F, Geo C, int hx, 
 // offsets are per-thread constants from small tables; f and c~ of the next
 // step's cells are loaded a step ahead.  Same operations in the same order
 // as rbgs_tile, so both kernels produce the same bits.
-template <int FIRST, bool ZERO, bool PROLONG>
+template <int TX, int FIRST, bool ZERO, bool PROLONG>
 __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restrict__ xin,
                                                 const float* __restrict__ ec, Geo C, int hx, int hy, int hz,
                                                 const float* __restrict__ f, float* __restrict__ xout, int KZ) {
-    constexpr int TX = 32, TY = 8, SX = TX + 4, SY = TY + 4, PL = SX * SY, NR = 5;
-    constexpr int NA = (TX + 2) / 2 * (TY + 2);         // first-colour cells per halo-box plane (170)
-    constexpr int NB = TX / 2 * TY;                      // second-colour cells per tile plane (128)
+    constexpr int NT2 = 256, TY = 8, SX = TX + 4, SY = TY + 4, PL = SX * SY, NR = 5;
+    constexpr int AW = (TX + 2) / 2;                     // first-colour cells per halo-box row
+    constexpr int NA = AW * (TY + 2);                    // ... per halo-box plane (170 / 330)
+    constexpr int NB = TX / 2 * TY;                      // second-colour cells per tile plane (128 / 256)
+    constexpr int QS = (PL + NT2 - 1) / NT2;             // staged positions per thread
+    constexpr int QA = (NA + NT2 - 1) / NT2;             // first-colour tasks per thread
+    constexpr int QW = TX * TY / NT2;                    // written cells per thread
+    static_assert(NB <= NT2 && SX + SY <= NT2 && QW * NT2 == TX * TY, "tile does not fit the block");
     __shared__ float X[NR * PL];
     __shared__ float R[NR * PL];
     __shared__ int ox[SX], oy[SY], pxy[SX + SY];
     const Geo& g = L.g;
-    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int k0 = blockIdx.z * KZ, k1 = min(k0 + KZ, g.nz);
     const int sy = g.nx, sz = g.nx * g.ny;
@@ -166,12 +171,12 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
     };
     auto zpar = [&](int p) -> int { return C.nx * C.ny * (zwrap(p) >> hz); };
 
-    // staging positions of this thread: tid and tid + 256 of the 432 in-plane positions
-    int spos[2], sbase[2], spar[2];
-    bool sok[2];
+    // staging positions of this thread: tid + 256 q of the in-plane positions
+    int spos[QS], sbase[QS], spar[QS];
+    bool sok[QS];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        spos[q] = tid + q * TX * TY;
+    for (int q = 0; q < QS; ++q) {
+        spos[q] = tid + q * NT2;
         const bool use = spos[q] < PL;
         const int sj = use ? spos[q] / SX : 0, si = use ? spos[q] - sj * SX : 0;
         sok[q] = use && (ox[si] | oy[sj]) >= 0;
@@ -179,10 +184,10 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
         spar[q] = pxy[si] + pxy[SX + sj];
         if (!use) spos[q] = -1;
     }
-    float vx[2], vr[2];
+    float vx[QS], vr[QS];
     auto fetch = [&](int zo, int zp) {                   // plane with offset zo -> registers
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < QS; ++q) {
             vx[q] = 0.f;
             vr[q] = __int_as_float(0x7f800000);          // +inf
             if (sok[q] && zo >= 0) {
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
     };
     auto store = [&](int o) {                            // registers -> ring slot at offset o
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+        for (int q = 0; q < QS; ++q)
             if (spos[q] >= 0) {
                 X[o + spos[q]] = vx[q];
                 R[o + spos[q]] = vr[q];
@@ -226,21 +231,35 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
         return __fdividef(num, d);
     };
 
-    // first-colour task of this thread (tid < 170): pair am of halo-box row
-    // abj; its cell alternates between the two x positions of the pair
-    const bool hasA = tid < NA;
-    const int am = hasA ? tid % ((TX + 2) / 2) : 0, abj = hasA ? tid / ((TX + 2) / 2) : 0;
-    const int aeE = (abj + 1) * SX + 2 * am + 1, aoy = oy[abj + 1];
-    const int aoE = ox[2 * am + 1], aoO = ox[2 * am + 2];
-    const int apar = (FIRST + i0 + j0 + abj) & 1;              // odd-x on plane p iff (apar + p) & 1
-    // second-colour task (tid < 128): pair bm of tile row btj
+    // first-colour tasks of this thread: task tid + 256 u is pair am of
+    // halo-box row abj; its cell alternates between the pair's two x positions
+    bool hasA[QA];
+    int aeE[QA], aoy[QA], aoE[QA], aoO[QA], apar[QA];
+#pragma unroll
+    for (int u = 0; u < QA; ++u) {
+        const int ta = tid + u * NT2;
+        hasA[u] = ta < NA;
+        const int am = hasA[u] ? ta % AW : 0, abj = hasA[u] ? ta / AW : 0;
+        aeE[u] = (abj + 1) * SX + 2 * am + 1;
+        aoy[u] = oy[abj + 1];
+        aoE[u] = ox[2 * am + 1];
+        aoO[u] = ox[2 * am + 2];
+        apar[u] = (FIRST + i0 + j0 + abj) & 1;           // odd-x on plane p iff (apar + p) & 1
+    }
+    // second-colour task (tid < NB): pair bm of tile row btj
     const bool hasB = tid < NB;
     const int bm = tid % (TX / 2), btj = (tid / (TX / 2)) % TY;
     const int beE = (btj + 2) * SX + 2 * bm + 2;
     const int bidxE = i0 + 2 * bm + sy * (j0 + btj);
     const int bpar = (1 - FIRST + i0 + j0 + btj) & 1;
-    const int wpos = (threadIdx.y + 2) * SX + threadIdx.x + 2;
-    const int wbase = (i0 + threadIdx.x) + sy * (j0 + threadIdx.y);
+    // written cells: tid + 256 v of the tile plane
+    int wpos[QW], wbase[QW];
+#pragma unroll
+    for (int v = 0; v < QW; ++v) {
+        const int w = tid + v * NT2, wx = w % TX, wy = w / TX;
+        wpos[v] = (wy + 2) * SX + wx + 2;
+        wbase[v] = (i0 + wx) + sy * (j0 + wy);
+    }
 
     // ring slot offsets of planes p - 2 .. p + 2 at step p (rotated each step)
     int om2 = 0 * PL, om1 = 1 * PL, o0 = 2 * PL, op1 = 3 * PL, op2 = 4 * PL;
@@ -248,33 +267,50 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
     int z0 = zoff(k0 - 1), z1 = zoff(k0), z2 = zoff(k0 + 1);
     // prologue: planes k0 - 2, k0 - 1 staged; plane k0 in registers
     fetch(zoff(k0 - 2), PROLONG ? zpar(k0 - 2) : 0);
-    store(om1);                          // plane k0 - 2 = p - 1 at the first step p = k0 - 1
+    store(om1);
     fetch(z0, PROLONG ? zpar(k0 - 1) : 0);
     store(o0);
     fetch(z1, PROLONG ? zpar(k0) : 0);
-    // f, c~ of the first-colour cell of plane p (loaded a step ahead)
-    float fa = 0.f, ca = 1.f, fb = 0.f, cb = 1.f;
-    bool okA = false;
-    int eA = 0;
-    {
-        const int p = k0 - 1, odd = (apar + p) & 1;
-        const int a = odd ? aoO : aoE;
-        okA = hasA && (a | aoy | z0) >= 0;
-        eA = aeE + odd;
-        if (okA) {
-            fa = f[a + aoy + z0];
-            ca = L.ct[a + aoy + z0];
+    // f, c~ of the first-colour cells of plane p (loaded a step ahead)
+    float fa[QA], ca[QA];
+    bool okA[QA];
+    int eA[QA];
+    auto load_a = [&](int p, int zo, bool in_chunk) {
+#pragma unroll
+        for (int u = 0; u < QA; ++u) {
+            const int odd = (apar[u] + p) & 1;
+            const int a = odd ? aoO[u] : aoE[u];
+            okA[u] = hasA[u] && in_chunk && (a | aoy[u] | zo) >= 0;
+            eA[u] = aeE[u] + odd;
+            fa[u] = 0.f;
+            ca[u] = 1.f;
+            if (okA[u]) {
+                fa[u] = f[a + aoy[u] + zo];
+                ca[u] = L.ct[a + aoy[u] + zo];
+            }
         }
-    }
+    };
+    load_a(k0 - 1, z0, true);
+    float fb = 0.f, cb = 1.f;
     bool okB = false;
     int eB = 0;
     for (int p = k0 - 1; p <= k1 + 1; ++p) {
         // (1) stage plane p + 1, fetch plane p + 2
         if (p <= k1) store(op1);
         if (p + 1 <= k1) fetch(z2, PROLONG ? zpar(p + 2) : 0);
-        const float fA = fa, cA = ca, fB = fb, cB = cb;
-        const bool doA = okA && p <= k1, doB = okB;
-        const int eAc = eA, eBc = eB;
+        float fA[QA], cA[QA];
+        bool doA[QA];
+        int eAc[QA];
+#pragma unroll
+        for (int u = 0; u < QA; ++u) {
+            fA[u] = fa[u];
+            cA[u] = ca[u];
+            doA[u] = okA[u] && p <= k1;
+            eAc[u] = eA[u];
+        }
+        const float fB = fb, cB = cb;
+        const bool doB = okB;
+        const int eBc = eB;
         // f, c~ of the second-colour cell of plane p (used at step p + 1)
         {
             const int odd = (bpar + p) & 1;
@@ -288,23 +324,18 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
         }
         __syncthreads();
         // (2) first colour on plane p (tile + halo)
-        if (doA) X[o0 + eAc] = gs(eAc, om1, o0, op1, fA, cA);
-        // f, c~ of the first-colour cell of plane p + 1
-        {
-            const int odd = (apar + p + 1) & 1;
-            const int a = odd ? aoO : aoE;
-            okA = hasA && p + 1 <= k1 && (a | aoy | z1) >= 0;
-            eA = aeE + odd;
-            if (okA) {
-                fa = f[a + aoy + z1];
-                ca = L.ct[a + aoy + z1];
-            }
-        }
+#pragma unroll
+        for (int u = 0; u < QA; ++u)
+            if (doA[u]) X[o0 + eAc[u]] = gs(eAc[u], om1, o0, op1, fA[u], cA[u]);
+        load_a(p + 1, z1, p + 1 <= k1);                  // for the next step
         __syncthreads();
         // (3) second colour on plane p - 1 (tile)
         if (doB) X[om1 + eBc] = gs(eBc, om2, om1, o0, fB, cB);
         // (4) write plane p - 2
-        if (p - 2 >= k0) xout[wbase + sz * (p - 2)] = X[om2 + wpos];
+        if (p - 2 >= k0) {
+#pragma unroll
+            for (int v = 0; v < QW; ++v) xout[wbase[v] + sz * (p - 2)] = X[om2 + wpos[v]];
+        }
         // rotate to step p + 1
         const int t = om2;
         om2 = om1;
@@ -472,17 +503,22 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
     const Geo Cg = C ? C->g : g;
     count_launches(1);
     if (g.ny > 1 && g.nx % 32 == 0 && g.ny % 8 == 0 && g.nz >= 2) {
-        // whole 32 x 8 tiles: the in-place z-march; KZ planes per block, the
-        // largest of 64, 32, 16, 8 that still gives eight blocks per SM
-        const long long tiles = (long long)(g.nx / 32) * (g.ny / 8);
+        // whole TX x 8 tiles (TX = 64 when nx allows, else 32): the in-place
+        // z-march; KZ planes per block, the largest of 64, 32, 16, 8 that
+        // still gives eight blocks per SM
+        const int TXc = g.nx % 64 == 0 ? 64 : 32;
+        const long long tiles = (long long)(g.nx / TXc) * (g.ny / 8);
         int KZ = kz > 0 ? kz : 64;
         if (kz <= 0)
             while (KZ > 8 && tiles * hdiv(g.nz, KZ) < 8 * 152) KZ /= 2;
-        const dim3 grd(g.nx / 32, g.ny / 8, hdiv(g.nz, KZ)), blk(32, 8);
-#define LM_RBZ(F, Z, P) k_rbgs_zm<F, Z, P><<<grd, blk, 0, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout, KZ)
-        if (zero) { if (first) LM_RBZ(1, true, false); else LM_RBZ(0, true, false); }
-        else if (prolong) { if (first) LM_RBZ(1, false, true); else LM_RBZ(0, false, true); }
-        else { if (first) LM_RBZ(1, false, false); else LM_RBZ(0, false, false); }
+        const dim3 grd(g.nx / TXc, g.ny / 8, hdiv(g.nz, KZ)), blk(32, 8);
+#define LM_RBZ(T, F, Z, P) k_rbgs_zm<T, F, Z, P><<<grd, blk, 0, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout, KZ)
+#define LM_RBZT(T)                                                                                   \
+    if (zero) { if (first) LM_RBZ(T, 1, true, false); else LM_RBZ(T, 0, true, false); }            \
+    else if (prolong) { if (first) LM_RBZ(T, 1, false, true); else LM_RBZ(T, 0, false, true); }    \
+    else { if (first) LM_RBZ(T, 1, false, false); else LM_RBZ(T, 0, false, false); }
+        if (TXc == 64) { LM_RBZT(64) } else { LM_RBZT(32) }
+#undef LM_RBZT
 #undef LM_RBZ
     } else if (g.ny > 1) {
         constexpr int BX = 32, TY = 8;
