@@ -100,6 +100,94 @@ __global__ void __launch_bounds__(256) k_conv3(const TI* __restrict__ in, int Ci
     }
 }
 
+// ---- 3x3 convolution on the tensor cores (forward) --------------------------
+// The convolution as an implicit GEMM: M = pixels, N = output channels, K =
+// 9 taps x input channels.  Block: a 16 x 8 pixel tile, warp w owning pixel
+// row w (one m16 tile) and all NCO output channels (NCO/8 n8 tiles); K runs
+// over chunks of 16 input channels and the 9 taps.  mma.sync m16n8k16, BF16
+// operands, FP32 accumulation.  The input tile with a 1-pixel halo (zero
+// outside the image and past Cin) and the chunk's weights, transposed to
+// [tap][co][ci], are staged in shared memory with a 24-element pitch, so the
+// eight rows of a fragment load fall in distinct banks.
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <int NCO>
+__global__ void __launch_bounds__(256) k_conv3_mma(const bf16* __restrict__ in, int Cin, const bf16* __restrict__ W,
+                                                   const float* __restrict__ bias, bf16* __restrict__ out, int H,
+                                                   int Wd, int relu) {
+    constexpr int TXP = 16, TYP = 8, PX = TXP + 2, PY = TYP + 2, PITCH = 24;
+    __shared__ __align__(16) bf16 xs[PY * PX * PITCH];
+    __shared__ __align__(16) bf16 ws[9 * NCO * PITCH];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, tq = lane & 3;
+    const int b = blockIdx.z;
+    const int x0 = blockIdx.x * TXP, y0 = blockIdx.y * TYP;
+    float acc[NCO / 8][4];
+#pragma unroll
+    for (int n = 0; n < NCO / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    const bf16* inb = in + (size_t)b * H * Wd * Cin;
+    const bf16 zero = __float2bfloat16(0.f);
+    const uint32_t* xa = reinterpret_cast<const uint32_t*>(xs);
+    for (int ci0 = 0; ci0 < Cin; ci0 += 16) {
+        for (int e = threadIdx.x; e < PY * PX * 16; e += 256) {
+            const int c = e & 15, pix = e >> 4, px = pix % PX, py = pix / PX;
+            const int gy = y0 + py - 1, gx = x0 + px - 1;
+            bf16 v = zero;
+            if (ci0 + c < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd) v = inb[((size_t)gy * Wd + gx) * Cin + ci0 + c];
+            xs[pix * PITCH + c] = v;
+        }
+        for (int e = threadIdx.x; e < 9 * NCO * 16; e += 256) {
+            const int co = e % NCO, rest = e / NCO, ci = rest & 15, t = rest >> 4;
+            bf16 v = zero;
+            if (ci0 + ci < Cin) v = W[((size_t)t * Cin + ci0 + ci) * NCO + co];
+            ws[(t * NCO + co) * PITCH + ci] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int prow = (warp + t / 3) * PX + t % 3;      // staged pixel of row m = 0 for this tap
+            const uint32_t a0 = xa[((prow + g) * PITCH + 2 * tq) >> 1];
+            const uint32_t a1 = xa[((prow + g + 8) * PITCH + 2 * tq) >> 1];
+            const uint32_t a2 = xa[((prow + g) * PITCH + 2 * tq + 8) >> 1];
+            const uint32_t a3 = xa[((prow + g + 8) * PITCH + 2 * tq + 8) >> 1];
+#pragma unroll
+            for (int n = 0; n < NCO / 8; ++n) {
+                const uint32_t* wb = reinterpret_cast<const uint32_t*>(ws + (t * NCO + n * 8 + g) * PITCH);
+                mma_bf16_16816(acc[n], a0, a1, a2, a3, wb[tq], wb[tq + 4]);
+            }
+        }
+        __syncthreads();
+    }
+    const int gy = y0 + warp;
+    if (gy >= H) return;
+#pragma unroll
+    for (int n = 0; n < NCO / 8; ++n) {
+        const int co = n * 8 + 2 * tq;
+        const float bb0 = bias ? bias[co] : 0.f, bb1 = bias ? bias[co + 1] : 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {                            // pixel g (c0, c1), pixel g + 8 (c2, c3)
+            const int gx = x0 + g + 8 * h;
+            if (gx >= Wd) continue;
+            float v0 = acc[n][2 * h] + bb0, v1 = acc[n][2 * h + 1] + bb1;
+            if (relu) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+            }
+            __nv_bfloat162 pr;
+            pr.x = __float2bfloat16(v0);
+            pr.y = __float2bfloat16(v1);
+            *reinterpret_cast<__nv_bfloat162*>(out + (((size_t)b * H + gy) * Wd + gx) * NCO + co) = pr;
+        }
+    }
+}
+
 // wt[t][co][ci] = w[8 - t][ci][co]: the backward-data convolution is a
 // forward convolution of the output gradient with these weights.
 __global__ void k_wt_flip(const bf16* __restrict__ w, bf16* __restrict__ wt, int Cin, int Cout) {
@@ -419,11 +507,21 @@ int ensure_acts(lm_net* N, int B, int H, int W) {
 }
 
 void conv_fwd(lm_net* N, const lm_net::Conv& c, const bf16* in, bf16* out, int B, int H, int W, cudaStream_t s) {
+    count_launches(1);
+    const dim3 gm((W + 15) / 16, (H + 7) / 8, B);
+    const bf16* w = N->wb + c.w;
+    const float* bias = N->master + c.b;
+    switch (c.cout) {                           // tensor-core path for output widths that are multiples of 8
+        case 8: k_conv3_mma<8><<<gm, 256, 0, s>>>(in, c.cin, w, bias, out, H, W, 1); return;
+        case 16: k_conv3_mma<16><<<gm, 256, 0, s>>>(in, c.cin, w, bias, out, H, W, 1); return;
+        case 32: k_conv3_mma<32><<<gm, 256, 0, s>>>(in, c.cin, w, bias, out, H, W, 1); return;
+        case 48: k_conv3_mma<48><<<gm, 256, 0, s>>>(in, c.cin, w, bias, out, H, W, 1); return;
+        case 64: k_conv3_mma<64><<<gm, 256, 0, s>>>(in, c.cin, w, bias, out, H, W, 1); return;
+        default: break;
+    }
     const int ncoc = (c.cout + CT - 1) / CT;
     const dim3 grd((W + CT - 1) / CT, (H + CT - 1) / CT, B * ncoc);
-    count_launches(1);
-    k_conv3<bf16, bf16><<<grd, dim3(CT, CT), 0, s>>>(in, c.cin, N->wb + c.w, N->master + c.b, out, c.cout, H, W, 1,
-                                                    ncoc);
+    k_conv3<bf16, bf16><<<grd, dim3(CT, CT), 0, s>>>(in, c.cin, w, bias, out, c.cout, H, W, 1, ncoc);
 }
 
 // gin = conv3 backward-data of g (float32, Cout channels) through conv c

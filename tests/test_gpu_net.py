@@ -68,6 +68,27 @@ def test_forward_matches_oracle(lm):
     net.close()
 
 
+@pytest.mark.parametrize("ch,H,W", [((16, 32, 48, 64), 16, 16), ((8, 16, 24, 32), 24, 40)])
+def test_tensor_core_forward_matches_oracle(lm, ch, H, W):
+    """The production widths: every 3x3 convolution of the forward pass runs
+    on the tensor cores (output widths multiples of 8), incl. ragged tiles."""
+    rng = np.random.default_rng(11)
+    Pp = U.init_params(rng, cin=3, ch=ch)
+    for k in Pp:
+        if k.islower():
+            Pp[k] = rng.standard_normal(Pp[k].shape) * 0.1
+    x = rng.standard_normal((2, H, W, 3))
+    net = lm.Net(ch)
+    net.set_params(U.flat_params(Pp, 3, ch))
+    xd = torch.as_tensor(x.astype(np.float32).ravel(), device="cuda")
+    yd = torch.empty(2 * H * W, device="cuda")
+    net.forward(xd, yd, 2, H, W)
+    y = yd.cpu().numpy().astype(np.float64).reshape(2, H, W, 1)
+    y_ref, _ = U.forward(_oracle_params_as_gpu_sees_them(Pp), x, ch, rnd=_bf16)
+    assert np.linalg.norm(y - y_ref) <= 1e-2 * np.linalg.norm(y_ref)
+    net.close()
+
+
 def test_gradients_match_oracle(lm):
     rng, Pp, x = _setup(seed=6)
     net = lm.Net(CH)
