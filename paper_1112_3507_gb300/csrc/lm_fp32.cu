@@ -126,8 +126,17 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Lev32 F, Geo C, int hx, 
 // thus one pass over memory with no grid-wide barrier.  Work items
 // enumerate only cells of the colour being updated; wrapped in-plane
 // offsets are per-thread constants from small tables; f and c~ of the next
-// step's cells are loaded a step ahead.  Same operations in the same order
-// as rbgs_tile, so both kernels produce the same bits.
+// step's cells are loaded a step ahead.  Face weights and the final
+// division use the hardware reciprocal approximation (rcp_fast), so the
+// result can differ from rbgs_tile's in the last bits.
+// Reciprocal by the hardware approximation (rcp.approx.ftz: relative error
+// below 2^-22; +inf -> 0), the z-march's face weights and GS division.
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <int TX, int FIRST, bool ZERO, bool PROLONG>
 __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restrict__ xin,
                                                 const float* __restrict__ ec, Geo C, int hx, int hy, int hz,
@@ -214,12 +223,12 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
     auto gs = [&](int e, int sm, int s0, int sp, float fv, float cv) -> float {
         const int c = s0 + e;
         const float rc = R[c];
-        const float wxm = face32(rc, R[c - 1], L.c2x);
-        const float wxp = face32(rc, R[c + 1], L.c2x);
-        const float wym = face32(rc, R[c - SX], L.c2y);
-        const float wyp = face32(rc, R[c + SX], L.c2y);
-        const float wzm = face32(rc, R[sm + e], L.c2z);
-        const float wzp = face32(rc, R[sp + e], L.c2z);
+        const float wxm = L.c2x * rcp_fast(rc + R[c - 1]);
+        const float wxp = L.c2x * rcp_fast(rc + R[c + 1]);
+        const float wym = L.c2y * rcp_fast(rc + R[c - SX]);
+        const float wyp = L.c2y * rcp_fast(rc + R[c + SX]);
+        const float wzm = L.c2z * rcp_fast(rc + R[sm + e]);
+        const float wzp = L.c2z * rcp_fast(rc + R[sp + e]);
         const float d = cv + ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
         float num = fv;
         num = fmaf(wxm, X[c - 1], num);
@@ -228,7 +237,7 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
         num = fmaf(wyp, X[c + SX], num);
         num = fmaf(wzm, X[sm + e], num);
         num = fmaf(wzp, X[sp + e], num);
-        return __fdividef(num, d);
+        return num * rcp_fast(d);
     };
 
     // first-colour tasks of this thread: task tid + 256 u is pair am of
@@ -504,13 +513,14 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
     count_launches(1);
     if (g.ny > 1 && g.nx % 32 == 0 && g.ny % 8 == 0 && g.nz >= 2) {
         // whole TX x 8 tiles (TX = 64 when nx allows, else 32): the in-place
-        // z-march; KZ planes per block, the largest of 64, 32, 16, 8 that
-        // still gives eight blocks per SM
+        // z-march; KZ planes per block, the largest of 64, 32, ..., 2 that
+        // still gives eight blocks per SM (small levels are latency-bound:
+        // short chunks, more blocks)
         const int TXc = g.nx % 64 == 0 ? 64 : 32;
         const long long tiles = (long long)(g.nx / TXc) * (g.ny / 8);
         int KZ = kz > 0 ? kz : 64;
         if (kz <= 0)
-            while (KZ > 8 && tiles * hdiv(g.nz, KZ) < 8 * 152) KZ /= 2;
+            while (KZ > 2 && tiles * hdiv(g.nz, KZ) < 8 * 152) KZ /= 2;
         const dim3 grd(g.nx / TXc, g.ny / 8, hdiv(g.nz, KZ)), blk(32, 8);
 #define LM_RBZ(T, F, Z, P) k_rbgs_zm<T, F, Z, P><<<grd, blk, 0, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout, KZ)
 #define LM_RBZT(T)                                                                                   \
@@ -526,7 +536,7 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
         int KZ = kz;
         if (KZ <= 0) {
             KZ = 16;
-            while (KZ > 4 && (long long)tiles * hdiv(g.nz, KZ) < 1216) KZ /= 2;
+            while (KZ > 1 && (long long)tiles * hdiv(g.nz, KZ) < 1216) KZ /= 2;
         }
         const dim3 grd(hdiv(g.nx, 2 * BX), hdiv(g.ny, TY), hdiv(g.nz, KZ)), blk(BX, TY);
 #define LM_RB(F, Z, P) k_rbgs<BX, TY, true, F, Z, P><<<grd, blk, 0, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout, KZ)
