@@ -146,26 +146,14 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_sample(name: str, iters: int = 2, seed: int = 1) -> dict:
-    """Time the oracle's float64 Jacobi-PCG on the workload (single-threaded
-    numpy): one run of 1 iteration and one of 1 + `iters` iterations give the
-    set-up time and the time per iteration.  The oracle's own iteration count
-    to the workload's tolerance is measured on downsized grids (n/16, n/8,
-    n/4) and extrapolated by the fitted growth per grid doubling.  Returns the
-    estimated time to tolerance and the GDOF/s it implies."""
+def oracle_calibrate(name: str, seed: int = 1):
+    """The workload's problem and oracle operator, and the oracle's own
+    iteration count to the workload's tolerance: measured on downsized grids
+    of the same recipe and extrapolated by the fitted growth per doubling."""
     from oracle import poisson as P
-    from paper_1112_3507_gb300 import inputs as I
     w = WORKLOADS[name]
     p = make_problem(name, seed)
     op = P.operator_from_problem(p)
-    P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1)          # warm-up (first-touch of the arrays)
-    t0 = time.perf_counter()
-    P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1)
-    t1 = time.perf_counter()
-    _, it, _ = P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1 + iters)
-    t2 = time.perf_counter()
-    t_iter = max((t2 - t1) - (t1 - t0), 1e-9) / max(it - 1, 1)
-    t_setup = max((t1 - t0) - t_iter, 0.0)
     counts = []
     n = w["n"]
     big = n // 8 if n > 256 else n // 4               # largest downsized grid the oracle solves in seconds
@@ -179,16 +167,56 @@ def oracle_sample(name: str, iters: int = 2, seed: int = 1) -> dict:
         est_iters = counts[-1] * growth ** round(np.log2(n / big))
     else:
         est_iters = counts[0]
+    return p, op, counts, float(est_iters)
+
+
+def oracle_steps(name: str, steps: int, warmup: int, iters_per_step: int = 2) -> dict:
+    """The reference arm: calibrate once, then time warmup + steps bounded
+    samples, each `iters_per_step` full-size iterations of the oracle's
+    float64 Jacobi-PCG (its set-up included); each sample's time per
+    iteration times the oracle's iteration count to tolerance is that step's
+    estimated time to tolerance."""
+    from oracle import poisson as P
+    p, op, counts, est_iters = oracle_calibrate(name)
+    per_iter = []
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=iters_per_step)
+        if k >= warmup:
+            per_iter.append((time.perf_counter() - t0) / iters_per_step)
+    return dict(per_iter_s=per_iter, est_iters=est_iters, downsized_counts=counts, N=p.size,
+                iters_per_step=iters_per_step)
+
+
+def oracle_sample(name: str, iters: int = 2, seed: int = 1) -> dict:
+    """Time the oracle's float64 Jacobi-PCG on the workload (single-threaded
+    numpy): one run of 1 iteration and one of 1 + `iters` iterations give the
+    set-up time and the time per iteration.  The oracle's own iteration count
+    to the workload's tolerance is measured on downsized grids (n/16, n/8,
+    n/4) and extrapolated by the fitted growth per grid doubling.  Returns the
+    estimated time to tolerance and the GDOF/s it implies."""
+    from oracle import poisson as P
+    p, op, counts, est_iters = oracle_calibrate(name, seed)
+    P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1)          # warm-up (first-touch of the arrays)
+    t0 = time.perf_counter()
+    P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1)
+    t1 = time.perf_counter()
+    _, it, _ = P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1 + iters)
+    t2 = time.perf_counter()
+    t_iter = max((t2 - t1) - (t1 - t0), 1e-9) / max(it - 1, 1)
+    t_setup = max((t1 - t0) - t_iter, 0.0)
     est_s = t_setup + t_iter * est_iters
     return dict(t_iter_s=t_iter, t_setup_s=t_setup, sample_iters=it + 1, est_iters=float(est_iters),
                 downsized_counts=counts, est_time_s=est_s, value=p.size / est_s / 1e9, N=p.size)
 
 
-def oracle_subprocess(name: str, iters: int) -> dict:
+def oracle_subprocess(name: str, iters: int, call: str | None = None) -> dict:
+    """Run an oracle timing in a single-threaded child process."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    call = call or "bench.oracle_sample(%r, %d)" % (name, iters)
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "print('ORACLE_JSON', json.dumps(bench.oracle_sample(%r, %d)))" % (ROOT, name, iters))
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+            "print('ORACLE_JSON', json.dumps(%s))" % (ROOT, call))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     for line in r.stdout.splitlines():
         if line.startswith("ORACLE_JSON"):
             return json.loads(line.split(" ", 1)[1])
@@ -208,20 +236,21 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    samples = []
-    for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        s = oracle_sample(args.workload, iters=args.oracle_iters)
-        if step >= args.warmup:
-            samples.append((s, time.perf_counter() - t0))
-    vals = [s["value"] for s, _ in samples]
-    s0 = samples[-1][0]
-    value = statistics.median(vals)
+    r = oracle_subprocess(args.workload, 0, call="bench.oracle_steps(%r, %d, %d)" % (args.workload, args.steps,
+                                                                                   args.warmup))
+    t_iter = statistics.median(r["per_iter_s"])
+    est = t_iter * r["est_iters"]
+    value = r["N"] / est / 1e9
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": (f"per step {r['iters_per_step']} full-size iterations of the FP64 oracle's Jacobi-PCG on "
+                      f"{args.workload} (single-threaded numpy; median {t_iter:.3f} s/iter over {args.steps} "
+                      f"steps) x its iteration count to rtol extrapolated from downsized grids "
+                      f"{r['downsized_counts']} -> {r['est_iters']:.0f}; estimated time to tolerance {est:.1f} s")}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": s0["est_time_s"] * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload]["desc"], "cells": s0["N"]},
-            "cpu_baseline": cpu_block(s0, args.workload),
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload]["desc"], "cells": r["N"]},
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
