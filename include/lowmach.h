@@ -125,7 +125,7 @@ typedef struct {
     double seconds;         /* device time of the solve (CUDA events)             */
 } lm_solve_result;
 
-/* Defaults: mode LM_MIXED_MG_IR, rtol 1e-8, max_iter 10000, nu1 = nu2 = 2,
+/* Defaults: mode LM_MIXED_MG_IR, rtol 1e-8, max_iter 10000, nu1 = 2, nu2 = 3,
  * inner_rtol 1e-4, inner_max_iter 30, max_outer 12, check_every 8,
  * net_precond 0. */
 void lm_default_opts(lm_solve_opts* opts);
@@ -275,7 +275,7 @@ int  lm_net_features(lm_grid* g, const double* v, float* feat, double* scale, vo
  * z-chunk of every level shape is chosen by the autotuner (see
  * lm_autotune_set_cache).  The captured plan is cached per (grids,
  * coefficient versions, inner_max_iter, use_x0) and reused by later calls.
- * Requirements: 2D grids (ndim 2), nu1 = nu2 = 1 (lm_default_opts sets 2:
+ * Requirements: 2D grids (ndim 2), nu1 = nu2 = 1 (lm_default_opts sets 2 and 3:
  * set both to 1 for a batch), an exactly solved coarsest
  * level (grids whose halvings reach <= 64 cells), even periodic extents.
  * results[i] receives grid i's status, inner iterations (iters = vcycles),

@@ -524,7 +524,7 @@ void lm_default_opts(lm_solve_opts* o) {
     o->use_x0 = 0;
     o->max_outer = 12;
     o->nu1 = 2;
-    o->nu2 = 2;
+    o->nu2 = 3;
     o->inner_rtol = 1e-4;
     o->inner_max_iter = 30;
     o->check_every = 8;

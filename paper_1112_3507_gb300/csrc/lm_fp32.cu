@@ -33,6 +33,146 @@ __global__ void __launch_bounds__(256) k_apply32z(Lev32 L, const float* __restri
     }
 }
 
+// ---- 3D apply on whole tiles: a z-march over staged planes ----------------
+// y = A x with x.y and x.r accumulated to float64 accuracy, for 3D levels
+// whose nx, ny are multiples of the TX x 8 tile.  A block owns a tile's
+// columns over a chunk of KZ planes and marches up z with a four-plane ring
+// of x and rho staged on the tile plus one cell (periodic axes wrapped; past
+// a Neumann wall x = 0 and rho = +inf, so that face's weight is 0): at step
+// p it stores plane p + 1, issues the loads of plane p + 2 and, after one
+// barrier, forms y on plane p from shared memory.  c~ and r of the next
+// plane are loaded a step ahead.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float q;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(x));
+    return q;
+}
+
+template <int TX, bool DOT_XY, bool DOT_XR>
+__global__ void __launch_bounds__(256) k_apply32_zm(Lev32 L, const float* __restrict__ x, float* __restrict__ y,
+                                                   const float* __restrict__ r, Red red, int slot_xy, int slot_xr,
+                                                   int KZ) {
+    constexpr int NT2 = 256, TY = 8, SX = TX + 2, SY = TY + 2, PL = SX * SY, NR = 4;
+    constexpr int QS = (PL + NT2 - 1) / NT2, QW = TX * TY / NT2;
+    static_assert(SX + SY <= NT2 && QW * NT2 == TX * TY, "tile does not fit the block");
+    __shared__ float X[NR * PL];
+    __shared__ float R[NR * PL];
+    __shared__ int ox[SX], oy[SY];
+    __shared__ double sm[64];
+    const Geo& g = L.g;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int k0 = blockIdx.z * KZ, k1 = min(k0 + KZ, g.nz);
+    const int sy = g.nx, sz = g.nx * g.ny;
+    if (tid < SX) {
+        int c = i0 - 1 + tid;
+        if (c < 0) c = g.bcx == LM_BC_PERIODIC ? c + g.nx : -1;
+        else if (c >= g.nx) c = g.bcx == LM_BC_PERIODIC ? c - g.nx : -1;
+        ox[tid] = c;
+    } else if (tid < SX + SY) {
+        int c = j0 - 1 + tid - SX;
+        if (c < 0) c = g.bcy == LM_BC_PERIODIC ? c + g.ny : -1;
+        else if (c >= g.ny) c = g.bcy == LM_BC_PERIODIC ? c - g.ny : -1;
+        oy[tid - SX] = c < 0 ? -1 : sy * c;
+    }
+    __syncthreads();
+    auto zoff = [&](int p) -> int {                      // p within one plane of [0, nz)
+        if (p >= 0 && p < g.nz) return sz * p;
+        if (g.bcz != LM_BC_PERIODIC) return -1;
+        return sz * (p < 0 ? p + g.nz : p - g.nz);
+    };
+    int spos[QS], sbase[QS];
+    bool sok[QS];
+#pragma unroll
+    for (int q = 0; q < QS; ++q) {
+        spos[q] = tid + q * NT2;
+        const bool use = spos[q] < PL;
+        const int sj = use ? spos[q] / SX : 0, si = use ? spos[q] - sj * SX : 0;
+        sok[q] = use && (ox[si] | oy[sj]) >= 0;
+        sbase[q] = ox[si] + oy[sj];
+        if (!use) spos[q] = -1;
+    }
+    float vx[QS], vr[QS];
+    auto fetch = [&](int zo) {
+#pragma unroll
+        for (int q = 0; q < QS; ++q) {
+            vx[q] = 0.f;
+            vr[q] = __int_as_float(0x7f800000);          // +inf
+            if (sok[q] && zo >= 0) {
+                vx[q] = x[sbase[q] + zo];
+                vr[q] = L.rho[sbase[q] + zo];
+            }
+        }
+    };
+    auto store = [&](int o) {
+#pragma unroll
+        for (int q = 0; q < QS; ++q)
+            if (spos[q] >= 0) {
+                X[o + spos[q]] = vx[q];
+                R[o + spos[q]] = vr[q];
+            }
+    };
+    int we[QW], wg[QW];
+#pragma unroll
+    for (int v = 0; v < QW; ++v) {
+        const int w = tid + v * NT2, wx = w % TX, wy = w / TX;
+        we[v] = (wy + 1) * SX + wx + 1;
+        wg[v] = (i0 + wx) + sy * (j0 + wy);
+    }
+    FF axy{0.f, 0.f}, axr{0.f, 0.f};
+    float ctn[QW], rrn[QW];
+    auto load_c = [&](int p) {
+#pragma unroll
+        for (int v = 0; v < QW; ++v) {
+            ctn[v] = L.ct[wg[v] + sz * p];
+            rrn[v] = DOT_XR ? r[wg[v] + sz * p] : 0.f;
+        }
+    };
+    fetch(zoff(k0 - 1));
+    store(((k0 - 1) & 3) * PL);
+    fetch(zoff(k0));
+    store((k0 & 3) * PL);
+    fetch(zoff(k0 + 1));
+    load_c(k0);
+    for (int p = k0; p < k1; ++p) {
+        store(((p + 1) & 3) * PL);
+        if (p + 2 <= k1) fetch(zoff(p + 2));
+        float ctc[QW], rrc[QW];
+#pragma unroll
+        for (int v = 0; v < QW; ++v) {
+            ctc[v] = ctn[v];
+            rrc[v] = rrn[v];
+        }
+        if (p + 1 < k1) load_c(p + 1);
+        __syncthreads();
+        const int om = ((p - 1) & 3) * PL, o0 = (p & 3) * PL, op = ((p + 1) & 3) * PL;
+#pragma unroll
+        for (int v = 0; v < QW; ++v) {
+            const int c = o0 + we[v];
+            const float xc = X[c], rc = R[c];
+            float val = ctc[v] * xc;
+            val += L.c2x * rcp_approx(rc + R[c - 1]) * (xc - X[c - 1]);
+            val += L.c2x * rcp_approx(rc + R[c + 1]) * (xc - X[c + 1]);
+            val += L.c2y * rcp_approx(rc + R[c - SX]) * (xc - X[c - SX]);
+            val += L.c2y * rcp_approx(rc + R[c + SX]) * (xc - X[c + SX]);
+            val += L.c2z * rcp_approx(rc + R[om + we[v]]) * (xc - X[om + we[v]]);
+            val += L.c2z * rcp_approx(rc + R[op + we[v]]) * (xc - X[op + we[v]]);
+            y[wg[v] + sz * p] = val;
+            if (DOT_XY) ff_add_prod(axy, xc, val);
+            if (DOT_XR) ff_add_prod(axr, xc, rrc[v]);
+        }
+    }
+    if (DOT_XY && DOT_XR) {
+        double v[2] = {ff_value(axy), ff_value(axr)};
+        const int sl[2] = {slot_xy, slot_xr};
+        grid_reduce<2>(v, red, sl, sm);
+    } else if (DOT_XY) {
+        double v[1] = {ff_value(axy)};
+        const int sl[1] = {slot_xy};
+        grid_reduce<1>(v, red, sl, sm);
+    }
+}
+
 // scal[slot] = a.b; if fnorm_st: also fnorm_st->fnorm = sqrt(a.b), rel = 1.
 __global__ void __launch_bounds__(NT) k_dot32(int N, const float* __restrict__ a, const float* __restrict__ b,
                                               Red red, int slot, SolveState* fnorm_st) {
@@ -447,6 +587,26 @@ static dim3 cell_grid(const Geo& g) {
 void launch_apply32(const Lev32& L, cudaStream_t s, const float* x, float* y, const float* r, const Red& red,
                     int slot_xy, int slot_xr) {
     const Geo& g = L.g;
+    if (g.ny > 1 && g.nx % 32 == 0 && g.ny % 8 == 0 && g.nz >= 2) {
+        // whole TX x 8 tiles: the staged z-march; KZ planes per block, the
+        // largest of 64, 32, ..., 2 that still gives eight blocks per SM
+        const int TXc = g.nx % 64 == 0 ? 64 : 32;
+        const long long tiles = (long long)(g.nx / TXc) * (g.ny / 8);
+        int KZ = 64;
+        while (KZ > 2 && tiles * hdiv(g.nz, KZ) < 8 * 152) KZ /= 2;
+        const dim3 grd(g.nx / TXc, g.ny / 8, hdiv(g.nz, KZ)), blk(32, 8);
+        count_launches(1);
+        const bool dxy = slot_xy >= 0, dxr = slot_xr >= 0;
+#define LM_AZ(T, A, B) k_apply32_zm<T, A, B><<<grd, blk, 0, s>>>(L, x, y, r, red, slot_xy, slot_xr, KZ)
+#define LM_AZT(T)                              \
+    if (dxy && dxr) LM_AZ(T, true, true);      \
+    else if (dxy) LM_AZ(T, true, false);       \
+    else LM_AZ(T, false, false);
+        if (TXc == 64) { LM_AZT(64) } else { LM_AZT(32) }
+#undef LM_AZT
+#undef LM_AZ
+        return;
+    }
     const dim3 blk(32, 8);
     const bool y3 = g.ny > 1;
     int kz = 1;

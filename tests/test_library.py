@@ -51,7 +51,7 @@ def test_status_strings_and_defaults(lib):
     assert lm.status_string(lm.LM_ERR_NOT_POSITIVE).startswith("coefficients")
     o = lm.SolveOpts()
     lm.lib().lm_default_opts(ctypes.byref(o))
-    assert o.mode == lm.MIXED_MG_IR and o.rtol == 1e-8 and o.nu1 == 2 and o.nu2 == 2 and o.inner_rtol == 1e-4 and o.net_precond == 0
+    assert o.mode == lm.MIXED_MG_IR and o.rtol == 1e-8 and o.nu1 == 2 and o.nu2 == 3 and o.inner_rtol == 1e-4 and o.net_precond == 0
 
 
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
