@@ -173,6 +173,142 @@ __global__ void __launch_bounds__(256) k_apply32_zm(Lev32 L, const float* __rest
     }
 }
 
+// ---- 3D residual + restriction on whole tiles: a z-march -------------------
+// fc = mean over the children of (f - A x), for 3D fine levels whose nx, ny
+// are multiples of the TX x 8 tile: the same staged four-plane ring as
+// k_apply32_zm; each step forms the residual of one fine plane of the tile
+// in shared memory, the threads of the coarse cells add their children in
+// x and y, and the sum over the (1 << hz) fine planes of a coarse plane
+// is carried in a register until the coarse plane is written.
+template <int TX>
+__global__ void __launch_bounds__(256) k_resid_restrict_zm(Lev32 L, Geo C, int hx, int hy, int hz,
+                                                          const float* __restrict__ x, const float* __restrict__ f,
+                                                          float* __restrict__ fc, int KZ) {
+    constexpr int NT2 = 256, TY = 8, SX = TX + 2, SY = TY + 2, PL = SX * SY, NR = 4;
+    constexpr int QS = (PL + NT2 - 1) / NT2, QW = TX * TY / NT2;
+    __shared__ float X[NR * PL];
+    __shared__ float R[NR * PL];
+    __shared__ float RS[TX * TY];
+    __shared__ int ox[SX], oy[SY];
+    const Geo& g = L.g;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int k0 = blockIdx.z * KZ, k1 = min(k0 + KZ, g.nz);
+    const int sy = g.nx, sz = g.nx * g.ny;
+    if (tid < SX) {
+        int c = i0 - 1 + tid;
+        if (c < 0) c = g.bcx == LM_BC_PERIODIC ? c + g.nx : -1;
+        else if (c >= g.nx) c = g.bcx == LM_BC_PERIODIC ? c - g.nx : -1;
+        ox[tid] = c;
+    } else if (tid < SX + SY) {
+        int c = j0 - 1 + tid - SX;
+        if (c < 0) c = g.bcy == LM_BC_PERIODIC ? c + g.ny : -1;
+        else if (c >= g.ny) c = g.bcy == LM_BC_PERIODIC ? c - g.ny : -1;
+        oy[tid - SX] = c < 0 ? -1 : sy * c;
+    }
+    __syncthreads();
+    auto zoff = [&](int p) -> int {
+        if (p >= 0 && p < g.nz) return sz * p;
+        if (g.bcz != LM_BC_PERIODIC) return -1;
+        return sz * (p < 0 ? p + g.nz : p - g.nz);
+    };
+    int spos[QS], sbase[QS];
+    bool sok[QS];
+#pragma unroll
+    for (int q = 0; q < QS; ++q) {
+        spos[q] = tid + q * NT2;
+        const bool use = spos[q] < PL;
+        const int sj = use ? spos[q] / SX : 0, si = use ? spos[q] - sj * SX : 0;
+        sok[q] = use && (ox[si] | oy[sj]) >= 0;
+        sbase[q] = ox[si] + oy[sj];
+        if (!use) spos[q] = -1;
+    }
+    float vx[QS], vr[QS];
+    auto fetch = [&](int zo) {
+#pragma unroll
+        for (int q = 0; q < QS; ++q) {
+            vx[q] = 0.f;
+            vr[q] = __int_as_float(0x7f800000);          // +inf
+            if (sok[q] && zo >= 0) {
+                vx[q] = x[sbase[q] + zo];
+                vr[q] = L.rho[sbase[q] + zo];
+            }
+        }
+    };
+    auto store = [&](int o) {
+#pragma unroll
+        for (int q = 0; q < QS; ++q)
+            if (spos[q] >= 0) {
+                X[o + spos[q]] = vx[q];
+                R[o + spos[q]] = vr[q];
+            }
+    };
+    int we[QW], wg[QW], wl[QW];
+#pragma unroll
+    for (int v = 0; v < QW; ++v) {
+        const int w = tid + v * NT2, wx = w % TX, wy = w / TX;
+        we[v] = (wy + 1) * SX + wx + 1;
+        wg[v] = (i0 + wx) + sy * (j0 + wy);
+        wl[v] = w;
+    }
+    // coarse cell of this thread: (ci, cj) of the (TX >> hx) x (TY >> hy) coarse tile
+    const int CX = TX >> hx, CY = TY >> hy;
+    const bool hasC = tid < CX * CY;
+    const int cci = hasC ? tid % CX : 0, ccj = hasC ? tid / CX : 0;
+    const int cbase = ((i0 >> hx) + cci) + C.nx * ((j0 >> hy) + ccj);
+    const float inv = 1.f / (float)((1 << hx) << hy << hz);
+    float csum = 0.f;
+    float ctn[QW], fn[QW];
+    auto load_c = [&](int p) {
+#pragma unroll
+        for (int v = 0; v < QW; ++v) {
+            ctn[v] = L.ct[wg[v] + sz * p];
+            fn[v] = f[wg[v] + sz * p];
+        }
+    };
+    fetch(zoff(k0 - 1));
+    store(((k0 - 1) & 3) * PL);
+    fetch(zoff(k0));
+    store((k0 & 3) * PL);
+    fetch(zoff(k0 + 1));
+    load_c(k0);
+    for (int p = k0; p < k1; ++p) {
+        store(((p + 1) & 3) * PL);
+        if (p + 2 <= k1) fetch(zoff(p + 2));
+        float ctc[QW], fcur[QW];
+#pragma unroll
+        for (int v = 0; v < QW; ++v) {
+            ctc[v] = ctn[v];
+            fcur[v] = fn[v];
+        }
+        if (p + 1 < k1) load_c(p + 1);
+        __syncthreads();
+        const int om = ((p - 1) & 3) * PL, o0 = (p & 3) * PL, op = ((p + 1) & 3) * PL;
+#pragma unroll
+        for (int v = 0; v < QW; ++v) {
+            const int c = o0 + we[v];
+            const float xc = X[c], rc = R[c];
+            float val = ctc[v] * xc;
+            val += L.c2x * rcp_approx(rc + R[c - 1]) * (xc - X[c - 1]);
+            val += L.c2x * rcp_approx(rc + R[c + 1]) * (xc - X[c + 1]);
+            val += L.c2y * rcp_approx(rc + R[c - SX]) * (xc - X[c - SX]);
+            val += L.c2y * rcp_approx(rc + R[c + SX]) * (xc - X[c + SX]);
+            val += L.c2z * rcp_approx(rc + R[om + we[v]]) * (xc - X[om + we[v]]);
+            val += L.c2z * rcp_approx(rc + R[op + we[v]]) * (xc - X[op + we[v]]);
+            RS[wl[v]] = fcur[v] - val;
+        }
+        __syncthreads();
+        if (hasC) {
+            for (int b = 0; b <= hy; ++b)
+                for (int a = 0; a <= hx; ++a) csum += RS[((ccj << hy) + b) * TX + (cci << hx) + a];
+            if (hz == 0 || (p & 1)) {
+                fc[cbase + C.nx * C.ny * (p >> hz)] = csum * inv;
+                csum = 0.f;
+            }
+        }
+    }
+}
+
 // scal[slot] = a.b; if fnorm_st: also fnorm_st->fnorm = sqrt(a.b), rel = 1.
 __global__ void __launch_bounds__(NT) k_dot32(int N, const float* __restrict__ a, const float* __restrict__ b,
                                               Red red, int slot, SolveState* fnorm_st) {
@@ -661,6 +797,18 @@ void launch_coarsen(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cuda
 void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s,
                            const float* x, const float* f, float* fc) {
     count_launches(1);
+    const Geo& g = F.g;
+    if (g.ny > 1 && g.nx % 32 == 0 && g.ny % 8 == 0 && g.nz >= 2 && (!hz || g.nz % 2 == 0)) {
+        // whole TX x 8 tiles: the staged z-march; KZ (even) planes per block
+        const int TXc = g.nx % 64 == 0 ? 64 : 32;
+        const long long tiles = (long long)(g.nx / TXc) * (g.ny / 8);
+        int KZ = 64;
+        while (KZ > 2 && tiles * hdiv(g.nz, KZ) < 8 * 152) KZ /= 2;
+        const dim3 grd(g.nx / TXc, g.ny / 8, hdiv(g.nz, KZ)), blk(32, 8);
+        if (TXc == 64) k_resid_restrict_zm<64><<<grd, blk, 0, s>>>(F, C.g, hx, hy, hz, x, f, fc, KZ);
+        else k_resid_restrict_zm<32><<<grd, blk, 0, s>>>(F, C.g, hx, hy, hz, x, f, fc, KZ);
+        return;
+    }
     k_resid_restrict<<<cell_grid(C.g), dim3(32, 8), 0, s>>>(F, C.g, hx, hy, hz, x, f, fc);
 }
 
