@@ -469,18 +469,22 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
         spar[q] = pxy[si] + pxy[SX + sj];
         if (!use) spos[q] = -1;
     }
-    float vx[QS], vr[QS];
+    // x, rho and (PROLONG) the coarse correction of a staged plane, held in
+    // registers from their loads until the plane is stored a step later, so
+    // nothing waits on the loads within the step that issues them
+    float vx[QS], vr[QS], ve[QS];
     auto fetch = [&](int zo, int zp) {                   // plane with offset zo -> registers
 #pragma unroll
         for (int q = 0; q < QS; ++q) {
             vx[q] = 0.f;
+            ve[q] = 0.f;
             vr[q] = __int_as_float(0x7f800000);          // +inf
             if (sok[q] && zo >= 0) {
                 const int idx = sbase[q] + zo;
                 vr[q] = L.rho[idx];
                 if (!ZERO) {
                     vx[q] = xin[idx];
-                    if (PROLONG) vx[q] += ec[spar[q] + zp];
+                    if (PROLONG) ve[q] = ec[spar[q] + zp];
                 }
             }
         }
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
 #pragma unroll
         for (int q = 0; q < QS; ++q)
             if (spos[q] >= 0) {
-                X[o + spos[q]] = vx[q];
+                X[o + spos[q]] = PROLONG ? vx[q] + ve[q] : vx[q];
                 R[o + spos[q]] = vr[q];
             }
     };
@@ -550,6 +554,8 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
     int om2 = 0 * PL, om1 = 1 * PL, o0 = 2 * PL, op1 = 3 * PL, op2 = 4 * PL;
     // wrapped offsets of planes p, p + 1, p + 2 (shift register)
     int z0 = zoff(k0 - 1), z1 = zoff(k0), z2 = zoff(k0 + 1);
+    // parent plane offset of plane p + 2 (PROLONG), carried like z2
+    int zp2 = PROLONG ? zpar(k0 + 1) : 0;
     // prologue: planes k0 - 2, k0 - 1 staged; plane k0 in registers
     fetch(zoff(k0 - 2), PROLONG ? zpar(k0 - 2) : 0);
     store(om1);
@@ -582,7 +588,7 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
     for (int p = k0 - 1; p <= k1 + 1; ++p) {
         // (1) stage plane p + 1, fetch plane p + 2
         if (p <= k1) store(op1);
-        if (p + 1 <= k1) fetch(z2, PROLONG ? zpar(p + 2) : 0);
+        if (p + 1 <= k1) fetch(z2, zp2);
         float fA[QA], cA[QA];
         bool doA[QA];
         int eAc[QA];
@@ -635,6 +641,7 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
             if (c >= g.nz) c -= g.nz;
             if (c >= g.nz) c -= g.nz;
             z2 = (p + 3 < g.nz || g.bcz == LM_BC_PERIODIC) && c >= 0 && c < g.nz ? sz * c : -1;
+            if (PROLONG) zp2 = C.nx * C.ny * ((c >= 0 && c < g.nz ? c : 0) >> hz);
         }
     }
 }
