@@ -361,6 +361,58 @@ int learned_precond(lm_grid* g, float* z, const float* r, cudaStream_t s) {
     return LM_OK;
 }
 
+// One inner flexible-CG iteration with the V-cycle preconditioner:
+// z = M r, p = z (first) or z + beta p, q = A p with p.q and p.r, then the
+// e, r update and r.r (the last block sets the inner state's rel).
+void inner_iteration(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, bool first) {
+    MgLevel& M = g->mg[0];
+    const Red red{g->part, g->scal, g->ctr};
+    vcycle(g, 0, g->z32, g->r32, o->nu1, o->nu2, s);
+    if (!first) launch_dot32(g->N, g->G, s, g->z32, g->q32, red, 3, nullptr);
+    launch_fcg_beta_p(g->N, g->G, s, g->z32, g->p32, g->scal, first);
+    launch_apply32(M.L, s, g->p32, g->q32, g->r32, red, 0, 2);
+    launch_fcg_update(g->N, g->G, s, g->e32, g->r32, g->p32, g->q32, red, g->st_in);
+}
+
+// The two inner iterations as CUDA graphs, captured on the grid's own stream
+// (graphs launch on any stream) once per hierarchy version and smoothing
+// counts: an iteration is ~40 dependent launches, most of them tiny on the
+// coarse levels.  Returns false when capture is unavailable (the caller then
+// launches directly).
+bool ensure_inner_graphs(lm_grid* g, const lm_solve_opts* o) {
+    if (g->ig_exec[0] && g->ig_version == g->version && g->ig_nu1 == o->nu1 && g->ig_nu2 == o->nu2) return true;
+    for (cudaGraphExec_t& e : g->ig_exec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+    if (!g->cap_stream && cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+    for (int k = 0; k < 2; ++k) {
+        const long long before = lm_kernel_launches();
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+        inner_iteration(g, o, g->cap_stream, k == 0);
+        const cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+        g->ig_nk[k] = lm_kernel_launches() - before;
+        count_launches(-g->ig_nk[k]);                  // captured, not launched
+        if (e != cudaSuccess || !graph) {
+            cudaGetLastError();
+            return false;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&g->ig_exec[k], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            g->ig_exec[k] = nullptr;
+            cudaGetLastError();
+            return false;
+        }
+    }
+    g->ig_version = g->version;
+    g->ig_nu1 = o->nu1;
+    g->ig_nu2 = o->nu2;
+    return true;
+}
+
 // Inner float32 flexible CG on A32 e = r (r overwritten).  Preconditioner:
 // the V-cycle, or (*use_net) the learned two-level cycle above; a network
 // preconditioner that leaves the inner residual above 1/2 after 4
@@ -374,17 +426,25 @@ int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, in
     if ((rc = init_state(g, g->st_in, o->inner_rtol, s))) return rc;
     // the inner problem's reference norm: ||r|| of its right-hand side
     launch_dot32(g->N, g->G, s, g->r32, g->r32, red, 4, g->st_in);
+    bool graphs = false;
     for (int it = 0; it < o->inner_max_iter; ++it) {
         if (use_net && *use_net) {
             if ((rc = learned_precond(g, g->z32, g->r32, s))) return rc;
+            if (it > 0) launch_dot32(g->N, g->G, s, g->z32, g->q32, red, 3, nullptr);
+            launch_fcg_beta_p(g->N, g->G, s, g->z32, g->p32, g->scal, it == 0);
+            launch_apply32(M.L, s, g->p32, g->q32, g->r32, red, 0, 2);
+            launch_fcg_update(g->N, g->G, s, g->e32, g->r32, g->p32, g->q32, red, g->st_in);
         } else {
-            vcycle(g, 0, g->z32, g->r32, o->nu1, o->nu2, s);
+            if (!graphs) graphs = ensure_inner_graphs(g, o);
+            const int k = it == 0 ? 0 : 1;
+            if (graphs) {
+                CK(cudaGraphLaunch(g->ig_exec[k], s));
+                count_launches(g->ig_nk[k]);
+            } else {
+                inner_iteration(g, o, s, it == 0);
+            }
             ++*vcycles;
         }
-        if (it > 0) launch_dot32(g->N, g->G, s, g->z32, g->q32, red, 3, nullptr);
-        launch_fcg_beta_p(g->N, g->G, s, g->z32, g->p32, g->scal, it == 0);
-        launch_apply32(M.L, s, g->p32, g->q32, g->r32, red, 0, 2);
-        launch_fcg_update(g->N, g->G, s, g->e32, g->r32, g->p32, g->q32, red, g->st_in);
         CK(cudaGetLastError());
         ++*iters;
         if ((rc = sync_state(g, g->st_in, s))) return rc;
@@ -619,6 +679,9 @@ void lm_grid_destroy(lm_grid* g) {
     cudaFreeHost(g->dscal_host);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
+    for (cudaGraphExec_t& e : g->ig_exec)
+        if (e) cudaGraphExecDestroy(e);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
 }
 

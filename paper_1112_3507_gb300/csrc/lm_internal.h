@@ -73,6 +73,14 @@ struct lm_grid {
     float* nny = nullptr;           // network output (N)
     std::vector<lm::MgLevel> mg;
     std::vector<double> history;
+    // CUDA graphs of one inner flexible-CG iteration with the V-cycle (the
+    // first and the later ones), captured on cap_stream for hierarchy
+    // version ig_version and smoothing (ig_nu1, ig_nu2); ig_nk kernels each
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t ig_exec[2] = {nullptr, nullptr};
+    long long ig_nk[2] = {0, 0};
+    unsigned ig_version = ~0u;
+    int ig_nu1 = -1, ig_nu2 = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
