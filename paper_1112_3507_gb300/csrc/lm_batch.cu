@@ -440,7 +440,10 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
         G.st_in = g->st_in;
         G.red = Red{g->part, g->scal, g->ctr};
         G.N = g->N;
-        int kz = 1;
+        // rows per thread of the batched apply: at least 8 (2048 cells per
+        // block, so the per-block dot reduction stays small against the
+        // stencil work), more when the grid would exceed 4096 blocks
+        int kz = 8;
         while ((long long)hdiv(g->n[0], 32) * hdiv(hdiv(g->n[2], kz), 8) > 4096) kz *= 2;
         G.kz_apply = kz;
         lev0[i] = (int)hl.size();

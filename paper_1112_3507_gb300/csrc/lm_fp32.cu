@@ -757,7 +757,14 @@ void launch_apply32(const Lev32& L, cudaStream_t s, const float* x, float* y, co
         return y3 ? dim3(hdiv(g.nx, 32), hdiv(g.ny, 8), hdiv(g.nz, k))
                   : dim3(hdiv(g.nx, 32), hdiv(hdiv(g.nz, k), 8), 1);
     };
-    while ((long long)grid_for(kz).x * grid_for(kz).y * grid_for(kz).z > 4096) kz *= 2;
+    auto nblocks = [&](int k) { return (long long)grid_for(k).x * grid_for(k).y * grid_for(k).z; };
+    if (!y3)            // 2D: up to 8 rows per thread while two blocks per SM remain
+        for (int k = 8; k > 1; k /= 2)
+            if (nblocks(k) >= 2 * 152) {
+                kz = k;
+                break;
+            }
+    while (nblocks(kz) > 4096) kz *= 2;
     const dim3 grd = grid_for(kz);
     count_launches(1);
     const bool dxy = slot_xy >= 0, dxr = slot_xr >= 0;

@@ -118,49 +118,63 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint3
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-template <int NCO>
-__global__ void __launch_bounds__(256) k_conv3_mma(const bf16* __restrict__ in, int Cin, const bf16* __restrict__ W,
-                                                   const float* __restrict__ bias, bf16* __restrict__ out, int H,
-                                                   int Wd, int relu) {
+// NCB output channels per block (blockIdx.z = image x channel chunk), of
+// Cout in all.  SPLIT = false: BF16 input, BF16 output with bias and ReLU
+// (the forward pass).  SPLIT = true: float32 input split into a BF16 high
+// part and a BF16 remainder, two products per fragment (about 16 mantissa
+// bits of the input reach the FP32 accumulator), float32 output with
+// neither bias nor ReLU (the backward-data pass of float32 gradients).
+template <int NCB, bool SPLIT>
+__global__ void __launch_bounds__(256) k_conv3_mma(const void* __restrict__ in_, int Cin, const bf16* __restrict__ W,
+                                                   const float* __restrict__ bias, void* __restrict__ out_, int Cout,
+                                                   int H, int Wd, int relu) {
     constexpr int TXP = 16, TYP = 8, PX = TXP + 2, PY = TYP + 2, PITCH = 24;
-    __shared__ __align__(16) bf16 xs[PY * PX * PITCH];
-    __shared__ __align__(16) bf16 ws[9 * NCO * PITCH];
+    __shared__ __align__(16) bf16 xs[(SPLIT ? 2 : 1) * PY * PX * PITCH];
+    __shared__ __align__(16) bf16 ws[9 * NCB * PITCH];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, tq = lane & 3;
-    const int b = blockIdx.z;
+    const int nch = Cout / NCB;
+    const int b = blockIdx.z / nch, co0 = (blockIdx.z % nch) * NCB;
     const int x0 = blockIdx.x * TXP, y0 = blockIdx.y * TYP;
-    float acc[NCO / 8][4];
+    float acc[NCB / 8][4];
 #pragma unroll
-    for (int n = 0; n < NCO / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    const bf16* inb = in + (size_t)b * H * Wd * Cin;
+    for (int n = 0; n < NCB / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
     const bf16 zero = __float2bfloat16(0.f);
     const uint32_t* xa = reinterpret_cast<const uint32_t*>(xs);
+    constexpr int LO = PY * PX * PITCH / 2;              // uint32 offset of the remainder tile
     for (int ci0 = 0; ci0 < Cin; ci0 += 16) {
         for (int e = threadIdx.x; e < PY * PX * 16; e += 256) {
             const int c = e & 15, pix = e >> 4, px = pix % PX, py = pix / PX;
             const int gy = y0 + py - 1, gx = x0 + px - 1;
-            bf16 v = zero;
-            if (ci0 + c < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd) v = inb[((size_t)gy * Wd + gx) * Cin + ci0 + c];
-            xs[pix * PITCH + c] = v;
+            const bool inside = ci0 + c < Cin && gy >= 0 && gy < H && gx >= 0 && gx < Wd;
+            const size_t src = (((size_t)b * H + gy) * Wd + gx) * Cin + ci0 + c;
+            if (SPLIT) {
+                const float v = inside ? static_cast<const float*>(in_)[src] : 0.f;
+                const bf16 hi = __float2bfloat16(v);
+                xs[pix * PITCH + c] = hi;
+                xs[PY * PX * PITCH + pix * PITCH + c] = __float2bfloat16(v - __bfloat162float(hi));
+            } else {
+                xs[pix * PITCH + c] = inside ? static_cast<const bf16*>(in_)[src] : zero;
+            }
         }
-        for (int e = threadIdx.x; e < 9 * NCO * 16; e += 256) {
-            const int co = e % NCO, rest = e / NCO, ci = rest & 15, t = rest >> 4;
+        for (int e = threadIdx.x; e < 9 * NCB * 16; e += 256) {
+            const int co = e % NCB, rest = e / NCB, ci = rest & 15, t = rest >> 4;
             bf16 v = zero;
-            if (ci0 + ci < Cin) v = W[((size_t)t * Cin + ci0 + ci) * NCO + co];
-            ws[(t * NCO + co) * PITCH + ci] = v;
+            if (ci0 + ci < Cin) v = W[((size_t)t * Cin + ci0 + ci) * Cout + co0 + co];
+            ws[(t * NCB + co) * PITCH + ci] = v;
         }
         __syncthreads();
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
             const int prow = (warp + t / 3) * PX + t % 3;      // staged pixel of row m = 0 for this tap
-            const uint32_t a0 = xa[((prow + g) * PITCH + 2 * tq) >> 1];
-            const uint32_t a1 = xa[((prow + g + 8) * PITCH + 2 * tq) >> 1];
-            const uint32_t a2 = xa[((prow + g) * PITCH + 2 * tq + 8) >> 1];
-            const uint32_t a3 = xa[((prow + g + 8) * PITCH + 2 * tq + 8) >> 1];
+            const int i0 = ((prow + g) * PITCH + 2 * tq) >> 1, i1 = ((prow + g + 8) * PITCH + 2 * tq) >> 1;
+            const uint32_t a0 = xa[i0], a1 = xa[i1], a2 = xa[i0 + 4], a3 = xa[i1 + 4];
 #pragma unroll
-            for (int n = 0; n < NCO / 8; ++n) {
-                const uint32_t* wb = reinterpret_cast<const uint32_t*>(ws + (t * NCO + n * 8 + g) * PITCH);
+            for (int n = 0; n < NCB / 8; ++n) {
+                const uint32_t* wb = reinterpret_cast<const uint32_t*>(ws + (t * NCB + n * 8 + g) * PITCH);
                 mma_bf16_16816(acc[n], a0, a1, a2, a3, wb[tq], wb[tq + 4]);
+                if (SPLIT) mma_bf16_16816(acc[n], xa[LO + i0], xa[LO + i1], xa[LO + i0 + 4], xa[LO + i1 + 4], wb[tq],
+                                          wb[tq + 4]);
             }
         }
         __syncthreads();
@@ -168,24 +182,54 @@ __global__ void __launch_bounds__(256) k_conv3_mma(const bf16* __restrict__ in, 
     const int gy = y0 + warp;
     if (gy >= H) return;
 #pragma unroll
-    for (int n = 0; n < NCO / 8; ++n) {
-        const int co = n * 8 + 2 * tq;
-        const float bb0 = bias ? bias[co] : 0.f, bb1 = bias ? bias[co + 1] : 0.f;
+    for (int n = 0; n < NCB / 8; ++n) {
+        const int co = co0 + n * 8 + 2 * tq;
+        const float bb0 = (!SPLIT && bias) ? bias[co] : 0.f, bb1 = (!SPLIT && bias) ? bias[co + 1] : 0.f;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {                            // pixel g (c0, c1), pixel g + 8 (c2, c3)
             const int gx = x0 + g + 8 * h;
             if (gx >= Wd) continue;
             float v0 = acc[n][2 * h] + bb0, v1 = acc[n][2 * h + 1] + bb1;
-            if (relu) {
-                v0 = fmaxf(v0, 0.f);
-                v1 = fmaxf(v1, 0.f);
+            const size_t o = (((size_t)b * H + gy) * Wd + gx) * Cout + co;
+            if (SPLIT) {
+                *reinterpret_cast<float2*>(static_cast<float*>(out_) + o) = make_float2(v0, v1);
+            } else {
+                if (relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                __nv_bfloat162 pr;
+                pr.x = __float2bfloat16(v0);
+                pr.y = __float2bfloat16(v1);
+                *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(out_) + o) = pr;
             }
-            __nv_bfloat162 pr;
-            pr.x = __float2bfloat16(v0);
-            pr.y = __float2bfloat16(v1);
-            *reinterpret_cast<__nv_bfloat162*>(out + (((size_t)b * H + gy) * Wd + gx) * NCO + co) = pr;
         }
     }
+}
+
+// launch the tensor-core convolution for Cout output channels; false when
+// Cout has no supported channel chunk (the caller uses the FP32 kernel)
+template <bool SPLIT>
+bool conv3_mma(const void* in, int Cin, const bf16* W, const float* bias, void* out, int Cout, int B, int H, int Wd,
+               int relu, cudaStream_t s) {
+    int ncb = 0;
+    for (int c : {64, 56, 48, 40, 32, 16, 8})
+        if (Cout % c == 0) {
+            ncb = c;
+            break;
+        }
+    if (!ncb) return false;
+    const dim3 gm((Wd + 15) / 16, (H + 7) / 8, B * (Cout / ncb));
+    switch (ncb) {
+        case 64: k_conv3_mma<64, SPLIT><<<gm, 256, 0, s>>>(in, Cin, W, bias, out, Cout, H, Wd, relu); break;
+        case 56: k_conv3_mma<56, SPLIT><<<gm, 256, 0, s>>>(in, Cin, W, bias, out, Cout, H, Wd, relu); break;
+        case 48: k_conv3_mma<48, SPLIT><<<gm, 256, 0, s>>>(in, Cin, W, bias, out, Cout, H, Wd, relu); break;
+        case 40: k_conv3_mma<40, SPLIT><<<gm, 256, 0, s>>>(in, Cin, W, bias, out, Cout, H, Wd, relu); break;
+        case 32: k_conv3_mma<32, SPLIT><<<gm, 256, 0, s>>>(in, Cin, W, bias, out, Cout, H, Wd, relu); break;
+        case 16: k_conv3_mma<16, SPLIT><<<gm, 256, 0, s>>>(in, Cin, W, bias, out, Cout, H, Wd, relu); break;
+        default: k_conv3_mma<8, SPLIT><<<gm, 256, 0, s>>>(in, Cin, W, bias, out, Cout, H, Wd, relu); break;
+    }
+    return true;
 }
 
 // wt[t][co][ci] = w[8 - t][ci][co]: the backward-data convolution is a
@@ -508,17 +552,9 @@ int ensure_acts(lm_net* N, int B, int H, int W) {
 
 void conv_fwd(lm_net* N, const lm_net::Conv& c, const bf16* in, bf16* out, int B, int H, int W, cudaStream_t s) {
     count_launches(1);
-    const dim3 gm((W + 15) / 16, (H + 7) / 8, B);
     const bf16* w = N->wb + c.w;
     const float* bias = N->master + c.b;
-    switch (c.cout) {                           // tensor-core path for output widths that are multiples of 8
-        case 8: k_conv3_mma<8><<<gm, 256, 0, s>>>(in, c.cin, w, bias, out, H, W, 1); return;
-        case 16: k_conv3_mma<16><<<gm, 256, 0, s>>>(in, c.cin, w, bias, out, H, W, 1); return;
-        case 32: k_conv3_mma<32><<<gm, 256, 0, s>>>(in, c.cin, w, bias, out, H, W, 1); return;
-        case 48: k_conv3_mma<48><<<gm, 256, 0, s>>>(in, c.cin, w, bias, out, H, W, 1); return;
-        case 64: k_conv3_mma<64><<<gm, 256, 0, s>>>(in, c.cin, w, bias, out, H, W, 1); return;
-        default: break;
-    }
+    if (conv3_mma<false>(in, c.cin, w, bias, out, c.cout, B, H, W, 1, s)) return;
     const int ncoc = (c.cout + CT - 1) / CT;
     const dim3 grd((W + CT - 1) / CT, (H + CT - 1) / CT, B * ncoc);
     k_conv3<bf16, bf16><<<grd, dim3(CT, CT), 0, s>>>(in, c.cin, w, bias, out, c.cout, H, W, 1, ncoc);
@@ -526,9 +562,10 @@ void conv_fwd(lm_net* N, const lm_net::Conv& c, const bf16* in, bf16* out, int B
 
 // gin = conv3 backward-data of g (float32, Cout channels) through conv c
 void conv_bwd_data(lm_net* N, const lm_net::Conv& c, const float* g, float* gin, int B, int H, int W, cudaStream_t s) {
+    count_launches(1);
+    if (conv3_mma<true>(g, c.cout, N->wt + c.w, nullptr, gin, c.cin, B, H, W, 0, s)) return;
     const int ncoc = (c.cin + CT - 1) / CT;
     const dim3 grd((W + CT - 1) / CT, (H + CT - 1) / CT, B * ncoc);
-    count_launches(1);
     k_conv3<float, float><<<grd, dim3(CT, CT), 0, s>>>(g, c.cout, N->wt + c.w, nullptr, gin, c.cin, H, W, 0, ncoc);
 }
 

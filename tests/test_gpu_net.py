@@ -112,6 +112,36 @@ def test_gradients_match_oracle(lm):
     net.close()
 
 
+def test_gradients_at_production_widths(lm):
+    """Widths 16/32/48/64: every backward-data convolution (output widths 16
+    to 112, incl. the concatenations) runs on the tensor cores with the
+    split-precision input; gradients still match the oracle."""
+    ch = (16, 32, 48, 64)
+    rng = np.random.default_rng(12)
+    Pp = U.init_params(rng, cin=3, ch=ch)
+    for k in Pp:
+        if k.islower():
+            Pp[k] = rng.standard_normal(Pp[k].shape) * 0.1
+    x = rng.standard_normal((2, 16, 16, 3))
+    net = lm.Net(ch)
+    net.set_params(U.flat_params(Pp, 3, ch))
+    xd = torch.as_tensor(x.astype(np.float32).ravel(), device="cuda")
+    yd = torch.empty(2 * 256, device="cuda")
+    net.forward(xd, yd, 2, 16, 16)
+    gy = rng.standard_normal((2, 16, 16, 1))
+    net.backward(torch.as_tensor(gy.astype(np.float32).ravel(), device="cuda"))
+    g_gpu = U.unflat_params(net.grads(), 3, ch)
+    Q = _oracle_params_as_gpu_sees_them(Pp)
+    _, cache = U.forward(Q, x, ch, rnd=_bf16)
+    G, _ = U.backward(Q, cache, gy, ch)
+    a = np.concatenate([g_gpu[n].ravel() for n, _ in U.param_shapes(3, ch)])
+    b = np.concatenate([G[n].ravel() for n, _ in U.param_shapes(3, ch)])
+    assert np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)) > 0.9999
+    for n, _ in U.param_shapes(3, ch):
+        assert np.linalg.norm(g_gpu[n] - G[n]) <= 1e-2 * np.linalg.norm(G[n]) + 1e-6, n
+    net.close()
+
+
 def test_adam_reduces_loss_and_save_load(lm, tmp_path):
     rng, Pp, x = _setup(seed=7, B=4, H=32, W=32)
     net = lm.Net(CH)

@@ -43,7 +43,19 @@ PROBLEMS = {
     "box3d-64x16x24": lambda: I.make_problem(64, 24, 16, ma=0.01, contrast=20.0, noise=0.01, seed=7),
     "box3d-walls-32x8x16": lambda: I.make_problem(32, 16, 8, ma=0.02, contrast=10.0, noise=0.01, seed=8,
                                                   bc=(NEU, NEU, NEU)),
+    # the two-component semiconvection recipe (Ma = 0.001) on a downsized grid
+    "semi3d-32": lambda: I.config_semiconvection_3d(32),
 }
+
+
+_DIRECT = {}
+
+
+def _direct(name, p, op):
+    """The oracle's direct solve of a named problem (cached: the 3D ones take seconds)."""
+    if name not in _DIRECT:
+        _DIRECT[name] = P.solve_direct(op, p.f).ravel()
+    return _DIRECT[name]
 
 
 def _grid(p):
@@ -170,7 +182,7 @@ def test_jacobi_pcg_parity(name):
     """Row a3: float64 Jacobi-PCG solution vs the oracle's direct solve."""
     p = PROBLEMS[name]()
     op = P.operator_from_problem(p)
-    xs = P.solve_direct(op, p.f).ravel()
+    xs = _direct(name, p, op)
     with _grid(p) as g:
         r = g.solve(mode="jacobi", rtol=1e-13, max_iter=20000)
         x = g.solution()
@@ -189,7 +201,7 @@ def test_multigrid_modes_parity(name, mode, bar):
     iterative refinement around float32 FCG + V-cycle, vs the direct solve."""
     p = PROBLEMS[name]()
     op = P.operator_from_problem(p)
-    xs = P.solve_direct(op, p.f).ravel()
+    xs = _direct(name, p, op)
     with _grid(p) as g:
         r = g.solve(mode=mode, rtol=1e-13, max_iter=2000, max_outer=30)
         x = g.solution()
@@ -207,6 +219,25 @@ def test_mixed_config1_at_its_tolerance():
     assert r["status"] == 0 and r["rel_residual"] <= p.rtol
     assert P.rel_residual(op, x, p.f) <= p.rtol * 1.001
     assert r["outer_iters"] <= 5
+
+
+def test_smoothing_changes_between_solves():
+    """The inner iterations replay captured graphs keyed by the smoothing
+    counts: changing nu between solves on one grid gives the same bits as a
+    fresh grid solving with those counts."""
+    p = I.config_convection_3d(32, seed=9)
+    runs = [(1, 1), (2, 3), (1, 1), (3, 2)]
+    with _grid(p) as g:
+        got = []
+        for nu1, nu2 in runs:
+            r = g.solve(mode="mixed", rtol=1e-10, nu1=nu1, nu2=nu2)
+            assert r["status"] == 0
+            got.append(g.solution())
+    for (nu1, nu2), x in zip(runs, got):
+        with _grid(p) as g2:
+            g2.solve(mode="mixed", rtol=1e-10, nu1=nu1, nu2=nu2)
+            assert np.array_equal(g2.solution(), x)
+    assert np.array_equal(got[0], got[2])
 
 
 def test_deterministic_bitwise():
