@@ -425,8 +425,7 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
     constexpr int QA = (NA + NT2 - 1) / NT2;             // first-colour tasks per thread
     constexpr int QW = TX * TY / NT2;                    // written cells per thread
     static_assert(NB <= NT2 && SX + SY <= NT2 && QW * NT2 == TX * TY, "tile does not fit the block");
-    __shared__ float X[NR * PL];
-    __shared__ float R[NR * PL];
+    __shared__ float2 XR[NR * PL];                       // (x, rho) per staged cell: one 64-bit access
     __shared__ int ox[SX], oy[SY], pxy[SX + SY];
     const Geo& g = L.g;
     const int tid = threadIdx.x + 32 * threadIdx.y;
@@ -493,8 +492,7 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
 #pragma unroll
         for (int q = 0; q < QS; ++q)
             if (spos[q] >= 0) {
-                X[o + spos[q]] = PROLONG ? vx[q] + ve[q] : vx[q];
-                R[o + spos[q]] = vr[q];
+                XR[o + spos[q]] = make_float2(PROLONG ? vx[q] + ve[q] : vx[q], vr[q]);
             }
     };
 
@@ -502,21 +500,23 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
     // slot s0 (slots sm, sp: the planes below and above)
     auto gs = [&](int e, int sm, int s0, int sp, float fv, float cv) -> float {
         const int c = s0 + e;
-        const float rc = R[c];
-        const float wxm = L.c2x * rcp_fast(rc + R[c - 1]);
-        const float wxp = L.c2x * rcp_fast(rc + R[c + 1]);
-        const float wym = L.c2y * rcp_fast(rc + R[c - SX]);
-        const float wyp = L.c2y * rcp_fast(rc + R[c + SX]);
-        const float wzm = L.c2z * rcp_fast(rc + R[sm + e]);
-        const float wzp = L.c2z * rcp_fast(rc + R[sp + e]);
+        const float rc = XR[c].y;
+        const float2 nxm = XR[c - 1], nxp = XR[c + 1], nym = XR[c - SX], nyp = XR[c + SX];
+        const float2 nzm = XR[sm + e], nzp = XR[sp + e];
+        const float wxm = L.c2x * rcp_fast(rc + nxm.y);
+        const float wxp = L.c2x * rcp_fast(rc + nxp.y);
+        const float wym = L.c2y * rcp_fast(rc + nym.y);
+        const float wyp = L.c2y * rcp_fast(rc + nyp.y);
+        const float wzm = L.c2z * rcp_fast(rc + nzm.y);
+        const float wzp = L.c2z * rcp_fast(rc + nzp.y);
         const float d = cv + ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
         float num = fv;
-        num = fmaf(wxm, X[c - 1], num);
-        num = fmaf(wxp, X[c + 1], num);
-        num = fmaf(wym, X[c - SX], num);
-        num = fmaf(wyp, X[c + SX], num);
-        num = fmaf(wzm, X[sm + e], num);
-        num = fmaf(wzp, X[sp + e], num);
+        num = fmaf(wxm, nxm.x, num);
+        num = fmaf(wxp, nxp.x, num);
+        num = fmaf(wym, nym.x, num);
+        num = fmaf(wyp, nyp.x, num);
+        num = fmaf(wzm, nzm.x, num);
+        num = fmaf(wzp, nzp.x, num);
         return num * rcp_fast(d);
     };
 
@@ -617,15 +617,15 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
         // (2) first colour on plane p (tile + halo)
 #pragma unroll
         for (int u = 0; u < QA; ++u)
-            if (doA[u]) X[o0 + eAc[u]] = gs(eAc[u], om1, o0, op1, fA[u], cA[u]);
+            if (doA[u]) XR[o0 + eAc[u]].x = gs(eAc[u], om1, o0, op1, fA[u], cA[u]);
         load_a(p + 1, z1, p + 1 <= k1);                  // for the next step
         __syncthreads();
         // (3) second colour on plane p - 1 (tile)
-        if (doB) X[om1 + eBc] = gs(eBc, om2, om1, o0, fB, cB);
+        if (doB) XR[om1 + eBc].x = gs(eBc, om2, om1, o0, fB, cB);
         // (4) write plane p - 2
         if (p - 2 >= k0) {
 #pragma unroll
-            for (int v = 0; v < QW; ++v) xout[wbase[v] + sz * (p - 2)] = X[om2 + wpos[v]];
+            for (int v = 0; v < QW; ++v) xout[wbase[v] + sz * (p - 2)] = XR[om2 + wpos[v]].x;
         }
         // rotate to step p + 1
         const int t = om2;
