@@ -157,6 +157,15 @@ int build_mg(lm_grid* g, cudaStream_t s) {
         if (rc) return rc;
         launch_coarse_inverse(Lc.L, s, Lc.ainv);
     }
+    // the one-block coarse V-cycle takes over from the first level small
+    // enough, when the chain ends in a directly solved level
+    g->cc_level = -1;
+    if (g->mg.back().ainv)
+        for (size_t l = 0; l < g->mg.size(); ++l)
+            if (g->mg[l].L.g.N <= CC_MAX_CELLS && g->mg.size() - l <= (size_t)CC_MAXL && g->mg.size() - l >= 2) {
+                g->cc_level = (int)l;
+                break;
+            }
     CK(cudaGetLastError());
     g->mg_built = true;
     return LM_OK;
@@ -190,6 +199,24 @@ float* sweep_chain(MgLevel& M, cudaStream_t s, int count, const int* first, cons
 // adjoint order), so the cycle is symmetric for nu1 == nu2.
 void vcycle(lm_grid* g, int l, float* xout, const float* f, int nu1, int nu2, cudaStream_t s) {
     MgLevel& M = g->mg[l];
+    if (l == g->cc_level) {          // the rest of the cycle in one block
+        CoarseCycle cc{};
+        cc.nl = (int)g->mg.size() - l;
+        for (int i = 0; i < cc.nl; ++i) {
+            const MgLevel& Li = g->mg[l + i];
+            cc.L[i] = Li.L;
+            cc.hx[i] = Li.halved[0];
+            cc.hy[i] = Li.halved[1];
+            cc.hz[i] = Li.halved[2];
+            cc.x[i] = i == 0 ? xout : Li.xo;
+            cc.f[i] = i == 0 ? const_cast<float*>(f) : Li.f;
+        }
+        cc.ainv = g->mg.back().ainv;
+        cc.nu1 = nu1;
+        cc.nu2 = nu2;
+        launch_coarse_cycle(cc, s);
+        return;
+    }
     const bool last = (size_t)l + 1 == g->mg.size();
     int order[2 * COARSE_SWEEPS + 8];
     if (last) {

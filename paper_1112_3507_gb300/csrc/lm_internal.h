@@ -72,6 +72,7 @@ struct lm_grid {
     float* feat = nullptr;          // network input (N x 3)
     float* nny = nullptr;           // network output (N)
     std::vector<lm::MgLevel> mg;
+    int cc_level = -1;              // first level of the one-block coarse V-cycle (-1: none)
     std::vector<double> history;
     // CUDA graphs of one inner flexible-CG iteration with the V-cycle (the
     // first and the later ones), captured on cap_stream for hierarchy

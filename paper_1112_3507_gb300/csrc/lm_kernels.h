@@ -96,6 +96,20 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
                     int hy, int hz, const float* f, float* xout, int first, int zero, int prolong, int kz);
 void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s,
                            const float* x, const float* f, float* fc);
+// A whole coarse V-cycle (levels with at most CC_MAX_CELLS cells down to a
+// directly solved coarsest level) run by one block.
+constexpr int CC_MAXL = 5;
+constexpr int CC_MAX_CELLS = 4096;
+struct CoarseCycle {
+    int nl;                        // levels in the chain; the last is solved with ainv
+    Lev32 L[CC_MAXL];
+    int hx[CC_MAXL], hy[CC_MAXL], hz[CC_MAXL];   // halvings from chain level i to i + 1
+    float* x[CC_MAXL];             // level solutions (chain level 0: the caller's output)
+    float* f[CC_MAXL];             // level right-hand sides (chain level 0: the caller's rhs)
+    const float* ainv;
+    int nu1, nu2;
+};
+void launch_coarse_cycle(const CoarseCycle& cc, cudaStream_t s);
 void launch_coarse_inverse(const Lev32& L, cudaStream_t s, float* ainv);
 void launch_coarse_solve(int n, cudaStream_t s, const float* ainv, const float* f, float* x);
 
