@@ -52,8 +52,8 @@ DEFAULT_MODE = {"train2d": "learned"}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from an ncu
 # capture of the same kernel build on this workload, keyed (workload, kernel)
 NCU_TRAFFIC: dict = {
-    # plain level-0 sweep of the 256^3 workload: 286.3 MB read + 51.6 MB written
-    ("convection256", "k_rbgs_zm"): 337.91e6,
+    # plain level-0 sweep of the 256^3 workload: 282.7 MB read + 52.5 MB written
+    ("convection256", "k_rbgs_zm"): 335.20e6,
 }
 WEIGHTS = os.path.join(ROOT, "paper_1112_3507_gb300", "weights", "unet_16_32_48_64.bin")
 
