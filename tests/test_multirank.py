@@ -64,3 +64,18 @@ def test_reference_arm_does_no_work_off_rank_0(monkeypatch, capsys):
         workload, warmup, steps, oracle_iters, gpus = "plain64", 0, 1, 1, 2
     assert bench.run_reference(A()) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the CPU oracle and prints one JSON line
+    with the GPU arm's metric and unit (run on the smallest workload)."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "plain64", "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=600,
+                       env=dict(os.environ, RANK="0"))
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "GDOF/s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["steps"] == 2
