@@ -284,7 +284,7 @@ int  lm_net_features(lm_grid* g, const double* v, float* feat, double* scale, vo
  * grid's status; LM_ERR_INVALID_ARG / LM_ERR_STATE before any work. */
 int  lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* opts, lm_solve_result* results);
 
-/* Autotuner cache: a JSON object {"<gpu>|rbgs2d|<nx>x<nz>|bc<x><z>|f32": kz,
+/* Autotuner cache: a JSON object {"<gpu>|rbgs2d-zm|<nx>x<nz>|bc<x><z>|f32": kz,
  * ...} of the fastest sweep z-chunk per level shape, read on first use and
  * rewritten when new shapes are timed.  Default path: $LM_AUTOTUNE_CACHE or
  * $HOME/.cache/lowmach_autotune.json.  NULL or "" restores the default.

@@ -145,7 +145,10 @@ __global__ void __launch_bounds__(128, 8) kb_rbgs_pre(const BTask* __restrict__ 
     const BTask t = T[blockIdx.x];
     if (inner_off(Gs[t.g])) return;
     const BLev& V = Ls[t.l];
-    rbgs_tile<128, 1, false, 0, true, false>(V.L, nullptr, nullptr, V.C, 0, 0, 0, V.f, V.xa, V.kz, t.bx, t.by, 0);
+    if (V.L.g.nx % 256 == 0 && V.L.g.nz >= 2)        // whole 256-cell rows: the z-march (same tiles)
+        zm2d_tile<0, true, false>(V.L, nullptr, nullptr, V.C, 0, 0, V.f, V.xa, V.kz, t.bx, t.by);
+    else
+        rbgs_tile<128, 1, false, 0, true, false>(V.L, nullptr, nullptr, V.C, 0, 0, 0, V.f, V.xa, V.kz, t.bx, t.by, 0);
 }
 
 __global__ void __launch_bounds__(128, 8) kb_rbgs_post(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
@@ -153,8 +156,11 @@ __global__ void __launch_bounds__(128, 8) kb_rbgs_post(const BTask* __restrict__
     const BTask t = T[blockIdx.x];
     if (inner_off(Gs[t.g])) return;
     const BLev& V = Ls[t.l];
-    rbgs_tile<128, 1, false, 1, false, true>(V.L, V.xa, V.ec, V.C, V.hx, V.hy, V.hz, V.f, V.xo, V.kz, t.bx, t.by,
-                                             0);
+    if (V.L.g.nx % 256 == 0 && V.L.g.nz >= 2)
+        zm2d_tile<1, false, true>(V.L, V.xa, V.ec, V.C, V.hx, V.hz, V.f, V.xo, V.kz, t.bx, t.by);
+    else
+        rbgs_tile<128, 1, false, 1, false, true>(V.L, V.xa, V.ec, V.C, V.hx, V.hy, V.hz, V.f, V.xo, V.kz, t.bx,
+                                                 t.by, 0);
 }
 
 __global__ void __launch_bounds__(256) kb_resid_restrict(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
@@ -330,7 +336,7 @@ std::string gpu_name() {
 // on this level's own data (into its scratch buffer), remembered per shape.
 int tune_sweep_kz(const MgLevel& M, const float* fin, float* scratch, cudaStream_t s, bool* changed) {
     char key[256];
-    snprintf(key, sizeof key, "%s|rbgs2d|%dx%d|bc%d%d|f32", gpu_name().c_str(), M.L.g.nx, M.L.g.nz, M.L.g.bcx,
+    snprintf(key, sizeof key, "%s|rbgs2d-zm|%dx%d|bc%d%d|f32", gpu_name().c_str(), M.L.g.nx, M.L.g.nz, M.L.g.bcx,
              M.L.g.bcz);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) return it->second;

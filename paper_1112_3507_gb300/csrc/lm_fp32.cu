@@ -646,6 +646,13 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
     }
 }
 
+template <int FIRST, bool ZERO, bool PROLONG>
+__global__ void __launch_bounds__(128) k_rbgs_zm2d(Lev32 L, const float* __restrict__ xin,
+                                                  const float* __restrict__ ec, Geo C, int hx, int hz,
+                                                  const float* __restrict__ f, float* __restrict__ xout, int KZ) {
+    zm2d_tile<FIRST, ZERO, PROLONG>(L, xin, ec, C, hx, hz, f, xout, KZ, blockIdx.x, blockIdx.y);
+}
+
 template <int BX, int TY, bool HAS_Y, int FIRST, bool ZERO, bool PROLONG>
 __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, const float* __restrict__ xin,
                                                                    const float* __restrict__ ec, Geo C, int hx,
@@ -964,6 +971,18 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
         else if (prolong) { if (first) LM_RB(1, false, true); else LM_RB(0, false, true); }
         else { if (first) LM_RB(1, false, false); else LM_RB(0, false, false); }
 #undef LM_RB
+    } else if (g.ny == 1 && g.nx % 256 == 0 && g.nz >= 2) {
+        // 2D whole 256-cell rows: the in-place z-march; KZ rows per block
+        const int tiles = g.nx / 256;
+        int KZ = kz > 0 ? kz : 32;
+        if (kz <= 0)
+            while (KZ > 2 && (long long)tiles * hdiv(g.nz, KZ) < 1216) KZ /= 2;
+        const dim3 grd(tiles, hdiv(g.nz, KZ));
+#define LM_RB2(F, Z, P) k_rbgs_zm2d<F, Z, P><<<grd, 128, 0, s>>>(L, xin, ec, Cg, hx, hz, f, xout, KZ)
+        if (zero) { if (first) LM_RB2(1, true, false); else LM_RB2(0, true, false); }
+        else if (prolong) { if (first) LM_RB2(1, false, true); else LM_RB2(0, false, true); }
+        else { if (first) LM_RB2(1, false, false); else LM_RB2(0, false, false); }
+#undef LM_RB2
     } else {
         constexpr int BX = 128, TY = 1;
         const int tiles = hdiv(g.nx, 2 * BX);

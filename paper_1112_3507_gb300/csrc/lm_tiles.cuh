@@ -516,4 +516,210 @@ __device__ __forceinline__ void coarse_solve_block(int n, const float* __restric
     x[i] = s;
 }
 
+// ---- 2D red-black sweep on whole 256-cell rows: in-place z-march -----------
+//
+// The 2D counterpart of the 3D z-march sweep, for levels (ny = 1) whose nx is
+// a multiple of 256, on blocks of 128 threads: the block owns 256 columns
+// over a chunk of KZ rows and marches up z with a five-row ring of (x, rho)
+// staged on the row plus two cells (periodic x wrapped; past a wall x = 0
+// and rho = +inf, so that face's weight is 0).  At step p it stores row
+// p + 1 and issues the loads of row p + 2, updates the FIRST colour of row p
+// on the tile plus one cell each side in place (a first-colour update reads
+// only second-colour neighbours), the second colour of row p - 1, and
+// writes row p - 2.  Used by the single-grid sweep and the batched solver
+// (the same 256-wide tiles and row chunks as rbgs_tile).
+__device__ __forceinline__ float rcp_hw(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <int FIRST, bool ZERO, bool PROLONG>
+__device__ __forceinline__ void zm2d_tile(const Lev32& L, const float* __restrict__ xin,
+                                          const float* __restrict__ ec, const Geo& C, int hx, int hz,
+                                          const float* __restrict__ f, float* __restrict__ xout, int KZ, int bx,
+                                          int bz) {
+    constexpr int NT2 = 128, TX = 256, SX = TX + 4, NR = 5;
+    constexpr int NA = (TX + 2) / 2, NB = TX / 2;
+    constexpr int QS = (SX + NT2 - 1) / NT2, QA = (NA + NT2 - 1) / NT2, QW = TX / NT2;
+    __shared__ float2 XR[NR * SX];
+    __shared__ int ox[SX], px[SX];
+    __syncthreads();                                     // shared tiles may be reused by the next task
+    const Geo& g = L.g;
+    const int tid = threadIdx.x;
+    const int i0 = bx * TX;
+    const int k0 = bz * KZ, k1 = min(k0 + KZ, g.nz);
+    for (int t = tid; t < SX; t += NT2) {
+        int c = i0 - 2 + t;
+        if (c < 0) c = g.bcx == LM_BC_PERIODIC ? c + g.nx : -1;
+        else if (c >= g.nx) c = g.bcx == LM_BC_PERIODIC ? c - g.nx : -1;
+        ox[t] = c;
+        px[t] = c >> hx;
+    }
+    __syncthreads();
+    auto zwrap = [&](int p) -> int { return ((p % g.nz) + g.nz) % g.nz; };
+    auto zoff = [&](int p) -> int {
+        if (p >= 0 && p < g.nz) return g.nx * p;
+        return g.bcz == LM_BC_PERIODIC ? g.nx * zwrap(p) : -1;
+    };
+    auto zpar = [&](int p) -> int { return C.nx * (zwrap(p) >> hz); };
+    int spos[QS], sbase[QS], spar[QS];
+    bool sok[QS];
+#pragma unroll
+    for (int q = 0; q < QS; ++q) {
+        spos[q] = tid + q * NT2;
+        const bool use = spos[q] < SX;
+        sok[q] = use && ox[use ? spos[q] : 0] >= 0;
+        sbase[q] = use ? ox[spos[q]] : 0;
+        spar[q] = use ? px[spos[q]] : 0;
+        if (!use) spos[q] = -1;
+    }
+    float vx[QS], vr[QS], ve[QS];
+    auto fetch = [&](int zo, int zp) {
+#pragma unroll
+        for (int q = 0; q < QS; ++q) {
+            vx[q] = 0.f;
+            ve[q] = 0.f;
+            vr[q] = __int_as_float(0x7f800000);          // +inf
+            if (sok[q] && zo >= 0) {
+                const int idx = sbase[q] + zo;
+                vr[q] = L.rho[idx];
+                if (!ZERO) {
+                    vx[q] = xin[idx];
+                    if (PROLONG) ve[q] = ec[spar[q] + zp];
+                }
+            }
+        }
+    };
+    auto store = [&](int o) {
+#pragma unroll
+        for (int q = 0; q < QS; ++q)
+            if (spos[q] >= 0) XR[o + spos[q]] = make_float2(PROLONG ? vx[q] + ve[q] : vx[q], vr[q]);
+    };
+    auto gs = [&](int e, int sm, int s0, int sp, float fv, float cv) -> float {
+        const int c = s0 + e;
+        const float rc = XR[c].y;
+        const float2 nxm = XR[c - 1], nxp = XR[c + 1], nzm = XR[sm + e], nzp = XR[sp + e];
+        const float wxm = L.c2x * rcp_hw(rc + nxm.y);
+        const float wxp = L.c2x * rcp_hw(rc + nxp.y);
+        const float wzm = L.c2z * rcp_hw(rc + nzm.y);
+        const float wzp = L.c2z * rcp_hw(rc + nzp.y);
+        const float d = cv + (wxm + wxp) + (wzm + wzp);
+        float num = fv;
+        num = fmaf(wxm, nxm.x, num);
+        num = fmaf(wxp, nxp.x, num);
+        num = fmaf(wzm, nzm.x, num);
+        num = fmaf(wzp, nzp.x, num);
+        return num * rcp_hw(d);
+    };
+    // first-colour tasks: pair am of the halo row (x positions 2am and 2am + 1
+    // of the staged row shifted by one); second-colour task: pair bm of the tile
+    bool hasA[QA];
+    int aeE[QA], aoE[QA], aoO[QA];
+#pragma unroll
+    for (int u = 0; u < QA; ++u) {
+        const int am = tid + u * NT2;
+        hasA[u] = am < NA;
+        aeE[u] = 2 * (hasA[u] ? am : 0) + 1;
+        aoE[u] = ox[aeE[u]];
+        aoO[u] = ox[aeE[u] + 1];
+    }
+    const int apar = (FIRST + i0) & 1;
+    const int bpar = (1 - FIRST + i0) & 1;
+    const int beE = 2 * tid + 2;
+    const int bidxE = i0 + 2 * tid;
+    int wpos[QW], wbase[QW];
+#pragma unroll
+    for (int v = 0; v < QW; ++v) {
+        wpos[v] = tid + v * NT2 + 2;
+        wbase[v] = i0 + tid + v * NT2;
+    }
+    int om2 = 0 * SX, om1 = 1 * SX, o0 = 2 * SX, op1 = 3 * SX, op2 = 4 * SX;
+    int z0 = zoff(k0 - 1), z1 = zoff(k0), z2 = zoff(k0 + 1);
+    int zp2 = PROLONG ? zpar(k0 + 1) : 0;
+    fetch(zoff(k0 - 2), PROLONG ? zpar(k0 - 2) : 0);
+    store(om1);
+    fetch(z0, PROLONG ? zpar(k0 - 1) : 0);
+    store(o0);
+    fetch(z1, PROLONG ? zpar(k0) : 0);
+    float fa[QA], ca[QA];
+    bool okA[QA];
+    int eA[QA];
+    auto load_a = [&](int p, int zo, bool in_chunk) {
+#pragma unroll
+        for (int u = 0; u < QA; ++u) {
+            // staged position aeE + odd is global x = i0 - 1 + 2 am + odd, of
+            // colour (x + p) & 1 = FIRST when odd = (FIRST + i0 + p + 1) & 1
+            const int odd = (apar + p + 1) & 1;
+            const int a = odd ? aoO[u] : aoE[u];
+            okA[u] = hasA[u] && in_chunk && (a | zo) >= 0;
+            eA[u] = aeE[u] + odd;
+            fa[u] = 0.f;
+            ca[u] = 1.f;
+            if (okA[u]) {
+                fa[u] = f[a + zo];
+                ca[u] = L.ct[a + zo];
+            }
+        }
+    };
+    load_a(k0 - 1, z0, true);
+    float fb = 0.f, cb = 1.f;
+    bool okB = false;
+    int eB = 0;
+    for (int p = k0 - 1; p <= k1 + 1; ++p) {
+        if (p <= k1) store(op1);
+        if (p + 1 <= k1) fetch(z2, zp2);
+        float fA[QA], cA[QA];
+        bool doA[QA];
+        int eAc[QA];
+#pragma unroll
+        for (int u = 0; u < QA; ++u) {
+            fA[u] = fa[u];
+            cA[u] = ca[u];
+            doA[u] = okA[u] && p <= k1;
+            eAc[u] = eA[u];
+        }
+        const float fB = fb, cB = cb;
+        const bool doB = okB;
+        const int eBc = eB;
+        {
+            const int odd = (bpar + p) & 1;
+            okB = p >= k0 && p < k1;
+            eB = beE + odd;
+            if (okB) {
+                const int idx = bidxE + odd + g.nx * p;
+                fb = f[idx];
+                cb = L.ct[idx];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < QA; ++u)
+            if (doA[u]) XR[o0 + eAc[u]].x = gs(eAc[u], om1, o0, op1, fA[u], cA[u]);
+        load_a(p + 1, z1, p + 1 <= k1);
+        __syncthreads();
+        if (doB) XR[om1 + eBc].x = gs(eBc, om2, om1, o0, fB, cB);
+        if (p - 2 >= k0) {
+#pragma unroll
+            for (int v = 0; v < QW; ++v) xout[wbase[v] + g.nx * (p - 2)] = XR[om2 + wpos[v]].x;
+        }
+        const int t = om2;
+        om2 = om1;
+        om1 = o0;
+        o0 = op1;
+        op1 = op2;
+        op2 = t;
+        z0 = z1;
+        z1 = z2;
+        {
+            int c = p + 3;
+            if (c >= g.nz) c -= g.nz;
+            if (c >= g.nz) c -= g.nz;
+            const bool ok = (p + 3 < g.nz || g.bcz == LM_BC_PERIODIC) && c >= 0 && c < g.nz;
+            z2 = ok ? g.nx * c : -1;
+            if (PROLONG) zp2 = C.nx * ((ok ? c : 0) >> hz);
+        }
+    }
+}
+
 }  // namespace lm

@@ -64,7 +64,7 @@ def test_batch_matches_oracle_and_single_path(lm, tmp_path):
         for g in grids:
             g.close()
     tuned = json.loads(cache.read_text())
-    assert any("|rbgs2d|" in k for k in tuned) and all(v in (4, 8, 16, 32, 64) for v in tuned.values())
+    assert any("|rbgs2d-zm|" in k for k in tuned) and all(v in (4, 8, 16, 32, 64) for v in tuned.values())
 
 
 def test_batch_uneven_convergence_and_tolerance(lm, tmp_path):

@@ -45,6 +45,10 @@ PROBLEMS = {
                                                   bc=(NEU, NEU, NEU)),
     # the two-component semiconvection recipe (Ma = 0.001) on a downsized grid
     "semi3d-32": lambda: I.config_semiconvection_3d(32),
+    # whole 256-cell rows: the 2D z-march sweep
+    "rows2d-256x24": lambda: I.make_problem(256, 24, ma=0.01, contrast=15.0, noise=0.01, seed=10),
+    "rows2d-walls-512x10": lambda: I.make_problem(512, 10, ma=0.05, contrast=8.0, noise=0.01, seed=11,
+                                                  bc=(NEU, PER, NEU)),
 }
 
 
@@ -125,7 +129,8 @@ def test_apply_fp32(name):
 
 @pytest.mark.parametrize("name,nu", [("plain2d-64", 1), ("conv3d-16", 1), ("ragged3d-12x6x10", 1),
                                      ("ragged2d-37x50-walls", 1), ("conv3d-16", 2), ("plain2d-64", 3),
-                                     ("box3d-64x16x24", 1), ("box3d-64x16x24", 2), ("box3d-walls-32x8x16", 2)])
+                                     ("box3d-64x16x24", 1), ("box3d-64x16x24", 2), ("box3d-walls-32x8x16", 2),
+                                     ("rows2d-256x24", 2), ("rows2d-walls-512x10", 1)])
 def test_vcycle_matches_oracle(name, nu):
     """Row a4: one float32 V-cycle z = M r vs the oracle's float64 V-cycle on
     the same (float32-rounded) coefficients; same hierarchy."""
@@ -150,7 +155,8 @@ def test_vcycle_matches_oracle(name, nu):
 
 
 @pytest.mark.parametrize("name", ["plain2d-64", "conv3d-16", "ragged3d-12x6x10", "ragged2d-37x50-walls",
-                                  "column-1x1x40", "box3d-64x16x24", "box3d-walls-32x8x16"])
+                                  "column-1x1x40", "box3d-64x16x24", "box3d-walls-32x8x16", "rows2d-256x24",
+                                  "rows2d-walls-512x10"])
 @pytest.mark.parametrize("order", [0, 1])
 def test_sweep_matches_oracle(name, order):
     """Row a4 smoother: one float32 red-black (or black-red) Gauss-Seidel
