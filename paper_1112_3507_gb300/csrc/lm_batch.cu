@@ -171,6 +171,14 @@ __global__ void __launch_bounds__(256) kb_resid_restrict(const BTask* __restrict
     resid_restrict_tile(V.L, V.C, V.hx, V.hy, V.hz, V.xa, V.f, V.fc, t.bx, t.by, t.bz);
 }
 
+// one block per grid: the grid's coarse V-cycle (its levels from the one-block
+// cycle's first level down), in place of the per-level launches there
+__global__ void __launch_bounds__(1024) kb_coarse_cycle(const CoarseCycle* __restrict__ ccs,
+                                                        const BGrid* __restrict__ Gs) {
+    if (inner_off(Gs[blockIdx.x])) return;
+    coarse_cycle_block(ccs[blockIdx.x]);
+}
+
 __global__ void kb_coarse(const BTask* __restrict__ T, const BGrid* __restrict__ Gs, const BLev* __restrict__ Ls) {
     const BTask t = T[blockIdx.x];
     if (inner_off(Gs[t.g])) return;
@@ -381,6 +389,7 @@ struct Plan {
     SolveState* hgather = nullptr;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t g_first = nullptr, g_step = nullptr;
+    CoarseCycle* dcc = nullptr;          // per-grid one-block coarse cycles (null: per-level launches)
     int max_depth = 0;
     long long n_first = 0, n_step = 0;   // kernels per graph launch
 
@@ -392,6 +401,7 @@ struct Plan {
         cudaFree(dlevs);
         cudaFree(dlev0);
         cudaFree(dtasks);
+        cudaFree(dcc);
         cudaFree(dgather);
         cudaFreeHost(hgather);
     }
@@ -502,11 +512,44 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
             for (int bx = 0; bx < gx; ++bx) tasks.push_back(BTask{i, lev0[i], bx, by, 0, bx + gx * by, gx * gy});
     }
     tap.n = (int)tasks.size() - tap.off;
+    // one-block coarse cycles when every grid's hierarchy has one: the
+    // per-level task lists then stop at each grid's coarse-cycle level
+    bool fused = true;
+    std::vector<int> lstop(count);
+    for (int i = 0; i < count; ++i) {
+        fused = fused && grids[i]->cc_level >= 0;
+        lstop[i] = nlev[i] - 1;
+    }
+    if (fused) {
+        std::vector<CoarseCycle> hcc(count);
+        for (int i = 0; i < count; ++i) {
+            lm_grid* g = grids[i];
+            const int lc = g->cc_level;
+            lstop[i] = lc;
+            CoarseCycle& cc = hcc[i];
+            cc = CoarseCycle{};
+            cc.nl = (int)g->mg.size() - lc;
+            for (int k = 0; k < cc.nl; ++k) {
+                const MgLevel& Mk = g->mg[lc + k];
+                cc.L[k] = Mk.L;
+                cc.hx[k] = Mk.halved[0];
+                cc.hy[k] = Mk.halved[1];
+                cc.hz[k] = Mk.halved[2];
+                cc.x[k] = (lc + k == 0) ? g->z32 : Mk.xo;
+                cc.f[k] = (lc + k == 0) ? g->r32 : Mk.f;
+            }
+            cc.ainv = g->mg.back().ainv;
+            cc.nu1 = 1;
+            cc.nu2 = 1;
+        }
+        BCK(cudaMalloc(&P->dcc, sizeof(CoarseCycle) * count));
+        BCK(cudaMemcpy(P->dcc, hcc.data(), sizeof(CoarseCycle) * count, cudaMemcpyHostToDevice));
+    }
     std::vector<TaskList> tpre(P->max_depth), trr(P->max_depth);
     for (int d = 0; d < P->max_depth; ++d) {
         tpre[d].off = (int)tasks.size();
         for (int i = 0; i < count; ++i) {
-            if (d >= nlev[i] - 1) continue;
+            if (d >= lstop[i]) continue;
             const BLev& V = hl[lev0[i] + d];
             const int gx = hdiv(V.L.g.nx, 256), gy = hdiv(V.L.g.nz, V.kz);
             for (int by = 0; by < gy; ++by)
@@ -515,7 +558,7 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
         tpre[d].n = (int)tasks.size() - tpre[d].off;
         trr[d].off = (int)tasks.size();
         for (int i = 0; i < count; ++i) {
-            if (d >= nlev[i] - 1) continue;
+            if (d >= lstop[i]) continue;
             const BLev& V = hl[lev0[i] + d];
             const int gx = hdiv(V.C.nx, 32), gy = hdiv(V.C.nz, 8);
             for (int by = 0; by < gy; ++by)
@@ -554,7 +597,8 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
                 if (tpre[d].n) kb_rbgs_pre<<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls);
                 if (trr[d].n) kb_resid_restrict<<<trr[d].n, dim3(32, 8), 0, cs>>>(T + trr[d].off, Gs, Ls);
             }
-            kb_coarse<<<tco.n, 64, 0, cs>>>(T + tco.off, Gs, Ls);
+            if (P->dcc) kb_coarse_cycle<<<count, 1024, 0, cs>>>(P->dcc, Gs);
+            else kb_coarse<<<tco.n, 64, 0, cs>>>(T + tco.off, Gs, Ls);
             for (int d = P->max_depth - 1; d >= 0; --d)
                 if (tpre[d].n) kb_rbgs_post<<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls);
             if (it > 0) kb_dot_zq<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs);

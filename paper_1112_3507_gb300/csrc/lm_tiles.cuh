@@ -722,4 +722,94 @@ __device__ __forceinline__ void zm2d_tile(const Lev32& L, const float* __restric
     }
 }
 
+// ---- the coarse V-cycle in one block (see k_coarse_cycle) ------------------
+__device__ __forceinline__ float gs_cell32(const Lev32& L, const float* x, const float* f, int idx, int i, int j,
+                                           int k) {
+    const Geo& g = L.g;
+    const float rc = L.rho[idx];
+    const Nbr nx = nbr_x(idx, i, g), ny = nbr_y(idx, j, g), nz = nbr_z(idx, k, g);
+    const bool fxm = face_minus(i, g.nx, g.bcx), fxp = face_plus(i, g.nx, g.bcx);
+    const bool fym = face_minus(j, g.ny, g.bcy), fyp = face_plus(j, g.ny, g.bcy);
+    const bool fzm = face_minus(k, g.nz, g.bcz), fzp = face_plus(k, g.nz, g.bcz);
+    const float wxm = fxm ? face32(rc, L.rho[nx.im], L.c2x) : 0.f;
+    const float wxp = fxp ? face32(rc, L.rho[nx.ip], L.c2x) : 0.f;
+    const float wym = fym ? face32(rc, L.rho[ny.im], L.c2y) : 0.f;
+    const float wyp = fyp ? face32(rc, L.rho[ny.ip], L.c2y) : 0.f;
+    const float wzm = fzm ? face32(rc, L.rho[nz.im], L.c2z) : 0.f;
+    const float wzp = fzp ? face32(rc, L.rho[nz.ip], L.c2z) : 0.f;
+    const float d = L.ct[idx] + ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
+    float num = f[idx];
+    num = fmaf(wxm, fxm ? x[nx.im] : 0.f, num);
+    num = fmaf(wxp, fxp ? x[nx.ip] : 0.f, num);
+    num = fmaf(wym, fym ? x[ny.im] : 0.f, num);
+    num = fmaf(wyp, fyp ? x[ny.ip] : 0.f, num);
+    num = fmaf(wzm, fzm ? x[nz.im] : 0.f, num);
+    num = fmaf(wzp, fzp ? x[nz.ip] : 0.f, num);
+    return __fdividef(num, d);
+}
+
+__device__ __forceinline__ void coarse_cycle_block(const CoarseCycle& cc) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    auto colour = [&](int l, int col) {                  // update every cell of colour col in place
+        const Lev32& L = cc.L[l];
+        const Geo& g = L.g;
+        for (int idx = tid; idx < g.N; idx += nt) {
+            int i, j, k;
+            cell_coords(idx, g, i, j, k);
+            if (((i + j + k) & 1) == col) cc.x[l][idx] = gs_cell32(L, cc.x[l], cc.f[l], idx, i, j, k);
+        }
+        __syncthreads();
+    };
+    for (int l = 0; l + 1 < cc.nl; ++l) {
+        const Lev32& L = cc.L[l];
+        for (int idx = tid; idx < L.g.N; idx += nt) cc.x[l][idx] = 0.f;
+        __syncthreads();
+        for (int it = 0; it < cc.nu1; ++it) {
+            colour(l, 0);
+            colour(l, 1);
+        }
+        const Geo& C = cc.L[l + 1].g;
+        const int hx = cc.hx[l], hy = cc.hy[l], hz = cc.hz[l];
+        const float inv = 1.f / (float)((1 << hx) << hy << hz);
+        for (int e = tid; e < C.N; e += nt) {
+            int I, J, K;
+            cell_coords(e, C, I, J, K);
+            float sum = 0.f;
+            for (int c = 0; c <= hz; ++c)
+                for (int b = 0; b <= hy; ++b)
+                    for (int a = 0; a <= hx; ++a) {
+                        const int i = (I << hx) + a, j = (J << hy) + b, k = (K << hz) + c;
+                        const int idx = i + L.g.nx * (j + L.g.ny * k);
+                        sum += cc.f[l][idx] - apply32_at(idx, i, j, k, L, cc.x[l]);
+                    }
+            cc.f[l + 1][e] = sum * inv;
+        }
+        __syncthreads();
+    }
+    {
+        const int last = cc.nl - 1, n = cc.L[last].g.N;
+        for (int r = tid; r < n; r += nt) {
+            float v = 0.f;
+            for (int c = 0; c < n; ++c) v = fmaf(cc.ainv[r * n + c], cc.f[last][c], v);
+            cc.x[last][r] = v;
+        }
+        __syncthreads();
+    }
+    for (int l = cc.nl - 2; l >= 0; --l) {
+        const Lev32& L = cc.L[l];
+        const Geo& C = cc.L[l + 1].g;
+        const int hx = cc.hx[l], hy = cc.hy[l], hz = cc.hz[l];
+        for (int idx = tid; idx < L.g.N; idx += nt) {
+            int i, j, k;
+            cell_coords(idx, L.g, i, j, k);
+            cc.x[l][idx] += cc.x[l + 1][(i >> hx) + C.nx * ((j >> hy) + C.ny * (k >> hz))];
+        }
+        __syncthreads();
+        for (int it = 0; it < cc.nu2; ++it) {
+            colour(l, 1);
+            colour(l, 0);
+        }
+    }
+}
+
 }  // namespace lm

@@ -67,6 +67,26 @@ def test_batch_matches_oracle_and_single_path(lm, tmp_path):
     assert any("|rbgs2d-zm|" in k for k in tuned) and all(v in (4, 8, 16, 32, 64) for v in tuned.values())
 
 
+def test_batch_whole_row_grids_match_oracle(lm, tmp_path):
+    """Sides 64..512 (the workload's divided by 2): the whole-row 2D sweep and
+    the per-grid one-block coarse cycles inside the batched graph."""
+    lm.autotune_set_cache(str(tmp_path / "tune.json"))
+    problems = I.config_batch(count=4, seed=5, scale=2)
+    assert any(p.n[0] % 256 == 0 for p in problems)
+    grids = _batch(lm, problems)
+    try:
+        res = lm.batch_solve(grids, rtol=1e-11, max_outer=12, inner_max_iter=12)
+        for p, g, r in zip(problems, grids, res):
+            assert r["status"] == 0 and r["rel_residual"] <= 1e-11, r
+            op = P.operator_from_problem(p)
+            xs = P.solve_direct(op, p.f).ravel()
+            x = g.solution()
+            assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs), p.name
+    finally:
+        for g in grids:
+            g.close()
+
+
 def test_batch_uneven_convergence_and_tolerance(lm, tmp_path):
     """Grids converge at different steps; each stops at its own tolerance."""
     lm.autotune_set_cache(str(tmp_path / "t.json"))
