@@ -102,8 +102,17 @@ bool mg_supported(const lm_grid* g) {
 }
 
 // Multigrid hierarchy from the float32 coefficients (coarse c~, rho = child means).
-int build_mg(lm_grid* g, cudaStream_t s) {
-    if (g->mg_built) return LM_OK;
+int build_mg(lm_grid* g, cudaStream_t s, bool defer_inverse = false) {
+    // the coarsest level's dense inverse, now or left to the caller
+    auto inverse = [&](MgLevel& Lc) {
+        g->inv_pending = defer_inverse;
+        if (!defer_inverse) launch_coarse_inverse(Lc.L, s, Lc.ainv);
+    };
+    if (g->mg_built) {
+        if (g->inv_pending && !defer_inverse) inverse(g->mg.back());
+        CK(cudaGetLastError());
+        return LM_OK;
+    }
     if (!g->mg.empty()) {
         // the grid's shape never changes: keep the buffers, recompute the
         // coarse coefficients and the coarsest inverse from the new values
@@ -113,12 +122,13 @@ int build_mg(lm_grid* g, cudaStream_t s) {
             launch_coarsen(F.L, C.L, F.halved[0], F.halved[1], F.halved[2], s, C.ct, C.rho);
         }
         MgLevel& Lc = g->mg.back();
-        if (Lc.ainv) launch_coarse_inverse(Lc.L, s, Lc.ainv);
+        if (Lc.ainv) inverse(Lc);
         CK(cudaGetLastError());
         g->mg_built = true;
         return LM_OK;
     }
     ++g->version;       // new buffers: cached batch plans of this grid are stale
+    rbgs_row_allow_smem();
     MgLevel L0;
     L0.L = make_lev(g->n, g->bc, g->h, g->ct32, g->rho32);
     std::memcpy(L0.h, g->h, sizeof L0.h);
@@ -155,7 +165,7 @@ int build_mg(lm_grid* g, cudaStream_t s) {
     if (Lc.L.g.N <= COARSE_MAX) {
         int rc = dalloc(&Lc.ainv, (size_t)Lc.L.g.N * Lc.L.g.N);
         if (rc) return rc;
-        launch_coarse_inverse(Lc.L, s, Lc.ainv);
+        inverse(Lc);
     }
     // the one-block coarse V-cycle takes over from the first level small
     // enough, when the chain ends in a directly solved level
@@ -163,7 +173,13 @@ int build_mg(lm_grid* g, cudaStream_t s) {
     if (g->mg.back().ainv)
         for (size_t l = 0; l < g->mg.size(); ++l)
             if (g->mg[l].L.g.N <= CC_MAX_CELLS && g->mg.size() - l <= (size_t)CC_MAXL && g->mg.size() - l >= 2) {
-                g->cc_level = (int)l;
+                int N[CC_MAXL];
+                const int nl = (int)(g->mg.size() - l);
+                for (int i = 0; i < nl; ++i) N[i] = g->mg[l + i].L.g.N;
+                if (cc_smem_bytes(N, nl) <= CC_SMEM_MAX) {
+                    coarse_cycle_allow_smem();
+                    g->cc_level = (int)l;
+                }
                 break;
             }
     CK(cudaGetLastError());
@@ -593,7 +609,7 @@ int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double
 
 }  // namespace
 
-int lm::grid_build_mg(lm_grid* g, cudaStream_t s) { return build_mg(g, s); }
+int lm::grid_build_mg(lm_grid* g, cudaStream_t s, bool defer_inverse) { return build_mg(g, s, defer_inverse); }
 lm::Lev32 lm::make_level(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho) {
     return make_lev(n, bc, h, ct, rho);
 }

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) kb_resid_restrict(const BTask* __restrict
 
 // one block per grid: the grid's coarse V-cycle (its levels from the one-block
 // cycle's first level down), in place of the per-level launches there
-__global__ void __launch_bounds__(1024) kb_coarse_cycle(const CoarseCycle* __restrict__ ccs,
+__global__ void __launch_bounds__(CC_THREADS, 1) kb_coarse_cycle(const CoarseCycle* __restrict__ ccs,
                                                         const BGrid* __restrict__ Gs) {
     if (inner_off(Gs[blockIdx.x])) return;
     coarse_cycle_block(ccs[blockIdx.x]);
@@ -389,7 +389,11 @@ struct Plan {
     SolveState* hgather = nullptr;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t g_first = nullptr, g_step = nullptr;
+    CoarseInv* dinv_items = nullptr;     // the grids' coarsest levels, and the rows of their inverses
+    int* dinv_tasks = nullptr;
+    int n_inv_tasks = 0;
     CoarseCycle* dcc = nullptr;          // per-grid one-block coarse cycles (null: per-level launches)
+    size_t cc_smem = 0;                  // their dynamic shared memory (the largest chain's)
     int max_depth = 0;
     long long n_first = 0, n_step = 0;   // kernels per graph launch
 
@@ -402,6 +406,8 @@ struct Plan {
         cudaFree(dlev0);
         cudaFree(dtasks);
         cudaFree(dcc);
+        cudaFree(dinv_items);
+        cudaFree(dinv_tasks);
         cudaFree(dgather);
         cudaFreeHost(hgather);
     }
@@ -423,6 +429,20 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
     P->inner_max = o->inner_max_iter;
     P->first = !o->use_x0;
     P->count = count;
+    {   // every grid's coarsest inverse, one block per row of it
+        std::vector<CoarseInv> items(count);
+        std::vector<int> task;
+        for (int i = 0; i < count; ++i) {
+            const MgLevel& Lc = grids[i]->mg.back();
+            items[i] = CoarseInv{Lc.L, Lc.ainv};
+            for (int b = 0; b < Lc.L.g.N; ++b) task.push_back(i << 8 | b);
+        }
+        BCK(cudaMalloc(&P->dinv_items, sizeof(CoarseInv) * count));
+        BCK(cudaMalloc(&P->dinv_tasks, sizeof(int) * task.size()));
+        BCK(cudaMemcpy(P->dinv_items, items.data(), sizeof(CoarseInv) * count, cudaMemcpyHostToDevice));
+        BCK(cudaMemcpy(P->dinv_tasks, task.data(), sizeof(int) * task.size(), cudaMemcpyHostToDevice));
+        P->n_inv_tasks = (int)task.size();
+    }
 
     // autotune the sweep chunks of every level shape in the batch
     bool changed = false;
@@ -542,6 +562,8 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
             cc.nu1 = 1;
             cc.nu2 = 1;
         }
+        for (const CoarseCycle& cc : hcc) P->cc_smem = std::max(P->cc_smem, cc_smem_bytes(cc));
+        BCK(cudaFuncSetAttribute(kb_coarse_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC_SMEM_MAX));
         BCK(cudaMalloc(&P->dcc, sizeof(CoarseCycle) * count));
         BCK(cudaMemcpy(P->dcc, hcc.data(), sizeof(CoarseCycle) * count, cudaMemcpyHostToDevice));
     }
@@ -597,7 +619,7 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
                 if (tpre[d].n) kb_rbgs_pre<<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls);
                 if (trr[d].n) kb_resid_restrict<<<trr[d].n, dim3(32, 8), 0, cs>>>(T + trr[d].off, Gs, Ls);
             }
-            if (P->dcc) kb_coarse_cycle<<<count, 1024, 0, cs>>>(P->dcc, Gs);
+            if (P->dcc) kb_coarse_cycle<<<count, CC_THREADS, P->cc_smem, cs>>>(P->dcc, Gs);
             else kb_coarse<<<tco.n, 64, 0, cs>>>(T + tco.off, Gs, Ls);
             for (int d = P->max_depth - 1; d >= 0; --d)
                 if (tpre[d].n) kb_rbgs_post<<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls);
@@ -681,7 +703,7 @@ int lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* o, lm_
             if (grids[j] == g) return LM_ERR_INVALID_ARG;
     }
     for (int i = 0; i < count; ++i) {
-        const int rc = grid_build_mg(grids[i], s);
+        const int rc = grid_build_mg(grids[i], s, true);
         if (rc) return rc;
         if (!grids[i]->mg.back().ainv) return LM_ERR_INVALID_ARG;   // the batch path needs a direct coarsest level
     }
@@ -698,6 +720,15 @@ int lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* o, lm_
         if (rc) return rc;
         std::lock_guard<std::mutex> lk(g_plan_mu);
         g_plans.push_back(P);
+    }
+    {   // every grid's coarsest inverse left pending by its refresh, in one launch
+        bool pending = false;
+        for (int i = 0; i < count; ++i) pending = pending || grids[i]->inv_pending;
+        if (pending) {
+            launch_coarse_inverse_many(P->dinv_items, P->dinv_tasks, P->n_inv_tasks, s);
+            BCK(cudaGetLastError());
+            for (int i = 0; i < count; ++i) grids[i]->inv_pending = false;
+        }
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

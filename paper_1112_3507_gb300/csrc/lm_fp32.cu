@@ -646,6 +646,244 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
     }
 }
 
+// ---- 3D red-black sweep on whole rows: a warp per row, one barrier a plane --
+//
+// For 3D levels with nx = 32 CPT, ny a multiple of TY and nz >= 2.  A block
+// owns all nx columns of TY rows over a chunk of KZ planes; warp w owns row
+// j0 + w, and lane t the cell pairs (64 u + 2 t, 64 u + 2 t + 1), u < CPT / 2,
+// so a warp's accesses to a group of pairs are contiguous (conflict-free
+// 16-byte shared-memory accesses, coalesced global ones) and every pair holds
+// one cell of each colour.  The block marches up z with a five-plane ring of
+// (x, rho) staged on its rows plus two rows each side (periodic axes wrapped;
+// past a Neumann wall x = 0 and rho = +inf, also in a ghost cell at each row
+// end, so that face's weight c2 / (rho_c + inf) is 0 and no wall test is
+// needed).  At step p the block updates in place
+//   - the first colour of plane p on its rows and one halo row each side
+//     (a first-colour update reads only second-colour cells, which nobody
+//     has updated yet, so the halo values equal the neighbours' own), and
+//   - the second colour of plane p - 2 on its rows, whose first-colour
+//     neighbours (planes p - 3 .. p - 1, rows and halo rows) are final.
+// Neither update reads a cell the other writes, so one barrier per step
+// suffices.  Plane p - 3 is then final and written out, and plane p + 2,
+// loaded at the start of the step, is staged into its ring slot.  A row's
+// colour parity is uniform over its warp, so each warp takes the branch for
+// its parity, with compile-time offsets.  f and c~ of the next step's cells
+// are loaded a step ahead.
+
+// Gauss-Seidel update of the colour-A cell of each of a lane's CPT / 2 pairs;
+// c0: ring index of the lane's first pair; dzm, dzp: ring offsets of the
+// planes below and above; lrel0 / rrel1: offset of the left neighbour of the
+// row's first cell / the right neighbour of its last (a wrapped cell or a
+// ghost); fv, cv: f and c~ of the updated cells.
+template <int CPT, int A>
+__device__ __forceinline__ void gs_pairs(float2* __restrict__ XR, int c0, int RS, int dzm, int dzp, int lrel0,
+                                         int rrel1, const float* fv, const float* cv, float c2x, float c2y,
+                                         float c2z) {
+#pragma unroll
+    for (int u = 0; u < CPT / 2; ++u) {
+        const int pc = c0 + 64 * u, cc = pc + A;
+        const float4 pr = *reinterpret_cast<const float4*>(XR + pc);
+        const float2 me = A ? make_float2(pr.z, pr.w) : make_float2(pr.x, pr.y);
+        const float2 in = A ? make_float2(pr.x, pr.y) : make_float2(pr.z, pr.w);   // x-neighbour in the pair
+        const int orel = A == 0 ? (u == 0 ? lrel0 : -1) : (u == CPT / 2 - 1 ? rrel1 : 1);
+        const float2 out = XR[cc + orel];                                           // the other one
+        const float2 xm = A ? in : out, xp = A ? out : in;
+        const float2 ym = XR[cc - RS], yp = XR[cc + RS];
+        const float2 zm = XR[cc + dzm], zp = XR[cc + dzp];
+        const float rxm = rcp_fast(me.y + xm.y), rxp = rcp_fast(me.y + xp.y);
+        const float rym = rcp_fast(me.y + ym.y), ryp = rcp_fast(me.y + yp.y);
+        const float rzm = rcp_fast(me.y + zm.y), rzp = rcp_fast(me.y + zp.y);
+        const float sx = fmaf(rxp, xp.x, rxm * xm.x);
+        const float sy = fmaf(ryp, yp.x, rym * ym.x);
+        const float sz = fmaf(rzp, zp.x, rzm * zm.x);
+        const float num = fmaf(c2z, sz, fmaf(c2y, sy, fmaf(c2x, sx, fv[u])));
+        const float d = fmaf(c2z, rzm + rzp, fmaf(c2y, rym + ryp, fmaf(c2x, rxm + rxp, cv[u])));
+        XR[cc].x = num * rcp_fast(d);
+    }
+}
+
+template <int CPT, int TY>
+constexpr size_t rbgs_row_smem() {
+    return sizeof(float2) * 5 * (TY + 4) * (32 * CPT + 4);
+}
+
+template <int CPT, int TY, int FIRST, bool ZERO, bool PROLONG>
+__global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* __restrict__ xin,
+                                                        const float* __restrict__ ec, Geo C, int hx, int hy,
+                                                        int hz, const float* __restrict__ f,
+                                                        float* __restrict__ xout, int KZ) {
+    constexpr int NX = 32 * CPT, RS = NX + 4, NRW = TY + 4, PL = NRW * RS, NR = 5, H = CPT / 2;
+    static_assert(CPT % 2 == 0, "cells come in pairs");
+    extern __shared__ float4 row_smem[];
+    float2* XR = reinterpret_cast<float2*>(row_smem);
+    const Geo& g = L.g;
+    const int lane = threadIdx.x, wy = threadIdx.y, tid = lane + 32 * wy;
+    const int j0 = blockIdx.x * TY, k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
+    const int sz = NX * g.ny, i2 = 2 * lane;
+    const float INF = __int_as_float(0x7f800000);
+    for (int t = tid; t < NR * NRW; t += 32 * TY) {      // the row-end ghosts: x = 0, rho = +inf
+        XR[t * RS + 1] = make_float2(0.f, INF);
+        XR[t * RS + NX + 2] = make_float2(0.f, INF);
+    }
+    // staged row r <-> grid row j0 - 2 + r, wrapped; false past a wall
+    auto rowj = [&](int r, int& jw) -> bool {
+        int j = j0 - 2 + r;
+        if (j < 0 || j >= g.ny) {
+            if (g.bcy != LM_BC_PERIODIC) return false;
+            j = j < 0 ? j + g.ny : j - g.ny;
+        }
+        jw = j;
+        return true;
+    };
+    // plane p (k0 - 2 <= p <= k1 + 1) -> wrapped plane; false past a wall
+    auto plane = [&](int p, int& pw) -> bool {
+        if (p < 0 || p >= g.nz) {
+            if (g.bcz != LM_BC_PERIODIC) return false;
+            p = p < 0 ? p + g.nz : p - g.nz;
+        }
+        pw = p;
+        return true;
+    };
+    // staging: the warp's own row, and one halo row for warps 0..3
+    const int rT = wy + 2, rH = wy < 2 ? wy : TY + wy;
+    int jT = 0, jH = 0, jF = 0;
+    rowj(rT, jT);
+    const bool okH = wy < 4 && rowj(rH, jH);
+    // halo first-colour rows: j0 - 1 (warp 0) and j0 + TY (warp 1)
+    const int rF = wy == 0 ? 1 : TY + 2;
+    const bool okF = wy < 2 && rowj(rF, jF);
+    const bool perx = g.bcx == LM_BC_PERIODIC;
+    const int lrel0 = (lane == 0 && perx) ? NX - 1 : -1;
+    const int rrel1 = (lane == 31 && perx) ? 1 - NX : 1;
+
+    float vx[CPT], vr[CPT], ve[CPT], hxv[CPT], hrv[CPT], hev[CPT];
+    auto fetch_row = [&](int pw, bool ok, int jw, float* X, float* R, float* E) {
+        if (ok) {
+            const int o = sz * pw + NX * jw + i2;
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                const float2 r2 = *reinterpret_cast<const float2*>(L.rho + o + 64 * u);
+                R[2 * u] = r2.x;
+                R[2 * u + 1] = r2.y;
+                if (!ZERO) {
+                    const float2 x2 = *reinterpret_cast<const float2*>(xin + o + 64 * u);
+                    X[2 * u] = x2.x;
+                    X[2 * u + 1] = x2.y;
+                } else {
+                    X[2 * u] = X[2 * u + 1] = 0.f;
+                }
+                if (PROLONG) {
+                    const int po = C.nx * (jw >> hy) + C.nx * C.ny * (pw >> hz);
+                    E[2 * u] = ec[po + ((64 * u + i2) >> hx)];
+                    E[2 * u + 1] = ec[po + ((64 * u + i2 + 1) >> hx)];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                X[c] = 0.f;
+                R[c] = INF;
+                if (PROLONG) E[c] = 0.f;
+            }
+        }
+    };
+    auto fetch = [&](int p) {
+        int pw = 0;
+        const bool okp = plane(p, pw);
+        fetch_row(pw, okp, jT, vx, vr, ve);
+        if (wy < 4) fetch_row(pw, okp && okH, jH, hxv, hrv, hev);
+    };
+    auto store_row = [&](int s, int r, const float* X, const float* R, const float* E) {
+        float2* d = XR + (s * NRW + r) * RS + 2 + i2;
+#pragma unroll
+        for (int u = 0; u < H; ++u)
+            *reinterpret_cast<float4*>(d + 64 * u) =
+                make_float4(PROLONG ? X[2 * u] + E[2 * u] : X[2 * u], R[2 * u],
+                            PROLONG ? X[2 * u + 1] + E[2 * u + 1] : X[2 * u + 1], R[2 * u + 1]);
+    };
+    auto store = [&](int s) {
+        store_row(s, rT, vx, vr, ve);
+        if (wy < 4) store_row(s, rH, hxv, hrv, hev);
+    };
+    // f and c~ of a row's colour-a cells on plane p (cells 64 u + 2 t + a)
+    auto load_fc = [&](int p, bool ok, int jw, int a, float* F, float* Cv) {
+        int pw = 0;
+        if (ok && plane(p, pw)) {
+            const int o = sz * pw + NX * jw + i2 + a;
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                F[u] = f[o + 64 * u];
+                Cv[u] = L.ct[o + 64 * u];
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                F[u] = 0.f;
+                Cv[u] = 1.f;
+            }
+        }
+    };
+    auto parity = [&](int j, int p, int col) -> int { return (col + j + p) & 1; };   // updated cell of each pair
+    const int jTu = j0 + wy, jFu = wy == 0 ? j0 - 1 : j0 + TY;     // unwrapped rows (even periodic sizes)
+    float fT[H], cT[H], fF[H], cF[H], fS[H], cS[H];
+#pragma unroll
+    for (int u = 0; u < H; ++u) {
+        fS[u] = 0.f;
+        cS[u] = 1.f;
+    }
+    auto gs_row = [&](int a, int c0, int dzm, int dzp, const float* F, const float* Cv) {
+        if (a) gs_pairs<CPT, 1>(XR, c0, RS, dzm, dzp, lrel0, rrel1, F, Cv, L.c2x, L.c2y, L.c2z);
+        else gs_pairs<CPT, 0>(XR, c0, RS, dzm, dzp, lrel0, rrel1, F, Cv, L.c2x, L.c2y, L.c2z);
+    };
+
+    // prologue: planes k0 - 2 .. k0 staged; f, c~ of the first step's cells
+    int sl = (k0 + 8) % NR;                               // ring slot of plane k0 - 2
+    for (int p = k0 - 2; p <= k0; ++p) {
+        fetch(p);
+        store(sl);
+        sl = sl + 1 == NR ? 0 : sl + 1;
+    }
+    // slots of planes p - 3 .. p + 1 at step p = k0 - 1 (rotated each step)
+    int s_m3 = (k0 + 6) % NR, s_m2 = (k0 + 7) % NR, s_m1 = (k0 + 8) % NR, s_0 = (k0 + 9) % NR, s_p1 = (k0 + 10) % NR;
+    load_fc(k0 - 1, true, jT, parity(jTu, k0 - 1, FIRST), fT, cT);
+    load_fc(k0 - 1, okF, jF, parity(jFu, k0 - 1, FIRST), fF, cF);
+    __syncthreads();
+    for (int p = k0 - 1; p <= k1 + 2; ++p) {
+        const bool stage = p + 2 <= k1 + 1;
+        if (stage) fetch(p + 2);
+        int pw = 0;
+        if (p <= k1 && plane(p, pw)) {                    // first colour on plane p
+            const int dzm = (s_m1 - s_0) * PL, dzp = (s_p1 - s_0) * PL;
+            gs_row(parity(jTu, p, FIRST), (s_0 * NRW + rT) * RS + 2 + i2, dzm, dzp, fT, cT);
+            if (okF) gs_row(parity(jFu, p, FIRST), (s_0 * NRW + rF) * RS + 2 + i2, dzm, dzp, fF, cF);
+        }
+        load_fc(p + 1, p + 1 <= k1, jT, parity(jTu, p + 1, FIRST), fT, cT);
+        load_fc(p + 1, okF && p + 1 <= k1, jF, parity(jFu, p + 1, FIRST), fF, cF);
+        const int q = p - 2;
+        if (q >= k0 && q < k1)                            // second colour on plane p - 2
+            gs_row(parity(jTu, q, 1 - FIRST), (s_m2 * NRW + rT) * RS + 2 + i2, (s_m3 - s_m2) * PL,
+                   (s_m1 - s_m2) * PL, fS, cS);
+        load_fc(q + 1, q + 1 >= k0 && q + 1 < k1, jT, parity(jTu, q + 1, 1 - FIRST), fS, cS);
+        if (p - 3 >= k0 && p - 3 < k1) {                  // plane p - 3 is final
+            const float2* src = XR + (s_m3 * NRW + rT) * RS + 2 + i2;
+            float* dst = xout + sz * (p - 3) + NX * jT + i2;
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                const float4 a = *reinterpret_cast<const float4*>(src + 64 * u);
+                *reinterpret_cast<float2*>(dst + 64 * u) = make_float2(a.x, a.z);
+            }
+        }
+        if (stage) store(s_m3);                           // plane p + 2 takes plane p - 3's slot
+        __syncthreads();
+        const int t = s_m3;
+        s_m3 = s_m2;
+        s_m2 = s_m1;
+        s_m1 = s_0;
+        s_0 = s_p1;
+        s_p1 = t;
+    }
+}
+
 template <int FIRST, bool ZERO, bool PROLONG>
 __global__ void __launch_bounds__(128) k_rbgs_zm2d(Lev32 L, const float* __restrict__ xin,
                                                   const float* __restrict__ ec, Geo C, int hx, int hz,
@@ -662,20 +900,31 @@ __global__ void __launch_bounds__(BX * TY, 1024 / (BX * TY)) k_rbgs(Lev32 L, con
                                                    blockIdx.z);
 }
 
-// Inverse of the coarsest level's matrix (n <= 64) by in-place Gauss-Jordan
-// elimination in float64 (SPD: no pivoting needed); one block.
-__global__ void __launch_bounds__(1024) k_coarse_inverse(Lev32 L, float* __restrict__ ainv) {
-    // Gauss-Jordan inversion of the dense coarsest operator (n <= 64) in
-    // float64; block (64, 16): thread (j, r) owns column j of rows r, r+16, ...
+// Row b = blockIdx.x of the inverse of the dense coarsest operator (n <= 64),
+// in float64.  Every block factors A = L L^T (right-looking Cholesky) and
+// carries the forward solve of L y = e_b along; one warp then solves
+// L^T z = y.  A^-1 is symmetric, so z is row b as well as column b.  GB300
+// issues float64 at 1/64 of the float32 rate, so the factorisation is spread
+// over n SMs (one block each) instead of one Gauss-Jordan block, and every
+// trailing update runs with all lanes busy: the lower triangle of the
+// trailing block is enumerated through a packed (i, j) table ordered so that
+// the step-k triangle is a prefix of it.
+__device__ __forceinline__ void coarse_inverse_row(const Lev32& L, float* __restrict__ ainv, int b) {
     __shared__ double A[64 * 64];
-    __shared__ double colk[64], rowk[64];
+    __shared__ double y[64], yf[64], rinv[64];      // y: forward-solve updates; yf: final values
+    __shared__ int tri[64 * 65 / 2];
     const Geo& g = L.g;
-    const int n = g.N;
-    const int lin = threadIdx.x + 64 * threadIdx.y;
-    for (int e = lin; e < n * n; e += 1024) A[e] = 0.0;
+    const int n = g.N, tid = threadIdx.x;
+    for (int e = tid; e < n * n; e += 256) {
+        A[e] = 0.0;
+        const int i = e / n, j = e - i * n;
+        // column j from the last: (n - 1 - j)(n - j) / 2 entries come before it
+        if (i >= j) tri[(n - 1 - j) * (n - j) / 2 + (i - j)] = (i << 8) | j;
+    }
+    if (tid < n) y[tid] = tid == b ? 1.0 : 0.0;
     __syncthreads();
-    if (lin < n) {
-        const int idx = lin;
+    if (tid < n) {
+        const int idx = tid;
         const int i = idx % g.nx, j = (idx / g.nx) % g.ny, k = idx / (g.nx * g.ny);
         const double rc = L.rho[idx];
         double d = L.ct[idx];
@@ -697,28 +946,67 @@ __global__ void __launch_bounds__(1024) k_coarse_inverse(Lev32 L, float* __restr
         A[idx * n + idx] += d;
     }
     __syncthreads();
-    const int jc = threadIdx.x;
-    for (int kk = 0; kk < n; ++kk) {
-        // pivot row scaled by the pivot's inverse, and the pivot column
-        if (lin < n) {
-            const double ipiv = 1.0 / A[kk * n + kk];
-            colk[lin] = A[lin * n + kk];
-            rowk[lin] = lin == kk ? ipiv : A[kk * n + lin] * ipiv;
-        }
-        __syncthreads();
-        if (jc < n) {
-            const double rj = rowk[jc];
-            for (int i = threadIdx.y; i < n; i += 16) {
-                double v;
-                if (i == kk) v = rj;
-                else if (jc == kk) v = -colk[i] * rj;
-                else v = A[i * n + jc] - colk[i] * rj;
-                A[i * n + jc] = v;
+    for (int k = 0; k < n; ++k) {
+        // 1/sqrt(pivot), formed by each thread of rows k.. (float seed, one
+        // Newton step in float64: relative error ~1e-13, far below the float32
+        // the inverse is stored in); column k of L and the forward-solve step
+        const int i = k + tid;
+        if (i < n) {
+            const double p = A[k * n + k];
+            const float pf = (float)p;
+            double r;
+            if (pf > 1e-30f && pf < 1e30f) {
+                const double r0 = (double)rsqrtf(pf);
+                r = r0 * fma(-0.5 * p * r0, r0, 1.5);
+            } else {
+                r = 1.0 / sqrt(p);
+            }
+            const double yk = y[k] * r;                 // y[k] itself is not written in this phase
+            if (i == k) {
+                rinv[k] = r;
+                yf[k] = yk;
+            } else {
+                const double l = A[i * n + k] * r;
+                A[i * n + k] = l;
+                y[i] -= l * yk;
             }
         }
         __syncthreads();
+        const int m = n - 1 - k;
+#pragma unroll 4
+        for (int e = tid; e < m * (m + 1) / 2; e += 256) {
+            const int t = tri[e], ti = t >> 8, tj = t & 255;
+            A[ti * n + tj] -= A[ti * n + k] * A[tj * n + k];
+        }
+        __syncthreads();
     }
-    for (int e = lin; e < n * n; e += 1024) ainv[e] = (float)A[e];
+    if (tid < 32) {                                      // L^T z = y; lane owns rows tid, tid + 32
+        double z0 = tid < n ? yf[tid] : 0.0, z1 = tid + 32 < n ? yf[tid + 32] : 0.0;
+        for (int m = n - 1; m >= 0; --m) {
+            const double zm = __shfl_sync(0xffffffffu, m < 32 ? z0 : z1, m & 31) * rinv[m];
+            if ((m & 31) == tid) {
+                if (m < 32) z0 = zm;
+                else z1 = zm;
+            }
+            if (tid < m) z0 -= A[m * n + tid] * zm;
+            if (tid + 32 < m) z1 -= A[m * n + tid + 32] * zm;
+        }
+        if (tid < n) ainv[b * n + tid] = (float)z0;
+        if (tid + 32 < n) ainv[b * n + tid + 32] = (float)z1;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_coarse_inverse(Lev32 L, float* __restrict__ ainv) {
+    coarse_inverse_row(L, ainv, blockIdx.x);
+}
+
+// The inverses of several grids' coarsest levels in one launch: block t
+// computes row (task[t] & 255) of item (task[t] >> 8).
+__global__ void __launch_bounds__(256) k_coarse_inverse_many(const CoarseInv* __restrict__ items,
+                                                             const int* __restrict__ task) {
+    const int t = task[blockIdx.x];
+    const CoarseInv& it = items[t >> 8];
+    coarse_inverse_row(it.L, it.ainv, t & 255);
 }
 
 __global__ void k_coarse_solve(int n, const float* __restrict__ ainv, const float* __restrict__ f,
@@ -733,9 +1021,9 @@ __global__ void k_coarse_solve(int n, const float* __restrict__ ainv, const floa
 // the residual restricted to the next level's rhs, recursion, then the
 // prolonged correction and nu2 black-red sweeps; the coarsest level is
 // solved with its dense inverse.  Replaces ~3 launches per level and sweep
-// that are all latency-bound at these sizes.  Same operations per cell as
-// rbgs_tile and resid_restrict_tile.
-__global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseCycle cc) { coarse_cycle_block(cc); }
+// that are all latency-bound at these sizes; the chain lives in shared memory
+// (cc_smem_bytes), so only the setup and the final store touch global memory.
+__global__ void __launch_bounds__(CC_THREADS, 1) k_coarse_cycle(CoarseCycle cc) { coarse_cycle_block(cc); }
 
 // ---- host launchers -----------------------------------------------------------
 
@@ -844,6 +1132,42 @@ void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int h
     k_resid_restrict<<<cell_grid(C.g), dim3(32, 8), 0, s>>>(F, C.g, hx, hy, hz, x, f, fc);
 }
 
+// The whole-row sweep's shared memory exceeds the default 48 KB: raise the
+// limit of every instantiation (host, once per hierarchy build).
+template <int CPT, int TY>
+static void rbgs_row_allow() {
+    const int sm = (int)rbgs_row_smem<CPT, TY>();
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 0, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 1, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 0, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+void rbgs_row_allow_smem() {
+    rbgs_row_allow<8, 16>();
+    rbgs_row_allow<4, 16>();
+}
+
+static bool aligned8(const void* p) { return ((uintptr_t)p & 7) == 0; }
+
+template <int CPT>
+static void launch_rbgs_row(const Lev32& L, cudaStream_t s, const float* xin, const float* ec, const Geo& Cg,
+                            int hx, int hy, int hz, const float* f, float* xout, int first, int zero, int prolong) {
+    constexpr int TY = 16;
+    const Geo& g = L.g;
+    const int ntile = g.ny / TY;
+    const int chunks = std::max(1, std::min(g.nz / 2, 152 / ntile));
+    const int KZ = hdiv(g.nz, chunks);
+    const dim3 grd(ntile, hdiv(g.nz, KZ)), blk(32, TY);
+    const size_t sm = rbgs_row_smem<CPT, TY>();
+#define LM_ROW(F, Z, P) k_rbgs_row<CPT, TY, F, Z, P><<<grd, blk, sm, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout, KZ)
+    if (zero) { if (first) LM_ROW(1, true, false); else LM_ROW(0, true, false); }
+    else if (prolong) { if (first) LM_ROW(1, false, true); else LM_ROW(0, false, true); }
+    else { if (first) LM_ROW(1, false, false); else LM_ROW(0, false, false); }
+#undef LM_ROW
+}
+
 // One red-black sweep xout = S(xin [+ P ec]); first = colour updated first;
 // kz = planes per block (<= 0: enough blocks to fill the GPU).
 void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const float* ec, const Lev32* C, int hx,
@@ -851,6 +1175,13 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
     const Geo& g = L.g;
     const Geo Cg = C ? C->g : g;
     count_launches(1);
+    if (kz <= 0 && g.ny > 1 && g.ny % 16 == 0 && g.nz >= 2 && (g.nx == 256 || g.nx == 128) && aligned8(xin) &&
+        aligned8(xout) && aligned8(ec)) {
+        // whole rows of 256 or 128 cells: a warp per row, 16 rows per block
+        if (g.nx == 256) launch_rbgs_row<8>(L, s, xin, ec, Cg, hx, hy, hz, f, xout, first, zero, prolong);
+        else launch_rbgs_row<4>(L, s, xin, ec, Cg, hx, hy, hz, f, xout, first, zero, prolong);
+        return;
+    }
     if (g.ny > 1 && g.nx % 32 == 0 && g.ny % 8 == 0 && g.nz >= 2) {
         // whole TX x 8 tiles (TX = 64 when nx allows, else 32): the in-place
         // z-march; KZ planes per block, the largest of 64, 32, ..., 2 that
@@ -916,13 +1247,21 @@ void launch_rbgs(const Lev32& L, cudaStream_t s, const float* xin, const float* 
                  int hz, const float* f, float* xout, int first, int zero, int prolong) {
     launch_rbgs_kz(L, s, xin, ec, C, hx, hy, hz, f, xout, first, zero, prolong, 0);
 }
+void coarse_cycle_allow_smem() {
+    cudaFuncSetAttribute(k_coarse_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC_SMEM_MAX);
+}
 void launch_coarse_cycle(const CoarseCycle& cc, cudaStream_t s) {
     count_launches(1);
-    k_coarse_cycle<<<1, 1024, 0, s>>>(cc);
+    k_coarse_cycle<<<1, CC_THREADS, cc_smem_bytes(cc), s>>>(cc);
+}
+void launch_coarse_inverse_many(const CoarseInv* items, const int* task, int ntask, cudaStream_t s) {
+    if (ntask <= 0) return;
+    count_launches(1);
+    k_coarse_inverse_many<<<ntask, 256, 0, s>>>(items, task);
 }
 void launch_coarse_inverse(const Lev32& L, cudaStream_t s, float* ainv) {
     count_launches(1);
-    k_coarse_inverse<<<1, dim3(64, 16), 0, s>>>(L, ainv);
+    k_coarse_inverse<<<L.g.N, 256, 0, s>>>(L, ainv);
 }
 void launch_coarse_solve(int n, cudaStream_t s, const float* ainv, const float* f, float* x) {
     count_launches(1);

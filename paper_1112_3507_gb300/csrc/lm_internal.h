@@ -67,6 +67,7 @@ struct lm_grid {
     bool have_coefs = false, have_rhs = false, have_x0 = false;
     bool have_dinv = false;         // inverse Jacobi diagonal (formed on the first Jacobi solve)
     bool mg_built = false;
+    bool inv_pending = false;       // hierarchy built, its coarsest inverse not yet computed
     unsigned version = 0;           // bumped when the hierarchy buffers are (re)allocated
     lm_net* net = nullptr;          // learned warm start / preconditioner (2D grids)
     float* feat = nullptr;          // network input (N x 3)
@@ -87,7 +88,9 @@ struct lm_grid {
 
 
 namespace lm {
-int grid_build_mg(lm_grid* g, cudaStream_t s);      // multigrid hierarchy (idempotent)
+// multigrid hierarchy (idempotent); defer_inverse leaves the coarsest inverse
+// to the caller (inv_pending), which computes many grids' in one launch
+int grid_build_mg(lm_grid* g, cudaStream_t s, bool defer_inverse = false);
 void batch_forget_grid(const lm_grid* g);            // drop cached batch plans that use g
 int net_forward(lm_net* N, const float* x, float* y, int B, int H, int W, cudaStream_t s);
 int net_backward(lm_net* N, const float* gy, cudaStream_t s);

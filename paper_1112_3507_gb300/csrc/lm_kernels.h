@@ -109,8 +109,32 @@ struct CoarseCycle {
     const float* ainv;
     int nu1, nu2;
 };
+constexpr int CC_THREADS = 1024;                 // threads of the block that runs a cycle
+constexpr int CC_PER = CC_MAX_CELLS / CC_THREADS;  // cells a thread owns on a chain level
+constexpr size_t CC_SMEM_MAX = 200 * 1024;       // shared-memory limit of the one-block cycle
+// Shared memory of the one-block cycle over levels of N_0 .. N_{nl-1} cells:
+// seven floats per cell and the dense inverse of the coarsest level.
+inline size_t cc_smem_bytes(const int* N, int nl) {
+    size_t b = 0;
+    for (int l = 0; l < nl; ++l) b += 7 * sizeof(float) * (size_t)N[l];
+    return b + sizeof(float) * (size_t)N[nl - 1] * (size_t)N[nl - 1];
+}
+inline size_t cc_smem_bytes(const CoarseCycle& cc) {
+    int N[CC_MAXL];
+    for (int l = 0; l < cc.nl; ++l) N[l] = cc.L[l].g.N;
+    return cc_smem_bytes(N, cc.nl);
+}
 void launch_coarse_cycle(const CoarseCycle& cc, cudaStream_t s);
+void coarse_cycle_allow_smem();
+void rbgs_row_allow_smem();                      // raises the whole-row sweep's dynamic shared-memory limit                  // raises k_coarse_cycle's dynamic shared-memory limit
 void launch_coarse_inverse(const Lev32& L, cudaStream_t s, float* ainv);
+// one grid's coarsest level and where its dense inverse goes
+struct CoarseInv {
+    Lev32 L;
+    float* ainv;
+};
+// rows (task & 255) of items[task >> 8] for every task: many grids' inverses in one launch
+void launch_coarse_inverse_many(const CoarseInv* items, const int* task, int ntask, cudaStream_t s);
 void launch_coarse_solve(int n, cudaStream_t s, const float* ainv, const float* f, float* x);
 
 }  // namespace lm

@@ -723,92 +723,172 @@ __device__ __forceinline__ void zm2d_tile(const Lev32& L, const float* __restric
 }
 
 // ---- the coarse V-cycle in one block (see k_coarse_cycle) ------------------
-__device__ __forceinline__ float gs_cell32(const Lev32& L, const float* x, const float* f, int idx, int i, int j,
-                                           int k) {
-    const Geo& g = L.g;
-    const float rc = L.rho[idx];
-    const Nbr nx = nbr_x(idx, i, g), ny = nbr_y(idx, j, g), nz = nbr_z(idx, k, g);
-    const bool fxm = face_minus(i, g.nx, g.bcx), fxp = face_plus(i, g.nx, g.bcx);
-    const bool fym = face_minus(j, g.ny, g.bcy), fyp = face_plus(j, g.ny, g.bcy);
-    const bool fzm = face_minus(k, g.nz, g.bcz), fzp = face_plus(k, g.nz, g.bcz);
-    const float wxm = fxm ? face32(rc, L.rho[nx.im], L.c2x) : 0.f;
-    const float wxp = fxp ? face32(rc, L.rho[nx.ip], L.c2x) : 0.f;
-    const float wym = fym ? face32(rc, L.rho[ny.im], L.c2y) : 0.f;
-    const float wyp = fyp ? face32(rc, L.rho[ny.ip], L.c2y) : 0.f;
-    const float wzm = fzm ? face32(rc, L.rho[nz.im], L.c2z) : 0.f;
-    const float wzp = fzp ? face32(rc, L.rho[nz.ip], L.c2z) : 0.f;
-    const float d = L.ct[idx] + ((wxm + wxp) + (wym + wyp)) + (wzm + wzp);
-    float num = f[idx];
-    num = fmaf(wxm, fxm ? x[nx.im] : 0.f, num);
-    num = fmaf(wxp, fxp ? x[nx.ip] : 0.f, num);
-    num = fmaf(wym, fym ? x[ny.im] : 0.f, num);
-    num = fmaf(wyp, fyp ? x[ny.ip] : 0.f, num);
-    num = fmaf(wzm, fzm ? x[nz.im] : 0.f, num);
-    num = fmaf(wzp, fzp ? x[nz.ip] : 0.f, num);
-    return __fdividef(num, d);
-}
+//
+// The block keeps the whole chain in shared memory: per level x, f, the three
+// minus-face conductances (plus faces are the neighbours' minus faces), c~ and
+// the inverse diagonal, seven floats per cell (cc_smem_bytes), and the dense
+// inverse of the coarsest level.  Face weights and diagonals are formed once
+// per cycle; every later phase reads shared memory only.  Each thread owns
+// cells tid + CC_THREADS q of a level and keeps their (i, j, k) in registers.
 
 __device__ __forceinline__ void coarse_cycle_block(const CoarseCycle& cc) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    auto colour = [&](int l, int col) {                  // update every cell of colour col in place
+    extern __shared__ float cc_sm[];
+    const int tid = threadIdx.x;
+    const int nl = cc.nl;
+    struct CS {
+        float *x, *f, *wx, *wy, *wz, *ct, *di;
+    };
+    auto cs = [&](int l) -> CS {                        // level l's arrays, laid out level after level
+        float* b = cc_sm;
+        for (int m = 0; m < l; ++m) b += 7 * cc.L[m].g.N;
+        const int N = cc.L[l].g.N;
+        return CS{b, b + N, b + 2 * N, b + 3 * N, b + 4 * N, b + 5 * N, b + 6 * N};
+    };
+    // setup: x = 0, f (level 0: the caller's rhs), c~ and minus-face weights
+    for (int l = 0; l < nl; ++l) {
         const Lev32& L = cc.L[l];
         const Geo& g = L.g;
-        for (int idx = tid; idx < g.N; idx += nt) {
+        const CS s = cs(l);
+        for (int idx = tid; idx < g.N; idx += CC_THREADS) {
             int i, j, k;
             cell_coords(idx, g, i, j, k);
-            if (((i + j + k) & 1) == col) cc.x[l][idx] = gs_cell32(L, cc.x[l], cc.f[l], idx, i, j, k);
+            const float rc = L.rho[idx];
+            s.wx[idx] = face_minus(i, g.nx, g.bcx) ? face32(rc, L.rho[nbr_x(idx, i, g).im], L.c2x) : 0.f;
+            s.wy[idx] = face_minus(j, g.ny, g.bcy) ? face32(rc, L.rho[nbr_y(idx, j, g).im], L.c2y) : 0.f;
+            s.wz[idx] = face_minus(k, g.nz, g.bcz) ? face32(rc, L.rho[nbr_z(idx, k, g).im], L.c2z) : 0.f;
+            s.ct[idx] = L.ct[idx];
+            s.f[idx] = l == 0 ? cc.f[0][idx] : 0.f;
+            s.x[idx] = 0.f;
+        }
+    }
+    const int nc = cc.L[nl - 1].g.N;
+    float* const Ai = cs(nl - 1).x + 7 * nc;            // after the last level's arrays
+    for (int e = tid; e < nc * nc; e += CC_THREADS) Ai[e] = cc.ainv[e];
+    __syncthreads();
+    // plus-face weight of cell idx along an axis: the minus face of its plus
+    // neighbour, 0 past a wall
+    auto wplus = [&](const float* w, bool has, int ip) -> float { return has ? w[ip] : 0.f; };
+    for (int l = 0; l < nl; ++l) {
+        const Geo& g = cc.L[l].g;
+        const CS s = cs(l);
+        for (int idx = tid; idx < g.N; idx += CC_THREADS) {
+            int i, j, k;
+            cell_coords(idx, g, i, j, k);
+            const float d = s.ct[idx] + ((s.wx[idx] + wplus(s.wx, face_plus(i, g.nx, g.bcx), nbr_x(idx, i, g).ip)) +
+                                         (s.wy[idx] + wplus(s.wy, face_plus(j, g.ny, g.bcy), nbr_y(idx, j, g).ip))) +
+                            (s.wz[idx] + wplus(s.wz, face_plus(k, g.nz, g.bcz), nbr_z(idx, k, g).ip));
+            s.di[idx] = 1.f / d;
+        }
+    }
+    __syncthreads();
+
+    int ci[CC_PER], cj[CC_PER], ck[CC_PER];
+    auto coords = [&](int l) {
+        const Geo& g = cc.L[l].g;
+#pragma unroll
+        for (int q = 0; q < CC_PER; ++q) {
+            const int idx = tid + q * CC_THREADS;
+            ci[q] = cj[q] = ck[q] = 0;
+            if (idx < g.N) cell_coords(idx, g, ci[q], cj[q], ck[q]);
+        }
+    };
+    // (A x) at cell idx of a level from its shared arrays
+    auto apply_at = [&](const Geo& g, const CS& s, int idx, int i, int j, int k) -> float {
+        const float xc = s.x[idx];
+        float y = s.ct[idx] * xc;
+        Nbr n = nbr_x(idx, i, g);
+        if (face_minus(i, g.nx, g.bcx)) y += s.wx[idx] * (xc - s.x[n.im]);
+        if (face_plus(i, g.nx, g.bcx)) y += s.wx[n.ip] * (xc - s.x[n.ip]);
+        n = nbr_y(idx, j, g);
+        if (face_minus(j, g.ny, g.bcy)) y += s.wy[idx] * (xc - s.x[n.im]);
+        if (face_plus(j, g.ny, g.bcy)) y += s.wy[n.ip] * (xc - s.x[n.ip]);
+        n = nbr_z(idx, k, g);
+        if (face_minus(k, g.nz, g.bcz)) y += s.wz[idx] * (xc - s.x[n.im]);
+        if (face_plus(k, g.nz, g.bcz)) y += s.wz[n.ip] * (xc - s.x[n.ip]);
+        return y;
+    };
+    // one colour of a red-black sweep on level l, in place
+    auto colour = [&](int l, int col) {
+        const Geo& g = cc.L[l].g;
+        const CS s = cs(l);
+#pragma unroll
+        for (int q = 0; q < CC_PER; ++q) {
+            const int idx = tid + q * CC_THREADS;
+            const int i = ci[q], j = cj[q], k = ck[q];
+            if (idx < g.N && ((i + j + k) & 1) == col) {
+                float num = s.f[idx];
+                Nbr n = nbr_x(idx, i, g);
+                if (face_minus(i, g.nx, g.bcx)) num = fmaf(s.wx[idx], s.x[n.im], num);
+                if (face_plus(i, g.nx, g.bcx)) num = fmaf(s.wx[n.ip], s.x[n.ip], num);
+                n = nbr_y(idx, j, g);
+                if (face_minus(j, g.ny, g.bcy)) num = fmaf(s.wy[idx], s.x[n.im], num);
+                if (face_plus(j, g.ny, g.bcy)) num = fmaf(s.wy[n.ip], s.x[n.ip], num);
+                n = nbr_z(idx, k, g);
+                if (face_minus(k, g.nz, g.bcz)) num = fmaf(s.wz[idx], s.x[n.im], num);
+                if (face_plus(k, g.nz, g.bcz)) num = fmaf(s.wz[n.ip], s.x[n.ip], num);
+                s.x[idx] = num * s.di[idx];
+            }
         }
         __syncthreads();
     };
-    for (int l = 0; l + 1 < cc.nl; ++l) {
-        const Lev32& L = cc.L[l];
-        for (int idx = tid; idx < L.g.N; idx += nt) cc.x[l][idx] = 0.f;
-        __syncthreads();
+
+    for (int l = 0; l + 1 < nl; ++l) {
+        coords(l);
         for (int it = 0; it < cc.nu1; ++it) {
             colour(l, 0);
             colour(l, 1);
         }
+        const Geo& F = cc.L[l].g;
         const Geo& C = cc.L[l + 1].g;
+        const CS s = cs(l), c = cs(l + 1);
         const int hx = cc.hx[l], hy = cc.hy[l], hz = cc.hz[l];
         const float inv = 1.f / (float)((1 << hx) << hy << hz);
-        for (int e = tid; e < C.N; e += nt) {
+        for (int e = tid; e < C.N; e += CC_THREADS) {
             int I, J, K;
             cell_coords(e, C, I, J, K);
             float sum = 0.f;
-            for (int c = 0; c <= hz; ++c)
-                for (int b = 0; b <= hy; ++b)
-                    for (int a = 0; a <= hx; ++a) {
-                        const int i = (I << hx) + a, j = (J << hy) + b, k = (K << hz) + c;
-                        const int idx = i + L.g.nx * (j + L.g.ny * k);
-                        sum += cc.f[l][idx] - apply32_at(idx, i, j, k, L, cc.x[l]);
+            for (int cz = 0; cz <= hz; ++cz)
+                for (int by = 0; by <= hy; ++by)
+                    for (int ax = 0; ax <= hx; ++ax) {
+                        const int i = (I << hx) + ax, j = (J << hy) + by, k = (K << hz) + cz;
+                        const int idx = i + F.nx * (j + F.ny * k);
+                        sum += s.f[idx] - apply_at(F, s, idx, i, j, k);
                     }
-            cc.f[l + 1][e] = sum * inv;
+            c.f[e] = sum * inv;
         }
         __syncthreads();
     }
-    {
-        const int last = cc.nl - 1, n = cc.L[last].g.N;
-        for (int r = tid; r < n; r += nt) {
-            float v = 0.f;
-            for (int c = 0; c < n; ++c) v = fmaf(cc.ainv[r * n + c], cc.f[last][c], v);
-            cc.x[last][r] = v;
-        }
+    {   // coarsest level: x = A^-1 f, 16 threads per row
+        const CS s = cs(nl - 1);
+        const int r = tid >> 4, part = tid & 15;
+        float v = 0.f;
+        if (r < nc)
+            for (int c = part; c < nc; c += 16) v = fmaf(Ai[r * nc + c], s.f[c], v);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (r < nc && part == 0) s.x[r] = v;
         __syncthreads();
     }
-    for (int l = cc.nl - 2; l >= 0; --l) {
-        const Lev32& L = cc.L[l];
+    for (int l = nl - 2; l >= 0; --l) {
+        coords(l);
+        const Geo& g = cc.L[l].g;
         const Geo& C = cc.L[l + 1].g;
+        const CS s = cs(l), c = cs(l + 1);
         const int hx = cc.hx[l], hy = cc.hy[l], hz = cc.hz[l];
-        for (int idx = tid; idx < L.g.N; idx += nt) {
-            int i, j, k;
-            cell_coords(idx, L.g, i, j, k);
-            cc.x[l][idx] += cc.x[l + 1][(i >> hx) + C.nx * ((j >> hy) + C.ny * (k >> hz))];
+#pragma unroll
+        for (int q = 0; q < CC_PER; ++q) {
+            const int idx = tid + q * CC_THREADS;
+            if (idx < g.N) s.x[idx] += c.x[(ci[q] >> hx) + C.nx * ((cj[q] >> hy) + C.ny * (ck[q] >> hz))];
         }
         __syncthreads();
         for (int it = 0; it < cc.nu2; ++it) {
             colour(l, 1);
             colour(l, 0);
         }
+    }
+    {
+        const CS s = cs(0);
+        for (int idx = tid; idx < cc.L[0].g.N; idx += CC_THREADS) cc.x[0][idx] = s.x[idx];
     }
 }
 
