@@ -650,14 +650,15 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
 //
 // For 3D levels with nx = 32 CPT, ny a multiple of TY and nz >= 2.  A block
 // owns all nx columns of TY rows over a chunk of KZ planes; warp w owns row
-// j0 + w, and lane t the cell pairs (64 u + 2 t, 64 u + 2 t + 1), u < CPT / 2,
-// so a warp's accesses to a group of pairs are contiguous (conflict-free
-// 16-byte shared-memory accesses, coalesced global ones) and every pair holds
-// one cell of each colour.  The block marches up z with a five-plane ring of
-// (x, rho) staged on its rows plus two rows each side (periodic axes wrapped;
-// past a Neumann wall x = 0 and rho = +inf, also in a ghost cell at each row
-// end, so that face's weight c2 / (rho_c + inf) is 0 and no wall test is
-// needed).  At step p the block updates in place
+// j0 + w.  The block marches up z with a five-plane ring of (x, rho) staged
+// on its rows plus two rows each side (periodic axes wrapped; past a Neumann
+// wall x = 0 and rho = ROW_WALL, so that face's weight is negligible and no
+// wall test is needed).  A staged row keeps its even cells, then its
+// odd cells, each run between two ghost cells: the cells of one colour in a
+// row are then contiguous, and so are their x-neighbours (the other run), so
+// a warp updating 32 cells of one colour reads every neighbour with one
+// conflict-free access (lane t: cells 2 (t + 32 u) + a, u < CPT / 2).  At
+// step p the block updates in place
 //   - the first colour of plane p on its rows and one halo row each side
 //     (a first-colour update reads only second-colour cells, which nobody
 //     has updated yet, so the halo values equal the neighbours' own), and
@@ -667,39 +668,63 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
 // suffices.  Plane p - 3 is then final and written out, and plane p + 2,
 // loaded at the start of the step, is staged into its ring slot.  A row's
 // colour parity is uniform over its warp, so each warp takes the branch for
-// its parity, with compile-time offsets.  f and c~ of the next step's cells
-// are loaded a step ahead.
+// its parity.  f and c~ of the next step's cells are loaded a step ahead.
+// The halo rows' staging and updates are spread one pair group per warp.
 
-// Gauss-Seidel update of the colour-A cell of each of a lane's CPT / 2 pairs;
-// c0: ring index of the lane's first pair; dzm, dzp: ring offsets of the
-// planes below and above; lrel0 / rrel1: offset of the left neighbour of the
-// row's first cell / the right neighbour of its last (a wrapped cell or a
-// ghost); fv, cv: f and c~ of the updated cells.
+// rho of the cells past a wall: large but finite, so that a face weight
+// c2 / (rho_c + ROW_WALL) is negligible (x there is 0) and the product of an
+// axis's two face sums stays finite
+constexpr float ROW_WALL = 1e30f;
+
+// Ring index of even cell m (run E) and odd cell m (run O) of a staged row
+// of M = nx / 2 pairs; E(-1), E(M), O(-1), O(M) are the ghosts.
+__device__ __forceinline__ int run_e(int M, int m) { return 1 + m; }
+__device__ __forceinline__ int run_o(int M, int m) { return 3 + M + m; }
+
+// Gauss-Seidel value of cell 2 m + A of the row at ring index b (plane),
+// with dzm, dzp the ring offsets of the planes below and above; wrap: the
+// cell's outer x-neighbour (left of cell 0, right of cell nx - 1) wraps
+// around the row (periodic x) instead of reading the ghost.
+template <int A>
+__device__ __forceinline__ float gs_run(const float2* __restrict__ XR, int b, int M, int m, bool wrap, int RS,
+                                        int dzm, int dzp, float fv, float cv, float c2x, float c2y, float c2z) {
+    const int cc = b + (A ? run_o(M, m) : run_e(M, m));
+    const int im = A ? run_e(M, m) : (wrap ? run_o(M, M - 1) : run_o(M, m - 1));
+    const int ip = A ? (wrap ? run_e(M, 0) : run_e(M, m + 1)) : run_o(M, m);
+    const float2 me = XR[cc];
+    const float2 xm = XR[b + im], xp = XR[b + ip];
+    const float2 ym = XR[cc - RS], yp = XR[cc + RS];
+    const float2 zm = XR[cc + dzm], zp = XR[cc + dzp];
+    // the two faces of an axis share one reciprocal: 1/a = b/(ab), 1/b = a/(ab)
+    // (at most one face of an axis is a wall, rho = ROW_WALL, so ab stays finite)
+    const float axm = me.y + xm.y, axp = me.y + xp.y, tx = rcp_fast(axm * axp);
+    const float aym = me.y + ym.y, ayp = me.y + yp.y, ty = rcp_fast(aym * ayp);
+    const float azm = me.y + zm.y, azp = me.y + zp.y, tz = rcp_fast(azm * azp);
+    const float rxm = axp * tx, rxp = axm * tx, rym = ayp * ty, ryp = aym * ty, rzm = azp * tz, rzp = azm * tz;
+    const float sx = fmaf(rxp, xp.x, rxm * xm.x);
+    const float sy = fmaf(ryp, yp.x, rym * ym.x);
+    const float sz = fmaf(rzp, zp.x, rzm * zm.x);
+    const float num = fmaf(c2z, sz, fmaf(c2y, sy, fmaf(c2x, sx, fv)));
+    const float d = fmaf(c2z, rzm + rzp, fmaf(c2y, rym + ryp, fmaf(c2x, rxm + rxp, cv)));
+    return num * rcp_fast(d);
+}
+
+// The colour-A cells of a warp's row at ring index b: all values formed
+// before any is stored, so their loads can be in flight together.
 template <int CPT, int A>
-__device__ __forceinline__ void gs_pairs(float2* __restrict__ XR, int c0, int RS, int dzm, int dzp, int lrel0,
-                                         int rrel1, const float* fv, const float* cv, float c2x, float c2y,
-                                         float c2z) {
+__device__ __forceinline__ void gs_row_runs(float2* __restrict__ XR, int b, int lane, bool perx, int RS, int dzm,
+                                            int dzp, const float* fv, const float* cv, float c2x, float c2y,
+                                            float c2z) {
+    constexpr int H = CPT / 2, M = 16 * CPT;
+    float nv[H];
 #pragma unroll
-    for (int u = 0; u < CPT / 2; ++u) {
-        const int pc = c0 + 64 * u, cc = pc + A;
-        const float4 pr = *reinterpret_cast<const float4*>(XR + pc);
-        const float2 me = A ? make_float2(pr.z, pr.w) : make_float2(pr.x, pr.y);
-        const float2 in = A ? make_float2(pr.x, pr.y) : make_float2(pr.z, pr.w);   // x-neighbour in the pair
-        const int orel = A == 0 ? (u == 0 ? lrel0 : -1) : (u == CPT / 2 - 1 ? rrel1 : 1);
-        const float2 out = XR[cc + orel];                                           // the other one
-        const float2 xm = A ? in : out, xp = A ? out : in;
-        const float2 ym = XR[cc - RS], yp = XR[cc + RS];
-        const float2 zm = XR[cc + dzm], zp = XR[cc + dzp];
-        const float rxm = rcp_fast(me.y + xm.y), rxp = rcp_fast(me.y + xp.y);
-        const float rym = rcp_fast(me.y + ym.y), ryp = rcp_fast(me.y + yp.y);
-        const float rzm = rcp_fast(me.y + zm.y), rzp = rcp_fast(me.y + zp.y);
-        const float sx = fmaf(rxp, xp.x, rxm * xm.x);
-        const float sy = fmaf(ryp, yp.x, rym * ym.x);
-        const float sz = fmaf(rzp, zp.x, rzm * zm.x);
-        const float num = fmaf(c2z, sz, fmaf(c2y, sy, fmaf(c2x, sx, fv[u])));
-        const float d = fmaf(c2z, rzm + rzp, fmaf(c2y, rym + ryp, fmaf(c2x, rxm + rxp, cv[u])));
-        XR[cc].x = num * rcp_fast(d);
+    for (int u = 0; u < H; ++u) {
+        const int m = lane + 32 * u;
+        const bool wrap = perx && (A ? (u == H - 1 && lane == 31) : (u == 0 && lane == 0));
+        nv[u] = gs_run<A>(XR, b, M, m, wrap, RS, dzm, dzp, fv[u], cv[u], c2x, c2y, c2z);
     }
+#pragma unroll
+    for (int u = 0; u < H; ++u) XR[b + (A ? run_o(M, lane + 32 * u) : run_e(M, lane + 32 * u))].x = nv[u];
 }
 
 template <int CPT, int TY>
@@ -712,18 +737,20 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
                                                         const float* __restrict__ ec, Geo C, int hx, int hy,
                                                         int hz, const float* __restrict__ f,
                                                         float* __restrict__ xout, int KZ) {
-    constexpr int NX = 32 * CPT, RS = NX + 4, NRW = TY + 4, PL = NRW * RS, NR = 5, H = CPT / 2;
-    static_assert(CPT % 2 == 0, "cells come in pairs");
+    constexpr int NX = 32 * CPT, M = NX / 2, RS = NX + 4, NRW = TY + 4, PL = NRW * RS, NR = 5, H = CPT / 2;
+    static_assert(CPT % 2 == 0 && TY >= 4 * H / 2 && TY >= 2 * H, "a warp per halo pair group");
     extern __shared__ float4 row_smem[];
     float2* XR = reinterpret_cast<float2*>(row_smem);
     const Geo& g = L.g;
     const int lane = threadIdx.x, wy = threadIdx.y, tid = lane + 32 * wy;
     const int j0 = blockIdx.x * TY, k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
     const int sz = NX * g.ny, i2 = 2 * lane;
-    const float INF = __int_as_float(0x7f800000);
-    for (int t = tid; t < NR * NRW; t += 32 * TY) {      // the row-end ghosts: x = 0, rho = +inf
-        XR[t * RS + 1] = make_float2(0.f, INF);
-        XR[t * RS + NX + 2] = make_float2(0.f, INF);
+    for (int t = tid; t < NR * NRW; t += 32 * TY) {      // the run-end ghosts: x = 0, rho = ROW_WALL
+        const float2 gh = make_float2(0.f, ROW_WALL);
+        XR[t * RS + run_e(M, -1)] = gh;
+        XR[t * RS + run_e(M, M)] = gh;
+        XR[t * RS + run_o(M, -1)] = gh;
+        XR[t * RS + run_o(M, M)] = gh;
     }
     // staged row r <-> grid row j0 - 2 + r, wrapped; false past a wall
     auto rowj = [&](int r, int& jw) -> bool {
@@ -744,98 +771,96 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
         pw = p;
         return true;
     };
-    // staging: the warp's own row, and one halo row for warps 0..3
-    const int rT = wy + 2, rH = wy < 2 ? wy : TY + wy;
-    int jT = 0, jH = 0, jF = 0;
+    // the warp's own row; one pair group of a staged halo row (rows 0, 1,
+    // TY + 2, TY + 3) and of a first-colour halo row (rows 1, TY + 2) per warp
+    const int rT = wy + 2;
+    const int hs = wy & 3, uS = wy >> 2, rS = hs < 2 ? hs : TY + hs;
+    const int uF = wy >> 1, rF = (wy & 1) ? TY + 2 : 1;
+    int jT = 0, jS = 0, jF = 0;
     rowj(rT, jT);
-    const bool okH = wy < 4 && rowj(rH, jH);
-    // halo first-colour rows: j0 - 1 (warp 0) and j0 + TY (warp 1)
-    const int rF = wy == 0 ? 1 : TY + 2;
-    const bool okF = wy < 2 && rowj(rF, jF);
+    const bool hasS = uS < H, okS = hasS && rowj(rS, jS);
+    const bool okF = uF < H && rowj(rF, jF);
     const bool perx = g.bcx == LM_BC_PERIODIC;
-    const int lrel0 = (lane == 0 && perx) ? NX - 1 : -1;
-    const int rrel1 = (lane == 31 && perx) ? 1 - NX : 1;
 
-    float vx[CPT], vr[CPT], ve[CPT], hxv[CPT], hrv[CPT], hev[CPT];
-    auto fetch_row = [&](int pw, bool ok, int jw, float* X, float* R, float* E) {
-        if (ok) {
-            const int o = sz * pw + NX * jw + i2;
-#pragma unroll
-            for (int u = 0; u < H; ++u) {
-                const float2 r2 = *reinterpret_cast<const float2*>(L.rho + o + 64 * u);
-                R[2 * u] = r2.x;
-                R[2 * u + 1] = r2.y;
-                if (!ZERO) {
-                    const float2 x2 = *reinterpret_cast<const float2*>(xin + o + 64 * u);
-                    X[2 * u] = x2.x;
-                    X[2 * u + 1] = x2.y;
-                } else {
-                    X[2 * u] = X[2 * u + 1] = 0.f;
-                }
-                if (PROLONG) {
-                    const int po = C.nx * (jw >> hy) + C.nx * C.ny * (pw >> hz);
-                    E[2 * u] = ec[po + ((64 * u + i2) >> hx)];
-                    E[2 * u + 1] = ec[po + ((64 * u + i2 + 1) >> hx)];
-                }
-            }
+    // staged plane: the own row (H pairs) and the halo pair, in registers
+    float vx[CPT], vr[CPT], ve[CPT], sxh[2], srh[2], seh[2];
+    auto fetch_pair = [&](int o, int pw, int jw, int u, float* X, float* R, float* E) {
+        const float2 r2 = *reinterpret_cast<const float2*>(L.rho + o);
+        R[0] = r2.x;
+        R[1] = r2.y;
+        if (!ZERO) {
+            const float2 x2 = *reinterpret_cast<const float2*>(xin + o);
+            X[0] = x2.x;
+            X[1] = x2.y;
         } else {
-#pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-                X[c] = 0.f;
-                R[c] = INF;
-                if (PROLONG) E[c] = 0.f;
-            }
+            X[0] = X[1] = 0.f;
         }
+        if (PROLONG) {
+            const int po = C.nx * (jw >> hy) + C.nx * C.ny * (pw >> hz);
+            E[0] = ec[po + ((64 * u + i2) >> hx)];
+            E[1] = ec[po + ((64 * u + i2 + 1) >> hx)];
+        }
+    };
+    auto wall_pair = [&](float* X, float* R, float* E) {
+        X[0] = X[1] = 0.f;
+        R[0] = R[1] = ROW_WALL;
+        if (PROLONG) E[0] = E[1] = 0.f;
     };
     auto fetch = [&](int p) {
         int pw = 0;
         const bool okp = plane(p, pw);
-        fetch_row(pw, okp, jT, vx, vr, ve);
-        if (wy < 4) fetch_row(pw, okp && okH, jH, hxv, hrv, hev);
-    };
-    auto store_row = [&](int s, int r, const float* X, const float* R, const float* E) {
-        float2* d = XR + (s * NRW + r) * RS + 2 + i2;
 #pragma unroll
-        for (int u = 0; u < H; ++u)
-            *reinterpret_cast<float4*>(d + 64 * u) =
-                make_float4(PROLONG ? X[2 * u] + E[2 * u] : X[2 * u], R[2 * u],
-                            PROLONG ? X[2 * u + 1] + E[2 * u + 1] : X[2 * u + 1], R[2 * u + 1]);
+        for (int u = 0; u < H; ++u) {
+            if (okp) fetch_pair(sz * pw + NX * jT + 64 * u + i2, pw, jT, u, vx + 2 * u, vr + 2 * u, ve + 2 * u);
+            else wall_pair(vx + 2 * u, vr + 2 * u, ve + 2 * u);
+        }
+        if (hasS) {
+            if (okp && okS) fetch_pair(sz * pw + NX * jS + 64 * uS + i2, pw, jS, uS, sxh, srh, seh);
+            else wall_pair(sxh, srh, seh);
+        }
+    };
+    // pair m = lane + 32 u of row r: cell 2 m to run E, cell 2 m + 1 to run O
+    auto store_pair = [&](int b, int m, const float* X, const float* R, const float* E) {
+        XR[b + run_e(M, m)] = make_float2(PROLONG ? X[0] + E[0] : X[0], R[0]);
+        XR[b + run_o(M, m)] = make_float2(PROLONG ? X[1] + E[1] : X[1], R[1]);
     };
     auto store = [&](int s) {
-        store_row(s, rT, vx, vr, ve);
-        if (wy < 4) store_row(s, rH, hxv, hrv, hev);
+#pragma unroll
+        for (int u = 0; u < H; ++u) store_pair((s * NRW + rT) * RS, lane + 32 * u, vx + 2 * u, vr + 2 * u, ve + 2 * u);
+        if (hasS) store_pair((s * NRW + rS) * RS, lane + 32 * uS, sxh, srh, seh);
     };
-    // f and c~ of a row's colour-a cells on plane p (cells 64 u + 2 t + a)
-    auto load_fc = [&](int p, bool ok, int jw, int a, float* F, float* Cv) {
+    // f and c~ of cells 2 (lane + 32 u) + a, u < n, of a row at offset rowoff of plane p
+    auto load_fc = [&](int p, bool ok, int rowoff, int a, float* F, float* Cv, int n) {
         int pw = 0;
         if (ok && plane(p, pw)) {
-            const int o = sz * pw + NX * jw + i2 + a;
+            const int o = sz * pw + rowoff + i2 + a;
 #pragma unroll
-            for (int u = 0; u < H; ++u) {
-                F[u] = f[o + 64 * u];
-                Cv[u] = L.ct[o + 64 * u];
-            }
+            for (int u = 0; u < H; ++u)
+                if (u < n) {
+                    F[u] = f[o + 64 * u];
+                    Cv[u] = L.ct[o + 64 * u];
+                }
         } else {
 #pragma unroll
-            for (int u = 0; u < H; ++u) {
-                F[u] = 0.f;
-                Cv[u] = 1.f;
-            }
+            for (int u = 0; u < H; ++u)
+                if (u < n) {
+                    F[u] = 0.f;
+                    Cv[u] = 1.f;
+                }
         }
     };
     auto parity = [&](int j, int p, int col) -> int { return (col + j + p) & 1; };   // updated cell of each pair
-    const int jTu = j0 + wy, jFu = wy == 0 ? j0 - 1 : j0 + TY;     // unwrapped rows (even periodic sizes)
-    float fT[H], cT[H], fF[H], cF[H], fS[H], cS[H];
+    const int jTu = j0 + wy, jFu = (wy & 1) ? j0 + TY : j0 - 1;   // unwrapped rows (even periodic sizes)
+    auto gs_row = [&](int a, int b, int dzm, int dzp, const float* F, const float* Cv) {
+        if (a) gs_row_runs<CPT, 1>(XR, b, lane, perx, RS, dzm, dzp, F, Cv, L.c2x, L.c2y, L.c2z);
+        else gs_row_runs<CPT, 0>(XR, b, lane, perx, RS, dzm, dzp, F, Cv, L.c2x, L.c2y, L.c2z);
+    };
+    float fT[H], cT[H], fS[H], cS[H], fF[1], cF[1];
 #pragma unroll
     for (int u = 0; u < H; ++u) {
         fS[u] = 0.f;
         cS[u] = 1.f;
     }
-    auto gs_row = [&](int a, int c0, int dzm, int dzp, const float* F, const float* Cv) {
-        if (a) gs_pairs<CPT, 1>(XR, c0, RS, dzm, dzp, lrel0, rrel1, F, Cv, L.c2x, L.c2y, L.c2z);
-        else gs_pairs<CPT, 0>(XR, c0, RS, dzm, dzp, lrel0, rrel1, F, Cv, L.c2x, L.c2y, L.c2z);
-    };
-
     // prologue: planes k0 - 2 .. k0 staged; f, c~ of the first step's cells
     int sl = (k0 + 8) % NR;                               // ring slot of plane k0 - 2
     for (int p = k0 - 2; p <= k0; ++p) {
@@ -845,8 +870,8 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
     }
     // slots of planes p - 3 .. p + 1 at step p = k0 - 1 (rotated each step)
     int s_m3 = (k0 + 6) % NR, s_m2 = (k0 + 7) % NR, s_m1 = (k0 + 8) % NR, s_0 = (k0 + 9) % NR, s_p1 = (k0 + 10) % NR;
-    load_fc(k0 - 1, true, jT, parity(jTu, k0 - 1, FIRST), fT, cT);
-    load_fc(k0 - 1, okF, jF, parity(jFu, k0 - 1, FIRST), fF, cF);
+    load_fc(k0 - 1, true, NX * jT, parity(jTu, k0 - 1, FIRST), fT, cT, H);
+    load_fc(k0 - 1, okF, NX * jF + 64 * uF, parity(jFu, k0 - 1, FIRST), fF, cF, 1);
     __syncthreads();
     for (int p = k0 - 1; p <= k1 + 2; ++p) {
         const bool stage = p + 2 <= k1 + 1;
@@ -854,23 +879,29 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
         int pw = 0;
         if (p <= k1 && plane(p, pw)) {                    // first colour on plane p
             const int dzm = (s_m1 - s_0) * PL, dzp = (s_p1 - s_0) * PL;
-            gs_row(parity(jTu, p, FIRST), (s_0 * NRW + rT) * RS + 2 + i2, dzm, dzp, fT, cT);
-            if (okF) gs_row(parity(jFu, p, FIRST), (s_0 * NRW + rF) * RS + 2 + i2, dzm, dzp, fF, cF);
+            gs_row(parity(jTu, p, FIRST), (s_0 * NRW + rT) * RS, dzm, dzp, fT, cT);
+            if (okF) {                                    // this warp's pair group of a halo row
+                const int aF = parity(jFu, p, FIRST), b = (s_0 * NRW + rF) * RS, m = lane + 32 * uF;
+                const bool wrapF = perx && (aF ? (uF == H - 1 && lane == 31) : (uF == 0 && lane == 0));
+                const float v = aF ? gs_run<1>(XR, b, M, m, wrapF, RS, dzm, dzp, fF[0], cF[0], L.c2x, L.c2y, L.c2z)
+                                   : gs_run<0>(XR, b, M, m, wrapF, RS, dzm, dzp, fF[0], cF[0], L.c2x, L.c2y, L.c2z);
+                XR[b + (aF ? run_o(M, m) : run_e(M, m))].x = v;
+            }
         }
-        load_fc(p + 1, p + 1 <= k1, jT, parity(jTu, p + 1, FIRST), fT, cT);
-        load_fc(p + 1, okF && p + 1 <= k1, jF, parity(jFu, p + 1, FIRST), fF, cF);
+        load_fc(p + 1, p + 1 <= k1, NX * jT, parity(jTu, p + 1, FIRST), fT, cT, H);
+        load_fc(p + 1, okF && p + 1 <= k1, NX * jF + 64 * uF, parity(jFu, p + 1, FIRST), fF, cF, 1);
         const int q = p - 2;
         if (q >= k0 && q < k1)                            // second colour on plane p - 2
-            gs_row(parity(jTu, q, 1 - FIRST), (s_m2 * NRW + rT) * RS + 2 + i2, (s_m3 - s_m2) * PL,
-                   (s_m1 - s_m2) * PL, fS, cS);
-        load_fc(q + 1, q + 1 >= k0 && q + 1 < k1, jT, parity(jTu, q + 1, 1 - FIRST), fS, cS);
+            gs_row(parity(jTu, q, 1 - FIRST), (s_m2 * NRW + rT) * RS, (s_m3 - s_m2) * PL, (s_m1 - s_m2) * PL, fS,
+                   cS);
+        load_fc(q + 1, q + 1 >= k0 && q + 1 < k1, NX * jT, parity(jTu, q + 1, 1 - FIRST), fS, cS, H);
         if (p - 3 >= k0 && p - 3 < k1) {                  // plane p - 3 is final
-            const float2* src = XR + (s_m3 * NRW + rT) * RS + 2 + i2;
+            const int b = (s_m3 * NRW + rT) * RS;
             float* dst = xout + sz * (p - 3) + NX * jT + i2;
 #pragma unroll
             for (int u = 0; u < H; ++u) {
-                const float4 a = *reinterpret_cast<const float4*>(src + 64 * u);
-                *reinterpret_cast<float2*>(dst + 64 * u) = make_float2(a.x, a.z);
+                const int m = lane + 32 * u;
+                *reinterpret_cast<float2*>(dst + 64 * u) = make_float2(XR[b + run_e(M, m)].x, XR[b + run_o(M, m)].x);
             }
         }
         if (stage) store(s_m3);                           // plane p + 2 takes plane p - 3's slot
