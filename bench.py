@@ -516,7 +516,7 @@ def run_ours(args):
                          "traffic": traffic, "bytes_per_cell": sweep_bytes, "launch_us": t_sw * 1e6,
                          "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
                                          else "fallback 6800 GB/s (of fallback)"),
-                         "also": {"k_apply32z": {"bytes_per_cell": 16, "launch_us": t_ap * 1e6,
+                         "also": {"apply32": {"bytes_per_cell": 16, "launch_us": t_ap * 1e6,
                                                  "achieved": 16 * N / t_ap / 1e9,
                                                  "frac": 16 * N / t_ap / 1e9 / peak},
                                   "k_apply64": {"launch_us": t_k64 * 1e6,

@@ -173,6 +173,162 @@ __global__ void __launch_bounds__(256) k_apply32_zm(Lev32 L, const float* __rest
     }
 }
 
+// ---- float32 apply on whole rows: a warp per row, all lanes contiguous -------
+//
+// For 3D levels with nx = 32 CPT, ny a multiple of TY and nz >= 2 (the
+// levels the whole-row sweep takes).  A block owns all nx columns of TY rows
+// over a chunk of KZ planes and marches up z with a three-plane ring of
+// (x, rho) staged on its rows plus one row each side (periodic axes wrapped;
+// past a Neumann wall x = 0 and rho = +inf, so that face's weight is 0).
+// Lane t of warp w computes the cells t + 32 v of row j0 + w, so every
+// shared-memory and global access of a warp is contiguous.  A step computes
+// plane p, then (after a barrier) stages plane p + 2, loaded at the start of
+// the step, into plane p - 1's slot.  The ring is small enough for two
+// blocks per SM.  Fused dot products as in k_apply32_zm.
+template <int CPT, int TY>
+constexpr size_t apply_row_smem() {
+    return sizeof(float2) * 3 * (TY + 2) * (32 * CPT + 4);
+}
+
+template <int CPT, int TY, bool DOT_XY, bool DOT_XR>
+__global__ void __launch_bounds__(32 * TY, 2) k_apply32_row(Lev32 L, const float* __restrict__ x,
+                                                           float* __restrict__ y, const float* __restrict__ r,
+                                                           Red red, int slot_xy, int slot_xr, int KZ) {
+    constexpr int NX = 32 * CPT, RS = NX + 4, NRW = TY + 2, PL = NRW * RS, H = CPT / 2;
+    static_assert(CPT % 2 == 0 && TY >= 2 * H, "a warp per halo pair group");
+    extern __shared__ float4 ap_smem[];
+    float2* XR = reinterpret_cast<float2*>(ap_smem);
+    __shared__ double sm[64];
+    const Geo& g = L.g;
+    const int lane = threadIdx.x, wy = threadIdx.y, tid = lane + 32 * wy;
+    const int j0 = blockIdx.x * TY, k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
+    const int sz = NX * g.ny, i2 = 2 * lane;
+    const float INF = __int_as_float(0x7f800000);
+    for (int t = tid; t < 3 * NRW; t += 32 * TY) {       // row-end ghosts: x = 0, rho = +inf
+        XR[t * RS + 1] = make_float2(0.f, INF);
+        XR[t * RS + NX + 2] = make_float2(0.f, INF);
+    }
+    auto rowj = [&](int r_, int& jw) -> bool {           // staged row -> grid row; false past a wall
+        int j = j0 - 1 + r_;
+        if (j < 0 || j >= g.ny) {
+            if (g.bcy != LM_BC_PERIODIC) return false;
+            j = j < 0 ? j + g.ny : j - g.ny;
+        }
+        jw = j;
+        return true;
+    };
+    auto plane = [&](int p, int& pw) -> bool {
+        if (p < 0 || p >= g.nz) {
+            if (g.bcz != LM_BC_PERIODIC) return false;
+            p = p < 0 ? p + g.nz : p - g.nz;
+        }
+        pw = p;
+        return true;
+    };
+    const int rT = wy + 1;
+    const int uS = wy >> 1, rS = (wy & 1) ? TY + 1 : 0;   // this warp's pair group of a halo row
+    int jT = 0, jS = 0;
+    rowj(rT, jT);
+    const bool hasS = uS < H, okS = hasS && rowj(rS, jS);
+    const bool perx = g.bcx == LM_BC_PERIODIC;
+    float vx[CPT], vr[CPT], hx2[2], hr2[2];
+    auto fetch = [&](int p) {
+        int pw = 0;
+        const bool okp = plane(p, pw);
+#pragma unroll
+        for (int u = 0; u < H; ++u) {
+            if (okp) {
+                const int o = sz * pw + NX * jT + 64 * u + i2;
+                const float2 a = *reinterpret_cast<const float2*>(x + o), b = *reinterpret_cast<const float2*>(L.rho + o);
+                vx[2 * u] = a.x; vx[2 * u + 1] = a.y; vr[2 * u] = b.x; vr[2 * u + 1] = b.y;
+            } else {
+                vx[2 * u] = vx[2 * u + 1] = 0.f;
+                vr[2 * u] = vr[2 * u + 1] = INF;
+            }
+        }
+        if (hasS) {
+            if (okp && okS) {
+                const int o = sz * pw + NX * jS + 64 * uS + i2;
+                const float2 a = *reinterpret_cast<const float2*>(x + o), b = *reinterpret_cast<const float2*>(L.rho + o);
+                hx2[0] = a.x; hx2[1] = a.y; hr2[0] = b.x; hr2[1] = b.y;
+            } else {
+                hx2[0] = hx2[1] = 0.f;
+                hr2[0] = hr2[1] = INF;
+            }
+        }
+    };
+    auto store = [&](int s) {
+#pragma unroll
+        for (int u = 0; u < H; ++u)
+            *reinterpret_cast<float4*>(XR + (s * NRW + rT) * RS + 2 + 64 * u + i2) =
+                make_float4(vx[2 * u], vr[2 * u], vx[2 * u + 1], vr[2 * u + 1]);
+        if (hasS)
+            *reinterpret_cast<float4*>(XR + (s * NRW + rS) * RS + 2 + 64 * uS + i2) =
+                make_float4(hx2[0], hr2[0], hx2[1], hr2[1]);
+    };
+    float ctv[CPT], rrv[CPT];
+    auto load_c = [&](int p) {                            // c~ (and r) of the warp's row on plane p
+        const int o = sz * p + NX * jT + lane;
+#pragma unroll
+        for (int v = 0; v < CPT; ++v) {
+            ctv[v] = L.ct[o + 32 * v];
+            rrv[v] = DOT_XR ? r[o + 32 * v] : 0.f;
+        }
+    };
+    const int lrel = (lane == 0 && perx) ? NX - 1 : -1;         // left of cell 0, right of cell nx - 1
+    const int rrel = (lane == 31 && perx) ? 1 - NX : 1;
+    FF axy{0.f, 0.f}, axr{0.f, 0.f};
+    int sm1 = 0, s0 = 1, sp1 = 2;                         // slots of planes p - 1, p, p + 1
+    fetch(k0 - 1);
+    store(sm1);
+    fetch(k0);
+    store(s0);
+    fetch(k0 + 1);
+    store(sp1);
+    load_c(k0);
+    __syncthreads();
+    for (int p = k0; p < k1; ++p) {
+        const bool stage = p + 2 <= k1;
+        if (stage) fetch(p + 2);
+        const int b0 = (s0 * NRW + rT) * RS + 2 + lane, dzm = (sm1 - s0) * PL, dzp = (sp1 - s0) * PL;
+        float* yrow = y + sz * p + NX * jT + lane;
+#pragma unroll
+        for (int v = 0; v < CPT; ++v) {
+            const int c = b0 + 32 * v;
+            const float2 me = XR[c];
+            const float2 xm = XR[c + (v == 0 ? lrel : -1)], xp = XR[c + (v == CPT - 1 ? rrel : 1)];
+            const float2 ym = XR[c - RS], yp = XR[c + RS], zm = XR[c + dzm], zp = XR[c + dzp];
+            float val = ctv[v] * me.x;
+            val += L.c2x * rcp_approx(me.y + xm.y) * (me.x - xm.x);
+            val += L.c2x * rcp_approx(me.y + xp.y) * (me.x - xp.x);
+            val += L.c2y * rcp_approx(me.y + ym.y) * (me.x - ym.x);
+            val += L.c2y * rcp_approx(me.y + yp.y) * (me.x - yp.x);
+            val += L.c2z * rcp_approx(me.y + zm.y) * (me.x - zm.x);
+            val += L.c2z * rcp_approx(me.y + zp.y) * (me.x - zp.x);
+            yrow[32 * v] = val;
+            if (DOT_XY) ff_add_prod(axy, me.x, val);
+            if (DOT_XR) ff_add_prod(axr, me.x, rrv[v]);
+        }
+        if (p + 1 < k1) load_c(p + 1);
+        __syncthreads();
+        if (stage) store(sm1);                            // plane p + 2 takes plane p - 1's slot
+        __syncthreads();
+        const int t = sm1;
+        sm1 = s0;
+        s0 = sp1;
+        sp1 = t;
+    }
+    if (DOT_XY && DOT_XR) {
+        double v[2] = {ff_value(axy), ff_value(axr)};
+        const int sl[2] = {slot_xy, slot_xr};
+        grid_reduce<2>(v, red, sl, sm);
+    } else if (DOT_XY) {
+        double v[1] = {ff_value(axy)};
+        const int sl[1] = {slot_xy};
+        grid_reduce<1>(v, red, sl, sm);
+    }
+}
+
 // ---- 3D residual + restriction on whole tiles: a z-march -------------------
 // fc = mean over the children of (f - A x), for 3D fine levels whose nx, ny
 // are multiples of the TX x 8 tile: the same staged four-plane ring as
@@ -1064,9 +1220,32 @@ static dim3 cell_grid(const Geo& g) {
     return g.ny > 1 ? dim3(hdiv(g.nx, 32), hdiv(g.ny, 8), g.nz) : dim3(hdiv(g.nx, 32), hdiv(g.nz, 8), 1);
 }
 
+template <int CPT>
+static void launch_apply32_row(const Lev32& L, cudaStream_t s, const float* x, float* y, const float* r,
+                               const Red& red, int slot_xy, int slot_xr) {
+    constexpr int TY = 16;
+    const Geo& g = L.g;
+    const int ntile = g.ny / TY;
+    const int chunks = std::max(1, std::min(g.nz / 2, 2 * 152 / ntile));
+    const int KZ = hdiv(g.nz, chunks);
+    const dim3 grd(ntile, hdiv(g.nz, KZ)), blk(32, TY);
+    const size_t sm = apply_row_smem<CPT, TY>();
+    const bool dxy = slot_xy >= 0, dxr = slot_xr >= 0;
+    count_launches(1);
+    if (dxy && dxr) k_apply32_row<CPT, TY, true, true><<<grd, blk, sm, s>>>(L, x, y, r, red, slot_xy, slot_xr, KZ);
+    else if (dxy) k_apply32_row<CPT, TY, true, false><<<grd, blk, sm, s>>>(L, x, y, r, red, slot_xy, slot_xr, KZ);
+    else k_apply32_row<CPT, TY, false, false><<<grd, blk, sm, s>>>(L, x, y, r, red, slot_xy, slot_xr, KZ);
+}
+
 void launch_apply32(const Lev32& L, cudaStream_t s, const float* x, float* y, const float* r, const Red& red,
                     int slot_xy, int slot_xr) {
     const Geo& g = L.g;
+    if (g.ny > 1 && g.ny % 16 == 0 && g.nz >= 2 && (g.nx == 256 || g.nx == 128) && ((uintptr_t)x & 7) == 0) {
+        // whole rows of 256 or 128 cells: a warp per row, 16 rows per block
+        if (g.nx == 256) launch_apply32_row<8>(L, s, x, y, r, red, slot_xy, slot_xr);
+        else launch_apply32_row<4>(L, s, x, y, r, red, slot_xy, slot_xr);
+        return;
+    }
     if (g.ny > 1 && g.nx % 32 == 0 && g.ny % 8 == 0 && g.nz >= 2) {
         // whole TX x 8 tiles: the staged z-march; KZ planes per block, the
         // largest of 64, 32, ..., 2 that still gives eight blocks per SM
@@ -1175,9 +1354,18 @@ static void rbgs_row_allow() {
     cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
+template <int CPT, int TY>
+static void apply_row_allow() {
+    const int sm = (int)apply_row_smem<CPT, TY>();
+    cudaFuncSetAttribute(k_apply32_row<CPT, TY, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_apply32_row<CPT, TY, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_apply32_row<CPT, TY, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
 void rbgs_row_allow_smem() {
     rbgs_row_allow<8, 16>();
     rbgs_row_allow<4, 16>();
+    apply_row_allow<8, 16>();
+    apply_row_allow<4, 16>();
 }
 
 static bool aligned8(const void* p) { return ((uintptr_t)p & 7) == 0; }
