@@ -1220,6 +1220,167 @@ static dim3 cell_grid(const Geo& g) {
     return g.ny > 1 ? dim3(hdiv(g.nx, 32), hdiv(g.ny, 8), g.nz) : dim3(hdiv(g.nx, 32), hdiv(g.nz, 8), 1);
 }
 
+// fc = mean over the 2 x 2 x 2 children of (f - A x), on whole rows: the
+// staging and stencil of k_apply32_row; a thread adds the residuals of its
+// cells over a plane pair, lanes 2 i and 2 i + 1 combine the x pair by a
+// shuffle, and the odd row of each row pair stores its sums in fc, which the
+// even row (after the block barrier) adds to its own and scales.  For levels
+// halved along all three axes.
+template <int CPT, int TY>
+__global__ void __launch_bounds__(32 * TY, 2) k_resid_restrict_row(Lev32 L, Geo C, const float* __restrict__ x,
+                                                                  const float* __restrict__ f,
+                                                                  float* __restrict__ fc, int KZ) {
+    constexpr int NX = 32 * CPT, RS = NX + 4, NRW = TY + 2, PL = NRW * RS, H = CPT / 2;
+    static_assert(CPT % 2 == 0 && TY % 2 == 0 && TY >= 2 * H, "row pairs; a warp per halo pair group");
+    extern __shared__ float4 ap_smem[];
+    float2* XR = reinterpret_cast<float2*>(ap_smem);
+    const Geo& g = L.g;
+    const int lane = threadIdx.x, wy = threadIdx.y, tid = lane + 32 * wy;
+    const int j0 = blockIdx.x * TY, k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
+    const int sz = NX * g.ny, i2 = 2 * lane;
+    const float INF = __int_as_float(0x7f800000);
+    for (int t = tid; t < 3 * NRW; t += 32 * TY) {
+        XR[t * RS + 1] = make_float2(0.f, INF);
+        XR[t * RS + NX + 2] = make_float2(0.f, INF);
+    }
+    auto rowj = [&](int r_, int& jw) -> bool {
+        int j = j0 - 1 + r_;
+        if (j < 0 || j >= g.ny) {
+            if (g.bcy != LM_BC_PERIODIC) return false;
+            j = j < 0 ? j + g.ny : j - g.ny;
+        }
+        jw = j;
+        return true;
+    };
+    auto plane = [&](int p, int& pw) -> bool {
+        if (p < 0 || p >= g.nz) {
+            if (g.bcz != LM_BC_PERIODIC) return false;
+            p = p < 0 ? p + g.nz : p - g.nz;
+        }
+        pw = p;
+        return true;
+    };
+    const int rT = wy + 1;
+    const int uS = wy >> 1, rS = (wy & 1) ? TY + 1 : 0;
+    int jT = 0, jS = 0;
+    rowj(rT, jT);
+    const bool hasS = uS < H, okS = hasS && rowj(rS, jS);
+    const bool perx = g.bcx == LM_BC_PERIODIC;
+    float vx[CPT], vr[CPT], hx2[2], hr2[2];
+    auto fetch = [&](int p) {
+        int pw = 0;
+        const bool okp = plane(p, pw);
+#pragma unroll
+        for (int u = 0; u < H; ++u) {
+            if (okp) {
+                const int o = sz * pw + NX * jT + 64 * u + i2;
+                const float2 a = *reinterpret_cast<const float2*>(x + o), b = *reinterpret_cast<const float2*>(L.rho + o);
+                vx[2 * u] = a.x; vx[2 * u + 1] = a.y; vr[2 * u] = b.x; vr[2 * u + 1] = b.y;
+            } else {
+                vx[2 * u] = vx[2 * u + 1] = 0.f;
+                vr[2 * u] = vr[2 * u + 1] = INF;
+            }
+        }
+        if (hasS) {
+            if (okp && okS) {
+                const int o = sz * pw + NX * jS + 64 * uS + i2;
+                const float2 a = *reinterpret_cast<const float2*>(x + o), b = *reinterpret_cast<const float2*>(L.rho + o);
+                hx2[0] = a.x; hx2[1] = a.y; hr2[0] = b.x; hr2[1] = b.y;
+            } else {
+                hx2[0] = hx2[1] = 0.f;
+                hr2[0] = hr2[1] = INF;
+            }
+        }
+    };
+    auto store = [&](int s) {
+#pragma unroll
+        for (int u = 0; u < H; ++u)
+            *reinterpret_cast<float4*>(XR + (s * NRW + rT) * RS + 2 + 64 * u + i2) =
+                make_float4(vx[2 * u], vr[2 * u], vx[2 * u + 1], vr[2 * u + 1]);
+        if (hasS)
+            *reinterpret_cast<float4*>(XR + (s * NRW + rS) * RS + 2 + 64 * uS + i2) =
+                make_float4(hx2[0], hr2[0], hx2[1], hr2[1]);
+    };
+    float ctv[CPT], fv[CPT], acc[CPT];
+    auto load_c = [&](int p) {
+        const int o = sz * p + NX * jT + lane;
+#pragma unroll
+        for (int v = 0; v < CPT; ++v) {
+            ctv[v] = L.ct[o + 32 * v];
+            fv[v] = f[o + 32 * v];
+        }
+    };
+    const int lrel = (lane == 0 && perx) ? NX - 1 : -1;
+    const int rrel = (lane == 31 && perx) ? 1 - NX : 1;
+    int sm1 = 0, s0 = 1, sp1 = 2;
+    fetch(k0 - 1);
+    store(sm1);
+    fetch(k0);
+    store(s0);
+    fetch(k0 + 1);
+    store(sp1);
+    load_c(k0);
+    __syncthreads();
+    for (int p = k0; p < k1; ++p) {
+        const bool stage = p + 2 <= k1;
+        if (stage) fetch(p + 2);
+        const int b0 = (s0 * NRW + rT) * RS + 2 + lane, dzm = (sm1 - s0) * PL, dzp = (sp1 - s0) * PL;
+        const bool odd = (p - k0) & 1;                    // second plane of a pair (k0 is even)
+#pragma unroll
+        for (int v = 0; v < CPT; ++v) {
+            const int c = b0 + 32 * v;
+            const float2 me = XR[c];
+            const float2 xm = XR[c + (v == 0 ? lrel : -1)], xp = XR[c + (v == CPT - 1 ? rrel : 1)];
+            const float2 ym = XR[c - RS], yp = XR[c + RS], zm = XR[c + dzm], zp = XR[c + dzp];
+            float val = ctv[v] * me.x;
+            val += L.c2x * rcp_approx(me.y + xm.y) * (me.x - xm.x);
+            val += L.c2x * rcp_approx(me.y + xp.y) * (me.x - xp.x);
+            val += L.c2y * rcp_approx(me.y + ym.y) * (me.x - ym.x);
+            val += L.c2y * rcp_approx(me.y + yp.y) * (me.x - yp.x);
+            val += L.c2z * rcp_approx(me.y + zm.y) * (me.x - zm.x);
+            val += L.c2z * rcp_approx(me.y + zp.y) * (me.x - zp.x);
+            const float rv = fv[v] - val;
+            acc[v] = odd ? acc[v] + rv : rv;
+        }
+        float* const dst = fc + C.nx * (((j0 + wy) >> 1) + C.ny * (p >> 1)) + (lane >> 1);
+        if (odd) {                                        // x pairs; the odd row's sums to fc
+#pragma unroll
+            for (int v = 0; v < CPT; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], 1);
+            if ((wy & 1) && !(lane & 1)) {
+#pragma unroll
+                for (int v = 0; v < CPT; ++v) dst[16 * v] = acc[v];
+            }
+        }
+        if (p + 1 < k1) load_c(p + 1);
+        __syncthreads();
+        if (odd && !(wy & 1) && !(lane & 1)) {           // even row: add the odd row's sums, scale
+#pragma unroll
+            for (int v = 0; v < CPT; ++v) dst[16 * v] = (acc[v] + dst[16 * v]) * 0.125f;
+        }
+        if (stage) store(sm1);
+        __syncthreads();
+        const int t = sm1;
+        sm1 = s0;
+        s0 = sp1;
+        sp1 = t;
+    }
+}
+
+template <int CPT>
+static void launch_resid_restrict_row(const Lev32& F, const Geo& C, cudaStream_t s, const float* x, const float* f,
+                                      float* fc) {
+    constexpr int TY = 16;
+    const Geo& g = F.g;
+    const int ntile = g.ny / TY;
+    int chunks = std::max(1, std::min(g.nz / 2, 2 * 152 / ntile));
+    int KZ = hdiv(g.nz, chunks);
+    KZ += KZ & 1;                                         // chunks start on even planes
+    const dim3 grd(ntile, hdiv(g.nz, KZ)), blk(32, TY);
+    const size_t sm = apply_row_smem<CPT, TY>();
+    count_launches(1);
+    k_resid_restrict_row<CPT, TY><<<grd, blk, sm, s>>>(F, C, x, f, fc, KZ);
+}
+
 template <int CPT>
 static void launch_apply32_row(const Lev32& L, cudaStream_t s, const float* x, float* y, const float* r,
                                const Red& red, int slot_xy, int slot_xr) {
@@ -1326,8 +1487,15 @@ void launch_coarsen(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cuda
 }
 void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s,
                            const float* x, const float* f, float* fc) {
-    count_launches(1);
     const Geo& g = F.g;
+    if (hx && hy && hz && g.ny % 16 == 0 && g.nz % 2 == 0 && (g.nx == 256 || g.nx == 128) &&
+        ((uintptr_t)x & 7) == 0) {
+        // whole rows of 256 or 128 cells: a warp per row, 16 rows per block
+        if (g.nx == 256) launch_resid_restrict_row<8>(F, C.g, s, x, f, fc);
+        else launch_resid_restrict_row<4>(F, C.g, s, x, f, fc);
+        return;
+    }
+    count_launches(1);
     if (g.ny > 1 && g.nx % 32 == 0 && g.ny % 8 == 0 && g.nz >= 2 && (!hz || g.nz % 2 == 0)) {
         // whole TX x 8 tiles: the staged z-march; KZ (even) planes per block
         const int TXc = g.nx % 64 == 0 ? 64 : 32;
@@ -1366,6 +1534,10 @@ void rbgs_row_allow_smem() {
     rbgs_row_allow<4, 16>();
     apply_row_allow<8, 16>();
     apply_row_allow<4, 16>();
+    cudaFuncSetAttribute(k_resid_restrict_row<8, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)apply_row_smem<8, 16>());
+    cudaFuncSetAttribute(k_resid_restrict_row<4, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)apply_row_smem<4, 16>());
 }
 
 static bool aligned8(const void* p) { return ((uintptr_t)p & 7) == 0; }
