@@ -567,10 +567,10 @@ int solve_mixed_ir(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res, boo
     return rel <= o->rtol ? LM_OK : LM_ERR_NO_CONVERGENCE;
 }
 
-int copy_in(lm_grid* g, double* dst, const double* src, int on_device, cudaStream_t s) {
+int copy_in(lm_grid* g, double* dst, const double* src, int on_device, cudaStream_t s, bool sync = true) {
     CK(cudaMemcpyAsync(dst, src, sizeof(double) * g->N,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    if (!on_device) CK(cudaStreamSynchronize(s));   // the caller may reuse its host buffer
+    if (!on_device && sync) CK(cudaStreamSynchronize(s));   // the caller may reuse its host buffer
     return LM_OK;
 }
 
@@ -584,9 +584,11 @@ int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double
     int rc;
     if (!on_device) {
         if (!g->stage && (rc = dalloc(&g->stage, (size_t)3 * g->N))) return rc;
-        if ((rc = copy_in(g, g->stage, a_in, 0, s))) return rc;
-        if ((rc = copy_in(g, g->stage + g->N, rho_new, 0, s))) return rc;
-        if (!raw && (rc = copy_in(g, g->stage + 2 * (size_t)g->N, cs2, 0, s))) return rc;
+        // the host buffers are free again once the assembly below has been
+        // waited for, before this call returns
+        if ((rc = copy_in(g, g->stage, a_in, 0, s, false))) return rc;
+        if ((rc = copy_in(g, g->stage + g->N, rho_new, 0, s, false))) return rc;
+        if (!raw && (rc = copy_in(g, g->stage + 2 * (size_t)g->N, cs2, 0, s, false))) return rc;
         A = g->stage;
         R = g->stage + g->N;
         C = raw ? nullptr : g->stage + 2 * (size_t)g->N;
