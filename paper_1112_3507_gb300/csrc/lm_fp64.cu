@@ -30,17 +30,20 @@ __global__ void __launch_bounds__(NT) k_assemble(Geo g, const double* __restrict
         } else {
             const double ro = a_in[idx], c2 = cs2[idx];
             ok = ok && ro > 0.0 && isfinite(ro) && c2 > 0.0 && isfinite(c2);
-            c = 1.0 / ((dt * dt) * ro * c2);                   // Eq. cpoiss
+            c = __drcp_rn((dt * dt) * ro * c2);                // Eq. cpoiss: 1/(...) rounded to nearest
         }
         ok = ok && c > 0.0 && isfinite(c);
         if (!ok) atomicOr(bad, 1);
         int i, j, k;
         cell_coords(idx, g, i, j, k);
         // g_f = kappa_f / h^2 with kappa_f = 2/(rho_L + rho_R) (Eq. kappapoiss, harmonic
-        // mean), evaluated as (2/h^2)/(rho_L + rho_R): one float64 division per face
-        const double gxm = face_minus(i, g.nx, g.bcx) ? c2x / (rn + rho_new[nbr_x(idx, i, g).im]) : 0.0;
-        const double gym = face_minus(j, g.ny, g.bcy) ? c2y / (rn + rho_new[nbr_y(idx, j, g).im]) : 0.0;
-        const double gzm = face_minus(k, g.nz, g.bcz) ? c2z / (rn + rho_new[nbr_z(idx, k, g).im]) : 0.0;
+        // mean), evaluated as (2/h^2) * RN(1/(rho_L + rho_R)): a correctly rounded
+        // float64 reciprocal per face (cheaper than a division on GB300's float64
+        // pipe); exact scaling, so bit-identical to 2/(rho_L + rho_R)/h^2 when h is
+        // a power of two, within 2 ulp otherwise
+        const double gxm = face_minus(i, g.nx, g.bcx) ? c2x * __drcp_rn(rn + rho_new[nbr_x(idx, i, g).im]) : 0.0;
+        const double gym = face_minus(j, g.ny, g.bcy) ? c2y * __drcp_rn(rn + rho_new[nbr_y(idx, j, g).im]) : 0.0;
+        const double gzm = face_minus(k, g.nz, g.bcz) ? c2z * __drcp_rn(rn + rho_new[nbr_z(idx, k, g).im]) : 0.0;
         out.ct[idx] = c;
         out.gx[idx] = gxm;
         out.gy[idx] = gym;

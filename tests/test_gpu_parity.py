@@ -336,3 +336,28 @@ def test_full_size_convection_256():
     Ax = op.apply(x).ravel()
     idx = np.random.default_rng(3).integers(0, p.size, 4096)
     assert np.allclose(y[idx], Ax[idx], rtol=1e-13, atol=1e-13 * np.abs(Ax).max())
+
+
+@pytest.mark.parametrize("name", ["rows3d-256x32x8", "rows3d-walls-256x16x8"])
+def test_row_kernels_take_unaligned_vectors(name):
+    """The whole-row kernels read x in 8-byte pairs; vectors whose start is
+    only 4-byte aligned (a view one float into a buffer) take the tiled
+    kernels instead and give the same sweep and apply to float32 rounding."""
+    p = PROBLEMS[name]()
+    rng = np.random.default_rng(21)
+    f = rng.standard_normal(p.size).astype(np.float32)
+    x0 = rng.standard_normal(p.size).astype(np.float32)
+    with _grid(p) as g:
+        xa, fa = _dev(x0, torch.float32), _dev(f, torch.float32)
+        xu = torch.zeros(p.size + 1, dtype=torch.float32, device="cuda")[1:]
+        yu = torch.zeros(p.size + 1, dtype=torch.float32, device="cuda")[1:]
+        xu.copy_(xa)
+        assert xu.data_ptr() % 8 == 4 and yu.data_ptr() % 8 == 4
+        ya = torch.empty_like(xa)
+        for order in (0, 1):
+            g.mg_sweep(xa, fa, ya, order)
+            g.mg_sweep(xu, fa, yu, order)
+            assert torch.allclose(yu, ya, rtol=1e-5, atol=1e-5 * float(ya.abs().max()))
+        g.apply(xa, ya, prec=lm().PREC_FP32)
+        g.apply(xu, yu, prec=lm().PREC_FP32)
+        assert torch.allclose(yu, ya, rtol=1e-5, atol=1e-5 * float(ya.abs().max()))
