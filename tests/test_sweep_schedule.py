@@ -1,0 +1,129 @@
+"""The schedule of the whole-row red-black sweep, checked on the CPU.
+
+The 3D sweep kernel for levels with whole rows (k_rbgs_row) gives each block
+the rows j0 .. j0 + TY - 1 of a chunk of planes k0 .. k1 - 1 and marches up z:
+at step p it updates the first colour of plane p on its rows and one halo row
+each side, and the second colour of plane p - 2 on its rows, both from the
+values staged at the start of the step (one barrier per step); plane p - 3 is
+then final.  Halo rows, halo planes and rows past a periodic edge come from
+the sweep's input.  This test replays that schedule with numpy on small grids
+(several row tiles and z chunks, walls and periodic axes) and checks that it
+reproduces the oracle's sequential red-black sweep: the reading that the
+lag-two schedule needs no second barrier and no cross-block communication.
+The arithmetic of each update uses the oracle's face conductances; only the
+order of the updates is under test.
+"""
+import numpy as np
+import pytest
+
+from oracle import multigrid as OM
+from oracle import poisson as P
+
+PER, NEU = P.PERIODIC, P.NEUMANN
+
+
+def _faces(level):
+    """Per-cell conductances of the six faces, indexed [face][k, j, i]."""
+    op = level.op
+    gs = []
+    for a in range(3):
+        gs += [op.g_minus[a], op.g_plus(a)]
+    return gs
+
+
+def _row_schedule_sweep(level, x_in, f, first, TY, KZ, lag=2):
+    nz, ny, nx = level.shape
+    bcx, bcy, bcz = level.bc
+    g = _faces(level)
+    ct = level.ct
+    out = np.full_like(x_in, np.nan)
+
+    def wrap(n, c, bc):
+        if 0 <= c < n:
+            return c
+        return c % n if bc == PER else None
+
+    for j0 in range(0, ny, TY):
+        for k0 in range(0, nz, KZ):
+            k1 = min(k0 + KZ, nz)
+            rows = [wrap(ny, j0 - 2 + r, bcy) for r in range(TY + 4)]
+
+            def stage(p):
+                kw = wrap(nz, p, bcz)
+                a = np.zeros((TY + 4, nx))
+                if kw is not None:
+                    for r, jw in enumerate(rows):
+                        if jw is not None:
+                            a[r] = x_in[kw, jw]
+                return a
+
+            ring = {p: stage(p) for p in (k0 - 2, k0 - 1, k0)}
+
+            def update(snap, p, r, colour):
+                """New values of the colour-`colour` cells of staged row r on plane p."""
+                kw, jw = wrap(nz, p, bcz), rows[r]
+                i = np.arange(nx)
+                xc = snap[p]
+                xm, xp = np.roll(xc[r], 1), np.roll(xc[r], -1)     # x walls: face weight 0
+                num = f[kw, jw] + g[0][kw, jw] * xm + g[1][kw, jw] * xp
+                num = num + g[2][kw, jw] * xc[r - 1] + g[3][kw, jw] * xc[r + 1]
+                num = num + g[4][kw, jw] * snap[p - 1][r] + g[5][kw, jw] * snap[p + 1][r]
+                d = ct[kw, jw] + sum(g[q][kw, jw] for q in range(6))
+                sel = ((i + jw + kw) & 1) == colour
+                return sel, num / d
+
+            for p in range(k0 - 1, k1 + lag + 1):
+                snap = {q: a.copy() for q, a in ring.items()}      # the state at the barrier
+                writes = []
+                if p <= k1 and wrap(nz, p, bcz) is not None:
+                    for r in range(1, TY + 3):                    # the block's rows and one halo row each side
+                        if rows[r] is not None:
+                            writes.append((p, r) + update(snap, p, r, first))
+                q = p - lag
+                if k0 <= q < k1:
+                    for r in range(2, TY + 2):
+                        writes.append((q, r) + update(snap, q, r, 1 - first))
+                for pl, r, sel, v in writes:
+                    ring[pl][r][sel] = v[sel]
+                w = p - lag - 1                                   # final since the last step
+                if k0 <= w < k1:
+                    out[w, j0:j0 + TY] = ring[w][2:TY + 2]
+                    del ring[w]
+                if p + 2 <= k1 + 1:
+                    ring[p + 2] = stage(p + 2)
+    return out
+
+
+@pytest.mark.parametrize("shape,bc,TY,KZ", [
+    ((7, 32, 16), (PER, PER, NEU), 16, 3),       # (nz, ny, nx); bc per axis x, y, z
+    ((6, 16, 8), (NEU, NEU, PER), 8, 2),
+    ((8, 16, 12), (PER, NEU, PER), 16, 8),
+    ((5, 24, 10), (NEU, PER, NEU), 8, 1),
+])
+@pytest.mark.parametrize("order", ["RB", "BR"])
+def test_row_schedule_equals_sequential_sweep(shape, bc, TY, KZ, order):
+    rng = np.random.default_rng(sum(shape) + KZ)
+    ct = rng.uniform(0.05, 1.0, shape)
+    rho = rng.uniform(1.0, 20.0, shape)
+    level = OM.Level(ct, rho, (0.3, 0.5, 0.7), bc)
+    x = rng.standard_normal(shape)
+    f = rng.standard_normal(shape)
+    ref = OM.sweep(level, x, f, order)
+    got = _row_schedule_sweep(level, x, f, 0 if order == "RB" else 1, TY, KZ)
+    assert not np.isnan(got).any()
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_row_schedule_catches_a_one_plane_lag():
+    """Planted mistake: the second colour only one plane behind the first,
+    still with one barrier per step, reads plane q + 1's first colour before
+    that step's update is visible; the replay then differs from the sweep."""
+    shape, bc = (6, 16, 8), (PER, PER, NEU)
+    rng = np.random.default_rng(5)
+    level = OM.Level(rng.uniform(0.05, 1.0, shape), rng.uniform(1.0, 20.0, shape), (0.3, 0.5, 0.7), bc)
+    x, f = rng.standard_normal(shape), rng.standard_normal(shape)
+    ref = OM.sweep(level, x, f, "RB")
+    good = _row_schedule_sweep(level, x, f, 0, 16, 3, lag=2)
+    np.testing.assert_allclose(good, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    bad = _row_schedule_sweep(level, x, f, 0, 16, 3, lag=1)
+    assert not np.allclose(bad, ref, rtol=1e-6, atol=1e-6)
