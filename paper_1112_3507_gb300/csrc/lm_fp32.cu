@@ -182,16 +182,16 @@ __global__ void __launch_bounds__(256) k_apply32_zm(Lev32 L, const float* __rest
 // past a Neumann wall x = 0 and rho = +inf, so that face's weight is 0).
 // Lane t of warp w computes the cells t + 32 v of row j0 + w, so every
 // shared-memory and global access of a warp is contiguous.  A step computes
-// plane p, then (after a barrier) stages plane p + 2, loaded at the start of
-// the step, into plane p - 1's slot.  The ring is small enough for two
-// blocks per SM.  Fused dot products as in k_apply32_zm.
+// plane p from the slots of planes p - 1 .. p + 1 and stages plane p + 2,
+// loaded at the start of the step, into the fourth slot: one barrier per
+// step.  Fused dot products as in k_apply32_zm.
 template <int CPT, int TY>
 constexpr size_t apply_row_smem() {
-    return sizeof(float2) * 3 * (TY + 2) * (32 * CPT + 4);
+    return sizeof(float2) * 4 * (TY + 2) * (32 * CPT + 4);
 }
 
 template <int CPT, int TY, bool DOT_XY, bool DOT_XR>
-__global__ void __launch_bounds__(32 * TY, 2) k_apply32_row(Lev32 L, const float* __restrict__ x,
+__global__ void __launch_bounds__(32 * TY, 1) k_apply32_row(Lev32 L, const float* __restrict__ x,
                                                            float* __restrict__ y, const float* __restrict__ r,
                                                            Red red, int slot_xy, int slot_xr, int KZ) {
     constexpr int NX = 32 * CPT, RS = NX + 4, NRW = TY + 2, PL = NRW * RS, H = CPT / 2;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(32 * TY, 2) k_apply32_row(Lev32 L, const float
     const int j0 = blockIdx.x * TY, k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
     const int sz = NX * g.ny, i2 = 2 * lane;
     const float INF = __int_as_float(0x7f800000);
-    for (int t = tid; t < 3 * NRW; t += 32 * TY) {       // row-end ghosts: x = 0, rho = +inf
+    for (int t = tid; t < 4 * NRW; t += 32 * TY) {       // row-end ghosts: x = 0, rho = +inf
         XR[t * RS + 1] = make_float2(0.f, INF);
         XR[t * RS + NX + 2] = make_float2(0.f, INF);
     }
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(32 * TY, 2) k_apply32_row(Lev32 L, const float
     const int lrel = (lane == 0 && perx) ? NX - 1 : -1;         // left of cell 0, right of cell nx - 1
     const int rrel = (lane == 31 && perx) ? 1 - NX : 1;
     FF axy{0.f, 0.f}, axr{0.f, 0.f};
-    int sm1 = 0, s0 = 1, sp1 = 2;                         // slots of planes p - 1, p, p + 1
+    int sm1 = 0, s0 = 1, sp1 = 2, sp2 = 3;                // slots of planes p - 1 .. p + 2
     fetch(k0 - 1);
     store(sm1);
     fetch(k0);
@@ -310,13 +310,13 @@ __global__ void __launch_bounds__(32 * TY, 2) k_apply32_row(Lev32 L, const float
             if (DOT_XR) ff_add_prod(axr, me.x, rrv[v]);
         }
         if (p + 1 < k1) load_c(p + 1);
-        __syncthreads();
-        if (stage) store(sm1);                            // plane p + 2 takes plane p - 1's slot
+        if (stage) store(sp2);                            // no one reads that slot in this step
         __syncthreads();
         const int t = sm1;
         sm1 = s0;
         s0 = sp1;
-        sp1 = t;
+        sp1 = sp2;
+        sp2 = t;
     }
     if (DOT_XY && DOT_XR) {
         double v[2] = {ff_value(axy), ff_value(axr)};
@@ -1227,7 +1227,7 @@ static dim3 cell_grid(const Geo& g) {
 // even row (after the block barrier) adds to its own and scales.  For levels
 // halved along all three axes.
 template <int CPT, int TY>
-__global__ void __launch_bounds__(32 * TY, 2) k_resid_restrict_row(Lev32 L, Geo C, const float* __restrict__ x,
+__global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo C, const float* __restrict__ x,
                                                                   const float* __restrict__ f,
                                                                   float* __restrict__ fc, int KZ) {
     constexpr int NX = 32 * CPT, RS = NX + 4, NRW = TY + 2, PL = NRW * RS, H = CPT / 2;
@@ -1239,7 +1239,7 @@ __global__ void __launch_bounds__(32 * TY, 2) k_resid_restrict_row(Lev32 L, Geo 
     const int j0 = blockIdx.x * TY, k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
     const int sz = NX * g.ny, i2 = 2 * lane;
     const float INF = __int_as_float(0x7f800000);
-    for (int t = tid; t < 3 * NRW; t += 32 * TY) {
+    for (int t = tid; t < 4 * NRW; t += 32 * TY) {
         XR[t * RS + 1] = make_float2(0.f, INF);
         XR[t * RS + NX + 2] = make_float2(0.f, INF);
     }
@@ -1312,7 +1312,10 @@ __global__ void __launch_bounds__(32 * TY, 2) k_resid_restrict_row(Lev32 L, Geo 
     };
     const int lrel = (lane == 0 && perx) ? NX - 1 : -1;
     const int rrel = (lane == 31 && perx) ? 1 - NX : 1;
-    int sm1 = 0, s0 = 1, sp1 = 2;
+    int sm1 = 0, s0 = 1, sp1 = 2, sp2 = 3;
+    // an even row's pair sums wait one step (one barrier) for the odd row's
+    float accP[CPT];
+    float* dstP = nullptr;
     fetch(k0 - 1);
     store(sm1);
     fetch(k0);
@@ -1321,9 +1324,17 @@ __global__ void __launch_bounds__(32 * TY, 2) k_resid_restrict_row(Lev32 L, Geo 
     store(sp1);
     load_c(k0);
     __syncthreads();
+    auto finish_pairs = [&]() {                           // even row: add the odd row's sums, scale
+        if (dstP) {
+#pragma unroll
+            for (int v = 0; v < CPT; ++v) dstP[16 * v] = (accP[v] + dstP[16 * v]) * 0.125f;
+            dstP = nullptr;
+        }
+    };
     for (int p = k0; p < k1; ++p) {
         const bool stage = p + 2 <= k1;
         if (stage) fetch(p + 2);
+        finish_pairs();
         const int b0 = (s0 * NRW + rT) * RS + 2 + lane, dzm = (sm1 - s0) * PL, dzp = (sp1 - s0) * PL;
         const bool odd = (p - k0) & 1;                    // second plane of a pair (k0 is even)
 #pragma unroll
@@ -1346,24 +1357,27 @@ __global__ void __launch_bounds__(32 * TY, 2) k_resid_restrict_row(Lev32 L, Geo 
         if (odd) {                                        // x pairs; the odd row's sums to fc
 #pragma unroll
             for (int v = 0; v < CPT; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], 1);
-            if ((wy & 1) && !(lane & 1)) {
+            if (!(lane & 1)) {
+                if (wy & 1) {
 #pragma unroll
-                for (int v = 0; v < CPT; ++v) dst[16 * v] = acc[v];
+                    for (int v = 0; v < CPT; ++v) dst[16 * v] = acc[v];
+                } else {
+#pragma unroll
+                    for (int v = 0; v < CPT; ++v) accP[v] = acc[v];
+                    dstP = dst;
+                }
             }
         }
         if (p + 1 < k1) load_c(p + 1);
-        __syncthreads();
-        if (odd && !(wy & 1) && !(lane & 1)) {           // even row: add the odd row's sums, scale
-#pragma unroll
-            for (int v = 0; v < CPT; ++v) dst[16 * v] = (acc[v] + dst[16 * v]) * 0.125f;
-        }
-        if (stage) store(sm1);
+        if (stage) store(sp2);
         __syncthreads();
         const int t = sm1;
         sm1 = s0;
         s0 = sp1;
-        sp1 = t;
+        sp1 = sp2;
+        sp2 = t;
     }
+    finish_pairs();                                       // the last step ended with a barrier
 }
 
 template <int CPT>
@@ -1372,7 +1386,7 @@ static void launch_resid_restrict_row(const Lev32& F, const Geo& C, cudaStream_t
     constexpr int TY = 16;
     const Geo& g = F.g;
     const int ntile = g.ny / TY;
-    int chunks = std::max(1, std::min(g.nz / 2, 2 * 152 / ntile));
+    int chunks = std::max(1, std::min(g.nz / 2, 152 / ntile));
     int KZ = hdiv(g.nz, chunks);
     KZ += KZ & 1;                                         // chunks start on even planes
     const dim3 grd(ntile, hdiv(g.nz, KZ)), blk(32, TY);
@@ -1387,7 +1401,7 @@ static void launch_apply32_row(const Lev32& L, cudaStream_t s, const float* x, f
     constexpr int TY = 16;
     const Geo& g = L.g;
     const int ntile = g.ny / TY;
-    const int chunks = std::max(1, std::min(g.nz / 2, 2 * 152 / ntile));
+    const int chunks = std::max(1, std::min(g.nz / 2, 152 / ntile));
     const int KZ = hdiv(g.nz, chunks);
     const dim3 grd(ntile, hdiv(g.nz, KZ)), blk(32, TY);
     const size_t sm = apply_row_smem<CPT, TY>();
