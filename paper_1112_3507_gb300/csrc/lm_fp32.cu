@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_apply32_zm(Lev32 L, const float* __rest
 //
 // For 3D levels with nx = 32 CPT, ny a multiple of TY and nz >= 2 (the
 // levels the whole-row sweep takes).  A block owns all nx columns of TY rows
-// over a chunk of KZ planes and marches up z with a three-plane ring of
+// over a chunk of KZ planes and marches up z with a four-plane ring of
 // (x, rho) staged on its rows plus one row each side (periodic axes wrapped;
 // past a Neumann wall x = 0 and rho = +inf, so that face's weight is 0).
 // Lane t of warp w computes the cells t + 32 v of row j0 + w, so every
@@ -1224,8 +1224,8 @@ static dim3 cell_grid(const Geo& g) {
 // staging and stencil of k_apply32_row; a thread adds the residuals of its
 // cells over a plane pair, lanes 2 i and 2 i + 1 combine the x pair by a
 // shuffle, and the odd row of each row pair stores its sums in fc, which the
-// even row (after the block barrier) adds to its own and scales.  For levels
-// halved along all three axes.
+// even row adds to its own and scales at the next step (after the step's
+// barrier).  For levels halved along all three axes.
 template <int CPT, int TY>
 __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo C, const float* __restrict__ x,
                                                                   const float* __restrict__ f,
