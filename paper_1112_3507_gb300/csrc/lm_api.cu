@@ -678,6 +678,10 @@ int lm_grid_create(int ndim, const int64_t n[3], const double h[3], const int bc
         return code;
     };
     if (cudaGetDevice(&g->device) != cudaSuccess) return fail(LM_ERR_CUDA);
+    // the whole-row and one-block coarse-cycle kernels need more than the
+    // default 48 KB of shared memory: allow it before any entry point launches them
+    rbgs_row_allow_smem();
+    coarse_cycle_allow_smem();
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device);
     const long long want = (N + NT - 1) / NT;

@@ -361,3 +361,28 @@ def test_row_kernels_take_unaligned_vectors(name):
         g.apply(xa, ya, prec=lm().PREC_FP32)
         g.apply(xu, yu, prec=lm().PREC_FP32)
         assert torch.allclose(yu, ya, rtol=1e-5, atol=1e-5 * float(ya.abs().max()))
+
+
+def test_first_call_in_a_fresh_process_is_the_float32_apply():
+    """The whole-row kernels need more than 48 KB of shared memory, which the
+    library allows when a grid is created: a process whose first call is the
+    float32 apply on a 256-cell-row grid (no solve or cycle before it) gets
+    the same values as after a V-cycle."""
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_1112_3507_gb300 import lowmach as lm, inputs as I\n"
+        "p = I.make_problem(256, 8, 32, ma=0.01, contrast=15.0, noise=0.01, seed=12)\n"
+        "g = lm.Grid.for_problem(p); g.set_problem(p)\n"
+        "x = torch.randn(p.size, dtype=torch.float32, device='cuda', generator=torch.Generator('cuda').manual_seed(3))\n"
+        "y1 = torch.empty_like(x); y2 = torch.empty_like(x)\n"
+        "g.apply(x, y1, prec=lm.PREC_FP32)\n"
+        "z = torch.zeros_like(x); g.mg_vcycle(x, z, 1, 1)\n"
+        "g.apply(x, y2, prec=lm.PREC_FP32)\n"
+        "torch.cuda.synchronize()\n"
+        "assert torch.equal(y1, y2), 'first apply differs'\n"
+        "print('ok')\n")
+    root = __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
