@@ -275,6 +275,9 @@ int  lm_net_features(lm_grid* g, const double* v, float* feat, double* scale, vo
  * z-chunk of every level shape is chosen by the autotuner (see
  * lm_autotune_set_cache).  The captured plan is cached per (grids,
  * coefficient versions, inner_max_iter, use_x0) and reused by later calls.
+ * Grids whose coefficients changed since their last solve get their
+ * multigrid hierarchies refreshed first, their coarsest-level inverses all
+ * formed in one launch.
  * Requirements: 2D grids (ndim 2), nu1 = nu2 = 1 (lm_default_opts sets 2 and 3:
  * set both to 1 for a batch), an exactly solved coarsest
  * level (grids whose halvings reach <= 64 cells), even periodic extents.
