@@ -158,106 +158,155 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_calibrate(name: str, seed: int = 1):
-    """The workload's problem and oracle operator, and the oracle's own
-    iteration count to the workload's tolerance: measured on downsized grids
-    of the same recipe and extrapolated by the fitted growth per doubling."""
+ORACLE_SEEDS = (1, 2, 3)
+
+
+def host_cores() -> int:
+    """Host cores this process may run on (its CPU affinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_calibrate(name: str, seeds=ORACLE_SEEDS):
+    """The oracle's own iteration count to the workload's tolerance, averaged
+    over `seeds`.  3D workloads: measured on downsized grids of the same
+    recipe (n/16, n/8, n/4 for n <= 256) and extrapolated by the fitted growth
+    per grid doubling (an estimate); 2D workloads: the full-size count."""
     from oracle import poisson as P
     w = WORKLOADS[name]
-    p = make_problem(name, seed)
-    op = P.operator_from_problem(p)
-    counts = []
     n = w["n"]
     big = n // 8 if n > 256 else n // 4               # largest downsized grid the oracle solves in seconds
-    sizes = [big // 4, big // 2, big] if w["kind"] in ("conv3d", "semi3d") else [n]
-    for m in sizes:
-        q = downsized(name, m, seed) if len(sizes) > 1 else p
-        _, c, _ = P.solve_pcg_jacobi(P.operator_from_problem(q), q.f, rtol=p.rtol, maxiter=200000)
-        counts.append(c)
-    if len(counts) > 1:
-        growth = (counts[-1] / counts[0]) ** (1.0 / (len(counts) - 1))
-        est_iters = counts[-1] * growth ** round(np.log2(n / big))
-    else:
-        est_iters = counts[0]
-    return p, op, counts, float(est_iters)
+    three_d = w["kind"] in ("conv3d", "semi3d")
+    sizes = [big // 4, big // 2, big] if three_d else [n]
+    per_seed, ests = [], []
+    for seed in (seeds if w["kind"] != "semi3d" else seeds[:1]):
+        counts = []
+        for m in sizes:
+            q = downsized(name, m, seed) if three_d else make_problem(name, seed)
+            _, c, _ = P.solve_pcg_jacobi(P.operator_from_problem(q), q.f, rtol=q.rtol, maxiter=200000)
+            counts.append(c)
+        if len(counts) > 1:
+            growth = (counts[-1] / counts[0]) ** (1.0 / (len(counts) - 1))
+            ests.append(counts[-1] * growth ** round(np.log2(n / big)))
+        else:
+            ests.append(counts[0])
+        per_seed.append(counts)
+    return per_seed, float(np.mean(ests)), three_d
 
 
-def oracle_steps(name: str, steps: int, warmup: int, iters_per_step: int = 2) -> dict:
-    """The reference arm: calibrate once, then time warmup + steps bounded
-    samples, each `iters_per_step` full-size iterations of the oracle's
-    float64 Jacobi-PCG (its set-up included); each sample's time per
-    iteration times the oracle's iteration count to tolerance is that step's
-    estimated time to tolerance."""
+_OW = None      # (operator, rhs) of an oracle worker process
+
+
+def _oracle_worker(name, k, rounds, barrier, out):
+    """One oracle process: build the workload (seed 1) and its operator, then
+    time `rounds` bounded samples in step with the other workers: the
+    Jacobi-PCG set-up alone (maxiter = 0) and the set-up plus k iterations."""
     from oracle import poisson as P
-    p, op, counts, est_iters = oracle_calibrate(name)
-    per_iter = []
-    for k in range(warmup + steps):
+    p = make_problem(name, 1)
+    op = P.operator_from_problem(p)
+    barrier.wait()
+    for _ in range(rounds):
+        barrier.wait()
         t0 = time.perf_counter()
-        P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=iters_per_step)
-        if k >= warmup:
-            per_iter.append((time.perf_counter() - t0) / iters_per_step)
-    return dict(per_iter_s=per_iter, est_iters=est_iters, downsized_counts=counts, N=p.size,
-                iters_per_step=iters_per_step)
+        P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=0)
+        t1 = time.perf_counter()
+        P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=k)
+        t2 = time.perf_counter()
+        out.put((t1 - t0, max((t2 - t1) - (t1 - t0), 1e-9) / k))
 
 
-def oracle_sample(name: str, iters: int = 2, seed: int = 1) -> dict:
-    """Time the oracle's float64 Jacobi-PCG on the workload (single-threaded
-    numpy): one run of 1 iteration and one of 1 + `iters` iterations give the
-    set-up time and the time per iteration.  The oracle's own iteration count
-    to the workload's tolerance is measured on downsized grids (n/16, n/8,
-    n/4) and extrapolated by the fitted growth per grid doubling.  Returns the
-    estimated time to tolerance and the GDOF/s it implies."""
-    from oracle import poisson as P
-    p, op, counts, est_iters = oracle_calibrate(name, seed)
-    P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1)          # warm-up (first-touch of the arrays)
-    t0 = time.perf_counter()
-    P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1)
-    t1 = time.perf_counter()
-    _, it, _ = P.solve_pcg_jacobi(op, p.f, rtol=0.0, maxiter=1 + iters)
-    t2 = time.perf_counter()
-    t_iter = max((t2 - t1) - (t1 - t0), 1e-9) / max(it - 1, 1)
-    t_setup = max((t1 - t0) - t_iter, 0.0)
-    est_s = t_setup + t_iter * est_iters
-    return dict(t_iter_s=t_iter, t_setup_s=t_setup, sample_iters=it + 1, est_iters=float(est_iters),
-                downsized_counts=counts, est_time_s=est_s, value=p.size / est_s / 1e9, N=p.size)
+def oracle_time(name: str, k: int, procs: int, rounds: int) -> list:
+    """`rounds` bounded samples of the oracle on `procs` concurrent processes
+    (spawned, one problem each, single-threaded numpy): per round the
+    slowest process's set-up time and time per iteration."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(procs), ctx.Queue()
+    ws = [ctx.Process(target=_oracle_worker, args=(name, k, rounds, barrier, out)) for _ in range(procs)]
+    for w in ws:
+        w.start()
+    res = []
+    for _ in range(rounds):
+        got = [out.get(timeout=3600) for _ in range(procs)]
+        res.append((max(g[0] for g in got), max(g[1] for g in got)))
+    for w in ws:
+        w.join()
+    return res
 
 
-def oracle_subprocess(name: str, iters: int, call: str | None = None) -> dict:
-    """Run an oracle timing in a single-threaded child process."""
+def oracle_report(name: str, k: int = 3, steps: int = 1, warmup: int = 0, legs: str = "single,all") -> dict:
+    """Calibrate the oracle's iteration count (seeds 1-3), then time the
+    workload's bounded sample on the legs asked for: "single" (one
+    single-threaded process) and "all" (one process per host core at once,
+    independent replicas).  Per step: the estimated time to tolerance =
+    set-up + time per iteration x iterations."""
+    per_seed, est_iters, extrapolated = oracle_calibrate(name)
+    N = make_problem(name, 1).size if WORKLOADS[name]["kind"] != "batch" else 0
+    out = dict(N=N, est_iters=est_iters, per_seed_counts=per_seed, extrapolated=extrapolated, k=k,
+               host_cores=host_cores())
+    want = legs.split(",")
+    todo = ([("single", 1)] if "single" in want or host_cores() == 1 else []) + \
+        ([("all", host_cores())] if "all" in want and host_cores() > 1 else [])
+    for leg, procs in todo:
+        r = oracle_time(name, k, procs, warmup + steps)[warmup:]
+        est = [su + it * est_iters for su, it in r]
+        out[leg] = dict(procs=procs, setup_s=[su for su, _ in r], per_iter_s=[it for _, it in r], est_time_s=est,
+                        value=[procs * N / e / 1e9 for e in est])
+    return out
+
+
+def oracle_subprocess(call: str) -> dict:
+    """Run an oracle timing in a child process with single-threaded numpy."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    call = call or "bench.oracle_sample(%r, %d)" % (name, iters)
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
             "print('ORACLE_JSON', json.dumps(%s))" % (ROOT, call))
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600,
+                       cwd=ROOT)
     for line in r.stdout.splitlines():
         if line.startswith("ORACLE_JSON"):
             return json.loads(line.split(" ", 1)[1])
     raise RuntimeError("oracle sample failed:\n" + r.stdout[-2000:] + r.stderr[-2000:])
 
 
-def cpu_block(s: dict, name: str) -> dict:
-    return {"value": s["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{s['sample_iters']} iterations of the FP64 oracle's Jacobi-PCG on {name} "
-                       f"({s['t_iter_s']:.3f} s/iter + {s['t_setup_s']:.2f} s set-up, single-threaded numpy) "
-                       f"x its iteration count to rtol "
-                       f"extrapolated from downsized grids {s['downsized_counts']} -> {s['est_iters']:.0f}; "
-                       f"estimated time to tolerance {s['est_time_s']:.1f} s")}
+def _leg_text(r: dict, leg: str, name: str) -> str:
+    L = r[leg]
+    return (f"{L['procs']} concurrent single-threaded process(es), each {r['k']} iterations of the FP64 oracle's "
+            f"Jacobi-PCG on {name} seed 1 (median {statistics.median(L['per_iter_s']) * 1e3:.4g} ms/iteration + "
+            f"{statistics.median(L['setup_s']) * 1e3:.4g} ms set-up)")
+
+
+def cpu_block(r: dict, name: str) -> dict:
+    """cpu_baseline: the all-cores leg (one replica per host core), with the
+    single-thread leg beside it."""
+    main = "all" if "all" in r else "single"
+    est = ("extrapolated from downsized grids" if r["extrapolated"] else "measured at full size")
+    counts = " ".join(str(c) for c in r["per_seed_counts"])
+    blk = {"value": statistics.median(r[main]["value"]), "unit": UNIT, "cores": r[main]["procs"], "kind": "oracle",
+           "host_cores": r["host_cores"],
+           "sample": (f"{_leg_text(r, main, name)} x the oracle's iteration count to rtol, {est} "
+                      f"(seeds 1-3: {counts} -> {r['est_iters']:.0f}); estimated time to tolerance "
+                      f"{statistics.median(r[main]['est_time_s']):.4g} s per solve; value = replicas x cells / "
+                      f"that time")}
+    if main == "all" and "single" in r:
+        blk["single_thread"] = {"value": statistics.median(r["single"]["value"]), "cores": 1,
+                                "sample": _leg_text(r, "single", name),
+                                "est_time_s": statistics.median(r["single"]["est_time_s"])}
+    return blk
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    r = oracle_subprocess(args.workload, 0, call="bench.oracle_steps(%r, %d, %d)" % (args.workload, args.steps,
-                                                                                   args.warmup))
-    t_iter = statistics.median(r["per_iter_s"])
-    est = t_iter * r["est_iters"]
-    value = r["N"] / est / 1e9
-    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": (f"per step {r['iters_per_step']} full-size iterations of the FP64 oracle's Jacobi-PCG on "
-                      f"{args.workload} (single-threaded numpy; median {t_iter:.3f} s/iter over {args.steps} "
-                      f"steps) x its iteration count to rtol extrapolated from downsized grids "
-                      f"{r['downsized_counts']} -> {r['est_iters']:.0f}; estimated time to tolerance {est:.1f} s")}
+    r = oracle_subprocess("bench.oracle_report(%r, %d, %d, %d, 'all')" % (args.workload, args.oracle_iters,
+                                                                            args.steps, args.warmup))
+    leg = r["all"] if "all" in r else r["single"]
+    est = statistics.median(leg["est_time_s"])
+    value = statistics.median(leg["value"])
+    cpu = cpu_block(r, args.workload)
+    cpu["sample"] = f"per step: {cpu['sample']}"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -268,6 +317,26 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def fp64_roof(t_s: float, N: int, bytes_per_cell: int, fp64_ops_per_cell: int, hbm_gbs: float,
+              fp64_per_s: float, note: str) -> dict:
+    """A float64 kernel against its roof min(HBM, float64 issue): the time
+    it would take at each bound, the larger of the two (the roof), and the
+    fraction of that roof the measured time reaches."""
+    t_hbm = bytes_per_cell * N / (hbm_gbs * 1e9)
+    out = {"launch_us": t_s * 1e6, "bytes_per_cell": bytes_per_cell, "hbm_bound_us": t_hbm * 1e6,
+           "hbm_frac": t_hbm / t_s, "note": note}
+    if fp64_ops_per_cell is None:
+        # an op count the source does not fix (library reciprocals): the
+        # float64 operations a cell the measured time corresponds to
+        out["fp64_ops_per_cell_implied"] = t_s * fp64_per_s / N
+        return out
+    t_fp64 = fp64_ops_per_cell * N / fp64_per_s
+    roof = max(t_hbm, t_fp64)
+    out.update({"fp64_ops_per_cell": fp64_ops_per_cell, "fp64_bound_us": t_fp64 * 1e6,
+                "bound": "fp64" if t_fp64 >= t_hbm else "hbm", "frac_of_roof": roof / t_s})
+    return out
+
+
 def time_kernel(torch, fn, reps: int, stream) -> float:
     """Average duration (s) of fn() launched `reps` times, CUDA events on `stream`."""
     fn()
@@ -366,8 +435,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     kind = WORKLOADS[args.workload]["kind"]
     mode = args.mode or DEFAULT_MODE.get(kind, "mixed")
-    # the learned workload cycles through 8 held-out problems; the others solve one
-    probs = [make_problem(args.workload, seed=1 + k) for k in range(8 if kind == "train2d" else 1)]
+    # the learned workload cycles through 8 held-out problems, the convection
+    # workloads through seeds 1-3; the two-component recipe has one seed (7)
+    nprob = {"train2d": 8, "conv3d": 3, "plain2d": 3}.get(kind, 1)
+    probs = [make_problem(args.workload, seed=1 + k) for k in range(nprob)]
     p = probs[0]
     N = p.size
     dev_in = [[torch.as_tensor(a.ravel(), device=dev) for a in (q.rho_old, q.rho_new, q.cs2, q.f)] for q in probs]
@@ -476,6 +547,14 @@ def run_ours(args):
     x64 = torch.randn(N, dtype=torch.float64, device=dev)
     y64 = torch.empty_like(x64)
     t_k64 = time_kernel(torch, lambda: g.apply(x64, y64, prec=lm.PREC_FP64, stream=stream), reps, stream)
+    # the float64 roof: this GPU's measured float64 FMA rate (lm_probe_rate),
+    # and the float64 kernels against min(HBM, float64 issue)
+    fp64_rate = lm.probe_rate(0, 20000, stream)
+    fp32_rate = lm.probe_rate(1, 200000, stream)
+    ro0, rn0, c20, _ = dev_in[0]
+    t_asm = time_kernel(torch, lambda: g.set_coefficients(ro0, rn0, c20, probs[0].dt, stream), 5, stream)
+    jac_iters = max(base["jacobi"]["iters"], 1)
+    t_jac_iter = base["jacobi"]["time_to_tol_ms"] * 1e-3 / jac_iters
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -489,7 +568,8 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_block(oracle_subprocess(args.workload, args.oracle_iters), args.workload)
+        cpu = cpu_block(oracle_subprocess("bench.oracle_report(%r, %d)" % (args.workload, args.oracle_iters)),
+                        args.workload)
 
     if rank == 0:
         line = {
@@ -519,8 +599,21 @@ def run_ours(args):
                          "also": {"apply32": {"bytes_per_cell": 16, "launch_us": t_ap * 1e6,
                                                  "achieved": 16 * N / t_ap / 1e9,
                                                  "frac": 16 * N / t_ap / 1e9 / peak},
-                                  "k_apply64": {"launch_us": t_k64 * 1e6,
-                                                "note": "float64 ALU-bound on GB300, not HBM-bound"}}},
+                                  "k_apply64": fp64_roof(t_k64, N, 48, 14, peak, fp64_rate,
+                                                         "y = A x and x.(A x): 13 float64 operations a cell "
+                                                         "for the stencil, 1 for the dot"),
+                                  "k_assemble": fp64_roof(t_asm, N, 72, None, peak, fp64_rate,
+                                                          "c~ and three faces: 14 float64 operations and 4 "
+                                                          "correctly rounded float64 reciprocals a cell; timed "
+                                                          "through lm_set_coefficients (includes its host sync)"),
+                                  "fp64_jacobi_pcg_iteration": fp64_roof(
+                                      t_jac_iter, N, 120, 21, peak, fp64_rate,
+                                      "apply + p.q (14 ops), x/r update with r.r and r.z (5), p update (2); "
+                                      "three launches, 120 B a cell")}},
+            "fp64_peak": {"fma_per_s": fp64_rate, "tflops": 2 * fp64_rate / 1e12,
+                          "fp32_fma_per_s": fp32_rate, "ratio_fp32_to_fp64": fp32_rate / fp64_rate,
+                          "source": "lm_probe_rate: 8 independent FMA chains a thread, 8 blocks of 256 threads "
+                                    "per SM, CUDA events (of measured)"},
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,

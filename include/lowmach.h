@@ -294,6 +294,20 @@ int  lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* opts,
  * Clears the in-memory table. */
 int  lm_autotune_set_cache(const char* path);
 
+/* ---- measurement ---------------------------------------------------------- */
+
+/* Arithmetic-rate probe of the current device, the measured roof of the
+ * float64 kernels (the paper reports CPU timings only and has no
+ * counterpart).  which: 0 = float64 fused multiply-adds per second, 1 =
+ * float32 fused multiply-adds per second, 2 = float64 <-> float32
+ * conversions per second.  One launch of `steps` steps of 8 independent
+ * chains per thread, 8 blocks of 256 threads per SM, timed with CUDA events
+ * on `stream` after a short warm-up launch (steps = 20000 runs for tens of
+ * milliseconds in float64).  Allocates and frees 64 bytes of device memory;
+ * synchronises the stream.  LM_ERR_INVALID_ARG for a bad `which`, `steps`
+ * or pointer. */
+int  lm_probe_rate(int which, int steps, double* ops_per_s, void* stream);
+
 /* Allocation-free float64 apply: y = A x and *dot_out = x^T A x, like
  * lm_apply(LM_PREC_FP64) with dot_out, but with no grid object and no device
  * allocation at all.  The paper has no counterpart: this serves callers that

@@ -52,7 +52,10 @@ bool halvable(int n, int bc) {
     return true;
 }
 
-Lev32 make_lev(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho) {
+// A float32 level view; its rho array holds rho / rho_scale, so its face
+// factors 2/h^2 are divided by rho_scale too (exactly: a power of two).
+Lev32 make_lev(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho,
+               double rho_scale = 1.0) {
     Lev32 L{};
     L.g.nx = n[0];
     L.g.ny = n[1];
@@ -64,9 +67,9 @@ Lev32 make_lev(const int n[3], const int bc[3], const double h[3], const float* 
     L.g.ih2x = 1.0 / (h[0] * h[0]);
     L.g.ih2y = 1.0 / (h[1] * h[1]);
     L.g.ih2z = 1.0 / (h[2] * h[2]);
-    L.c2x = (float)(2.0 / (h[0] * h[0]));
-    L.c2y = (float)(2.0 / (h[1] * h[1]));
-    L.c2z = (float)(2.0 / (h[2] * h[2]));
+    L.c2x = (float)(2.0 / (h[0] * h[0]) / rho_scale);
+    L.c2y = (float)(2.0 / (h[1] * h[1]) / rho_scale);
+    L.c2z = (float)(2.0 / (h[2] * h[2]) / rho_scale);
     L.ct = ct;
     L.rho = rho;
     return L;
@@ -96,6 +99,7 @@ void free_mg(lm_grid* g) {
 }
 
 bool mg_supported(const lm_grid* g) {
+    if (!g->fp32_ok) return false;          // rho or c~ beyond what the float32 levels can hold
     for (int a = 0; a < 3; ++a)
         if (g->bc[a] == LM_BC_PERIODIC && g->n[a] > 1 && (g->n[a] % 2)) return false;
     return true;
@@ -130,7 +134,7 @@ int build_mg(lm_grid* g, cudaStream_t s, bool defer_inverse = false) {
     ++g->version;       // new buffers: cached batch plans of this grid are stale
     rbgs_row_allow_smem();
     MgLevel L0;
-    L0.L = make_lev(g->n, g->bc, g->h, g->ct32, g->rho32);
+    L0.L = make_lev(g->n, g->bc, g->h, g->ct32, g->rho32, g->rho_scale);
     std::memcpy(L0.h, g->h, sizeof L0.h);
     L0.xa = g->tmp_a;
     L0.xb = g->tmp_b;
@@ -157,7 +161,7 @@ int build_mg(lm_grid* g, cudaStream_t s, bool defer_inverse = false) {
         if ((rc = dalloc(&C.ct, Nc)) || (rc = dalloc(&C.rho, Nc)) || (rc = dalloc(&C.xa, Nc)) ||
             (rc = dalloc(&C.xb, Nc)) || (rc = dalloc(&C.xo, Nc)) || (rc = dalloc(&C.f, Nc)))
             return rc;
-        C.L = make_lev(nc, g->bc, C.h, C.ct, C.rho);
+        C.L = make_lev(nc, g->bc, C.h, C.ct, C.rho, g->rho_scale);
         launch_coarsen(F.L, C.L, hv[0], hv[1], hv[2], s, C.ct, C.rho);
         g->mg.push_back(C);
     }
@@ -543,18 +547,31 @@ int solve_mixed_ir(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res, boo
         return LM_OK;
     }
     double rel = g->st_host->rel;
+    const double fnorm = g->st_host->fnorm, sqN = std::sqrt((double)g->N);
+    // The inner right-hand side is r32 = r * rs, rs a power of two near
+    // 1/rms(r): the float32 inner solve is linear, and a right-hand side of
+    // about unit size keeps the products in its dot products clear of
+    // float32 underflow as the refinement drives r down.  The first residual
+    // is written unscaled and rescaled only when far from unit size; later
+    // ones are scaled as they are written, from the previous norm times the
+    // inner reduction.  The correction is scaled back exactly.
+    double rs = pow2_near_inv(rel * fnorm / sqN);
+    if (rs > 0x1p20 || rs < 0x1p-20) launch_scale32(g->N, g->G, s, g->r32, (float)rs);
+    else rs = 1.0;
     int outer = 0, iters = 0, vc = 0;
     int status = LM_OK;
     while (rel > o->rtol && outer < o->max_outer && iters < o->max_iter) {
         if ((rc = inner_fcg(g, o, s, &iters, &vc, &use_net))) return rc;
         if (g->st_host->status) status = g->st_host->status;
-        launch_ir_correct(g->N, g->G, s, g->x, g->e32);
-        launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, 0, g->st, 0, nullptr);
+        launch_ir_correct(g->N, g->G, s, g->x, g->e32, 1.0 / rs);
+        const double rs_next = pow2_near_inv(rel * fnorm * std::max(o->inner_rtol, 1e-12) / sqN);
+        launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, 0, g->st, 0, nullptr, rs_next);
         CK(cudaGetLastError());
         if ((rc = sync_state(g, g->st, s))) return rc;
         const double nrel = g->st_host->rel;
         g->history.push_back(nrel);
         ++outer;
+        rs = rs_next;
         if (!(nrel < rel) && status) break;       // inner breakdown and no progress
         rel = nrel;
         status = LM_OK;
@@ -593,18 +610,46 @@ int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double
         R = g->stage + g->N;
         C = raw ? nullptr : g->stage + 2 * (size_t)g->N;
     }
-    CK(cudaMemsetAsync(g->bad, 0, sizeof(int), s));
+    // flags: max 0, min all ones, no failures
+    CK(cudaMemsetAsync(g->asm_fl, 0, sizeof(AsmFlags), s));
+    CK(cudaMemsetAsync(&g->asm_fl->rho_min, 0xff, sizeof(unsigned long long), s));
     Op64Out dst{g->ct, g->gx, g->gy, g->gz, g->dinv, g->ct32, g->rho32};
-    launch_assemble(g->geo, g->G, s, A, R, C, dt, raw, g->h, dst, g->bad);
+    launch_assemble(g->geo, g->G, s, A, R, C, dt, raw, g->h, dst, g->asm_fl);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(g->bad_host, g->bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(g->asm_fl_host, g->asm_fl, sizeof(AsmFlags), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     g->mg_built = false;
     g->have_dinv = false;
-    if (*g->bad_host) {
+    const AsmFlags fl = *g->asm_fl_host;
+    if (fl.bad) {
         g->have_coefs = false;
         return LM_ERR_NOT_POSITIVE;
     }
+    // Range of the float32 copy of rho.  The whole-row sweep forms both faces
+    // of an axis from one reciprocal of the product (rho_c + rho_m)(rho_c +
+    // rho_p), with rho = 1e30 (about 2^99.7) past a wall: that stays a normal
+    // float32 while rho <= 2^26 and rho >= 2^-60.  Outside that band the copy
+    // is divided by a power of two centred on the geometric mean of the
+    // extremes (an exact scaling; the level face factors are divided by the
+    // same power); a range that no scaling fits (max/min >= 2^86), or a c~
+    // outside float32, leaves only the float64 Jacobi-PCG mode available.
+    double rmax = 0.0, rmin = 0.0;
+    std::memcpy(&rmax, &fl.rho_max, sizeof rmax);
+    std::memcpy(&rmin, &fl.rho_min, sizeof rmin);
+    constexpr double HI = 0x1p26, LO = 0x1p-60;
+    double scale = 1.0;
+    if (rmax > HI || rmin < LO) scale = std::ldexp(1.0, (int)std::lround(0.5 * (std::log2(rmax) + std::log2(rmin))));
+    g->fp32_ok = !fl.bad32 && rmax / scale <= HI && rmin / scale >= LO;
+    if (scale != 1.0 && g->fp32_ok) launch_scale32(g->N, g->G, s, g->rho32, (float)(1.0 / scale));
+    if (scale != g->rho_scale) {
+        // the level views carry the old face factors (and captured graphs and
+        // batch plans hold them): rebuild the hierarchy from scratch
+        free_mg(g);
+        lm::batch_forget_grid(g);
+        ++g->version;
+        g->rho_scale = scale;
+    }
+    CK(cudaGetLastError());
     g->have_coefs = true;
     return LM_OK;
 }
@@ -612,8 +657,9 @@ int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double
 }  // namespace
 
 int lm::grid_build_mg(lm_grid* g, cudaStream_t s, bool defer_inverse) { return build_mg(g, s, defer_inverse); }
-lm::Lev32 lm::make_level(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho) {
-    return make_lev(n, bc, h, ct, rho);
+lm::Lev32 lm::make_level(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho,
+                         double rho_scale) {
+    return make_lev(n, bc, h, ct, rho, rho_scale);
 }
 
 // ============================ C ABI =========================================
@@ -700,9 +746,9 @@ int lm_grid_create(int ndim, const int64_t n[3], const double h[3], const int bc
     if (cudaMemset(g->ctr, 0, sizeof(unsigned int)) != cudaSuccess) return fail(LM_ERR_CUDA);
     if ((rc = dalloc(&g->st, 1))) return fail(rc);
     if ((rc = dalloc(&g->st_in, 1))) return fail(rc);
-    if ((rc = dalloc(&g->bad, 1))) return fail(rc);
+    if ((rc = dalloc(&g->asm_fl, 1))) return fail(rc);
     if (cudaMallocHost((void**)&g->st_host, sizeof(SolveState)) != cudaSuccess) return fail(LM_ERR_OUT_OF_MEMORY);
-    if (cudaMallocHost((void**)&g->bad_host, sizeof(int)) != cudaSuccess) return fail(LM_ERR_OUT_OF_MEMORY);
+    if (cudaMallocHost((void**)&g->asm_fl_host, sizeof(AsmFlags)) != cudaSuccess) return fail(LM_ERR_OUT_OF_MEMORY);
     if (cudaMallocHost((void**)&g->dscal_host, 8 * sizeof(double)) != cudaSuccess) return fail(LM_ERR_OUT_OF_MEMORY);
     if (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess) return fail(LM_ERR_CUDA);
     if (cudaMemset(g->part, 0, sizeof(double) * NSLOT * MAX_PARTIALS) != cudaSuccess) return fail(LM_ERR_CUDA);
@@ -721,10 +767,10 @@ void lm_grid_destroy(lm_grid* g) {
     void* bufs[] = {g->ct, g->gx, g->gy, g->gz, g->dinv, g->f, g->x, g->x0, g->r, g->p, g->q,
                     g->ct32, g->rho32, g->r32, g->e32, g->z32, g->p32, g->q32, g->tmp_a, g->tmp_b,
                     g->scal, g->ctr, g->stage, g->part,
-                    g->dscal, g->st, g->st_in, g->hist_dev, g->bad};
+                    g->dscal, g->st, g->st_in, g->hist_dev, g->asm_fl};
     for (void* b : bufs) cudaFree(b);
     cudaFreeHost(g->st_host);
-    cudaFreeHost(g->bad_host);
+    cudaFreeHost(g->asm_fl_host);
     cudaFreeHost(g->dscal_host);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
@@ -844,7 +890,8 @@ int lm_apply(lm_grid* g, int prec, const void* x, void* y, double* dot_out, void
         launch_apply64(g->geo, g->G, s, op64(g), (const double*)x, (double*)y, dot_out ? g->part : nullptr);
         if (dot_out) launch_reduce_slot(g->part, 0, g->G, s, g->dscal);
     } else {
-        Lev32 L = make_lev(g->n, g->bc, g->h, g->ct32, g->rho32);
+        if (!g->fp32_ok) return LM_ERR_INVALID_ARG;
+        Lev32 L = make_lev(g->n, g->bc, g->h, g->ct32, g->rho32, g->rho_scale);
         const Red red{g->part, g->scal, g->ctr};
         launch_apply32(L, s, (const float*)x, (float*)y, nullptr, red, dot_out ? 0 : -1, -1);
         dot_dev = g->scal;

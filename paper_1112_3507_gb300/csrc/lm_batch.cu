@@ -696,6 +696,7 @@ int lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* o, lm_
         std::memset(&results[i], 0, sizeof(lm_solve_result));
         if (!g->have_coefs || !g->have_rhs) return LM_ERR_STATE;
         if (g->ndim != 2 || g->n[1] != 1) return LM_ERR_INVALID_ARG;       // the batch path is 2D
+        if (!g->fp32_ok) return LM_ERR_INVALID_ARG;                         // no float32 operator
         for (int a = 0; a < 3; ++a)
             if (g->bc[a] == LM_BC_PERIODIC && g->n[a] > 1 && (g->n[a] % 2)) return LM_ERR_INVALID_ARG;
         if (o->use_x0 && !g->have_x0) return LM_ERR_STATE;

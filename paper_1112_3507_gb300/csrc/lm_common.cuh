@@ -69,6 +69,33 @@ __device__ __forceinline__ bool face_plus(int c, int n, int bc) {
     return n > 1 && (c < n - 1 || bc == LM_BC_PERIODIC);
 }
 
+// ---- L2 prefetch ---------------------------------------------------------------
+
+// Planes ahead of their first use that the whole-row z-march kernels ask the
+// copy engine to bring into L2 (see prefetch_l2).
+#ifndef LM_PF_PLANES
+#define LM_PF_PLANES 1
+#endif
+constexpr int PF_PLANES = LM_PF_PLANES;
+
+// One bulk asynchronous prefetch of `bytes` (a multiple of 16) of global
+// memory into L2 (PTX cp.async.bulk.prefetch.L2, sm_90 and later): it holds
+// no register or shared memory, so a z-march can run it several planes ahead
+// of its staged loads, which then hit L2 instead of waiting on HBM.  Skipped
+// when the address is not 16-byte aligned, which the instruction requires.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    if (((uintptr_t)p & 15) == 0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The power of two nearest 1/v for v > 0 finite (1 otherwise), clamped to
+// 2^-100 .. 2^100: an exact scaling factor.
+__host__ __device__ __forceinline__ double pow2_near_inv(double v) {
+    if (!(v > 0.0) || !(v < 1e300)) return 1.0;
+    int e = -(int)rint(log2(v));
+    e = e < -100 ? -100 : (e > 100 ? 100 : e);
+    return ldexp(1.0, e);
+}
+
 // ---- reductions ------------------------------------------------------------
 
 __device__ __forceinline__ int lin_tid() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }

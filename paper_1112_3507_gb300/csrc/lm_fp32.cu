@@ -277,6 +277,17 @@ __global__ void __launch_bounds__(32 * TY, 1) k_apply32_row(Lev32 L, const float
     };
     const int lrel = (lane == 0 && perx) ? NX - 1 : -1;         // left of cell 0, right of cell nx - 1
     const int rrel = (lane == 31 && perx) ? 1 - NX : 1;
+    // L2 prefetch of the block's own rows, PF_PLANES steps ahead: x and rho of
+    // plane P are staged at step P - 2, c~ and r read at step P - 1; array
+    // a = 0..3 (x, rho, c~, r) is requested by thread a.
+    auto prefetch = [&](int a, int P) {
+        int pw = 0;
+        if (P > (a < 2 ? k1 : k1 - 1) || (!DOT_XR && a == 3) || !plane(P, pw)) return;
+        const float* base = a == 0 ? x : a == 1 ? L.rho : a == 2 ? L.ct : r;
+        prefetch_l2(base + sz * pw + NX * j0, NX * TY * sizeof(float));
+    };
+    if (tid < 4)
+        for (int d = 1; d <= PF_PLANES; ++d) prefetch(tid, (tid < 2 ? k0 + 1 : k0) + d);
     FF axy{0.f, 0.f}, axr{0.f, 0.f};
     int sm1 = 0, s0 = 1, sp1 = 2, sp2 = 3;                // slots of planes p - 1 .. p + 2
     fetch(k0 - 1);
@@ -289,6 +300,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_apply32_row(Lev32 L, const float
     __syncthreads();
     for (int p = k0; p < k1; ++p) {
         const bool stage = p + 2 <= k1;
+        if (tid < 4) prefetch(tid, (tid < 2 ? p + 2 : p + 1) + PF_PLANES);
         if (stage) fetch(p + 2);
         const int b0 = (s0 * NRW + rT) * RS + 2 + lane, dzm = (sm1 - s0) * PL, dzp = (sp1 - s0) * PL;
         float* yrow = y + sz * p + NX * jT + lane;
@@ -829,7 +841,8 @@ __global__ void __launch_bounds__(256) k_rbgs_zm(Lev32 L, const float* __restric
 
 // rho of the cells past a wall: large but finite, so that a face weight
 // c2 / (rho_c + ROW_WALL) is negligible (x there is 0) and the product of an
-// axis's two face sums stays finite
+// axis's two face sums stays finite (for rho within [2^-60, 2^26], the band
+// the assembly keeps the float32 copy of rho in)
 constexpr float ROW_WALL = 1e30f;
 
 // Ring index of even cell m (run E) and odd cell m (run O) of a staged row
@@ -1007,6 +1020,18 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
     };
     auto parity = [&](int j, int p, int col) -> int { return (col + j + p) & 1; };   // updated cell of each pair
     const int jTu = j0 + wy, jFu = (wy & 1) ? j0 + TY : j0 - 1;   // unwrapped rows (even periodic sizes)
+    // L2 prefetch of the block's own TY rows (contiguous: one bulk request per
+    // array and plane), PF_PLANES steps before their first use: x and rho of
+    // plane P are staged at step P - 2, f and c~ first read at step P - 1.
+    // Array a = 0..3 (x, rho, f, c~) is requested by thread a.
+    auto prefetch = [&](int a, int P) {
+        int pw = 0;
+        if (P > (a < 2 ? k1 + 1 : k1) || (ZERO && a == 0) || !plane(P, pw)) return;
+        const float* base = a == 0 ? xin : a == 1 ? L.rho : a == 2 ? f : L.ct;
+        prefetch_l2(base + sz * pw + NX * j0, NX * TY * sizeof(float));
+    };
+    if (tid < 4)
+        for (int d = 1; d <= PF_PLANES; ++d) prefetch(tid, (tid < 2 ? k0 : k0 - 1) + d);
     auto gs_row = [&](int a, int b, int dzm, int dzp, const float* F, const float* Cv) {
         if (a) gs_row_runs<CPT, 1>(XR, b, lane, perx, RS, dzm, dzp, F, Cv, L.c2x, L.c2y, L.c2z);
         else gs_row_runs<CPT, 0>(XR, b, lane, perx, RS, dzm, dzp, F, Cv, L.c2x, L.c2y, L.c2z);
@@ -1031,6 +1056,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
     __syncthreads();
     for (int p = k0 - 1; p <= k1 + 2; ++p) {
         const bool stage = p + 2 <= k1 + 1;
+        if (tid < 4) prefetch(tid, (tid < 2 ? p + 2 : p + 1) + PF_PLANES);
         if (stage) fetch(p + 2);
         int pw = 0;
         if (p <= k1 && plane(p, pw)) {                    // first colour on plane p
@@ -1312,6 +1338,15 @@ __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo 
     };
     const int lrel = (lane == 0 && perx) ? NX - 1 : -1;
     const int rrel = (lane == 31 && perx) ? 1 - NX : 1;
+    // L2 prefetch as in k_apply32_row; arrays x, rho, c~, f
+    auto prefetch = [&](int a, int P) {
+        int pw = 0;
+        if (P > (a < 2 ? k1 : k1 - 1) || !plane(P, pw)) return;
+        const float* base = a == 0 ? x : a == 1 ? L.rho : a == 2 ? L.ct : f;
+        prefetch_l2(base + sz * pw + NX * j0, NX * TY * sizeof(float));
+    };
+    if (tid < 4)
+        for (int d = 1; d <= PF_PLANES; ++d) prefetch(tid, (tid < 2 ? k0 + 1 : k0) + d);
     int sm1 = 0, s0 = 1, sp1 = 2, sp2 = 3;
     // an even row's pair sums wait one step (one barrier) for the odd row's
     float accP[CPT];
@@ -1333,6 +1368,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo 
     };
     for (int p = k0; p < k1; ++p) {
         const bool stage = p + 2 <= k1;
+        if (tid < 4) prefetch(tid, (tid < 2 ? p + 2 : p + 1) + PF_PLANES);
         if (stage) fetch(p + 2);
         finish_pairs();
         const int b0 = (s0 * NRW + rT) * RS + 2 + lane, dzm = (sm1 - s0) * PL, dzp = (sp1 - s0) * PL;
@@ -1555,6 +1591,7 @@ void rbgs_row_allow_smem() {
 }
 
 static bool aligned8(const void* p) { return ((uintptr_t)p & 7) == 0; }
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 template <int CPT>
 static void launch_rbgs_row(const Lev32& L, cudaStream_t s, const float* xin, const float* ec, const Geo& Cg,

@@ -19,8 +19,10 @@ __global__ void __launch_bounds__(NT) k_assemble(Geo g, const double* __restrict
                                                  const double* __restrict__ rho_new,
                                                  const double* __restrict__ cs2, double dt, int raw,
                                                  double c2x, double c2y, double c2z, Op64Out out,
-                                                 int* __restrict__ bad) {
+                                                 AsmFlags* __restrict__ fl) {
     const int stride = gridDim.x * blockDim.x;
+    unsigned long long rmax = 0ull, rmin = ~0ull;        // range of the valid rho^{n+1}
+    bool bad32 = false;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
         const double rn = rho_new[idx];
         double c;
@@ -33,7 +35,12 @@ __global__ void __launch_bounds__(NT) k_assemble(Geo g, const double* __restrict
             c = __drcp_rn((dt * dt) * ro * c2);                // Eq. cpoiss: 1/(...) rounded to nearest
         }
         ok = ok && c > 0.0 && isfinite(c);
-        if (!ok) atomicOr(bad, 1);
+        if (!ok) atomicOr(&fl->bad, 1);
+        if (rn > 0.0 && isfinite(rn)) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(rn);
+            rmax = b > rmax ? b : rmax;
+            rmin = b < rmin ? b : rmin;
+        }
         int i, j, k;
         cell_coords(idx, g, i, j, k);
         // g_f = kappa_f / h^2 with kappa_f = 2/(rho_L + rho_R) (Eq. kappapoiss, harmonic
@@ -48,9 +55,27 @@ __global__ void __launch_bounds__(NT) k_assemble(Geo g, const double* __restrict
         out.gx[idx] = gxm;
         out.gy[idx] = gym;
         out.gz[idx] = gzm;
-        out.ct32[idx] = (float)c;
+        const float c32 = (float)c;
+        bad32 = bad32 || !(c32 > 0.f) || isinf(c32);
+        out.ct32[idx] = c32;
         out.rho32[idx] = (float)rn;
     }
+    // the block's range and float32 flag: one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, rmax, o), b = __shfl_xor_sync(0xffffffffu, rmin, o);
+        rmax = a > rmax ? a : rmax;
+        rmin = b < rmin ? b : rmin;
+    }
+    bad32 = __any_sync(0xffffffffu, bad32);
+    if ((threadIdx.x & 31) == 0) {
+        if (rmax) atomicMax(&fl->rho_max, rmax);
+        if (rmin != ~0ull) atomicMin(&fl->rho_min, rmin);
+        if (bad32) atomicOr(&fl->bad32, 1);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_scale32(int N, float* __restrict__ x, float scale) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) x[i] *= scale;
 }
 
 // Inverse Jacobi diagonal 1/(c~ + sum of the cell's face conductances), from
@@ -247,27 +272,31 @@ __global__ void __launch_bounds__(NT) k_finish_rel(double* part, int G, SolveSta
 
 // ---- iterative refinement (float64 residual and correction) ---------------
 
-// r = f - A x in float64, stored as float32 for the inner solve; partial
-// r.r (slot 1) and f.f (slot 4).  zero_x: x := 0 first (r = f).
+// r = f - A x in float64, stored as float32 times rscale (a power of two
+// that keeps the inner problem's float32 values near unit size, so that the
+// products of its dot products neither underflow nor overflow) for the
+// inner solve; partial r.r (slot 1) and, with FNORM, f.f (slot 4).
+// zero_x: x := 0 first (r = f).
+template <bool FNORM>
 __global__ void __launch_bounds__(NT) k_ir_residual(Geo g, Op64 op, const double* __restrict__ f,
                                                     double* __restrict__ x, float* __restrict__ r32,
-                                                    double* __restrict__ part, int zero_x) {
+                                                    double* __restrict__ part, int zero_x, double rscale) {
     __shared__ double sm[64];
     double acc[2] = {0.0, 0.0};
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
         const double fi = f[idx];
         const double ri = zero_x ? fi : fi - apply64_at(idx, g, op, x);
-        r32[idx] = (float)ri;
+        r32[idx] = (float)(ri * rscale);
         acc[0] += ri * ri;
-        acc[1] += fi * fi;
+        if (FNORM) acc[1] += fi * fi;
     }
     if (zero_x)
         for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) x[idx] = 0.0;
     block_sum<2>(acc, sm);
     if (threadIdx.x == 0) {
         part[1 * MAX_PARTIALS + blockIdx.x] = acc[0];
-        part[4 * MAX_PARTIALS + blockIdx.x] = acc[1];
+        if (FNORM) part[4 * MAX_PARTIALS + blockIdx.x] = acc[1];
     }
 }
 
@@ -301,10 +330,13 @@ __global__ void __launch_bounds__(NT) k_warm_scale(int N, double* __restrict__ x
         x[idx] = alpha > 0.0 ? alpha * x[idx] : 0.0;
 }
 
-// x += e (float32 correction accumulated in float64)
-__global__ void __launch_bounds__(NT) k_ir_correct(int N, double* __restrict__ x, const float* __restrict__ e) {
+// x += e * escale (float32 correction accumulated in float64; escale undoes
+// the power-of-two scaling of the inner right-hand side, exactly)
+__global__ void __launch_bounds__(NT) k_ir_correct(int N, double* __restrict__ x, const float* __restrict__ e,
+                                                   double escale) {
     const int stride = gridDim.x * blockDim.x;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride) x[idx] += (double)e[idx];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride)
+        x[idx] += (double)e[idx] * escale;
 }
 
 
@@ -384,13 +416,18 @@ __global__ void __launch_bounds__(NT) k_fcg64_update(int N, double* __restrict__
         return;
     }
     const double alpha = pr / pq;
+    // the preconditioner's input in float32, scaled by a power of two near
+    // 1/rms of the previous residual: flexible CG is invariant under a
+    // positive scaling of z, and the scaling keeps the float32 V-cycle's
+    // values away from underflow as the residual shrinks
+    const double rs = pow2_near_inv(st->rel * st->fnorm * rsqrt((double)N));
     double acc[1] = {0.0};
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride) {
         x[idx] += alpha * p[idx];
         const double ri = r[idx] - alpha * q[idx];
         r[idx] = ri;
-        r32[idx] = (float)ri;
+        r32[idx] = (float)(ri * rs);
         acc[0] += ri * ri;
     }
     write_partials<1>(acc, part + 1 * MAX_PARTIALS, sm);
@@ -416,10 +453,14 @@ __global__ void __launch_bounds__(NT) k_set_fnorm(const double* part, int slot, 
 // ---- host launchers ---------------------------------------------------------
 
 void launch_assemble(const Geo& g, int G, cudaStream_t s, const double* a_in, const double* rho_new,
-                     const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, int* bad) {
+                     const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, AsmFlags* fl) {
     count_launches(1);
     k_assemble<<<G, NT, 0, s>>>(g, a_in, rho_new, cs2, dt, raw, 2.0 / (h[0] * h[0]), 2.0 / (h[1] * h[1]),
-                                2.0 / (h[2] * h[2]), out, bad);
+                                2.0 / (h[2] * h[2]), out, fl);
+}
+void launch_scale32(int N, int G, cudaStream_t s, float* x, float scale) {
+    count_launches(1);
+    k_scale32<<<G, NT, 0, s>>>(N, x, scale);
 }
 void launch_jacobi_diag(const Geo& g, int G, cudaStream_t s, const Op64& op, double* dinv) {
     count_launches(1);
@@ -455,9 +496,11 @@ void launch_true_residual(const PcgArgs& a, int G, cudaStream_t s) {
     k_finish_rel<<<1, NT, 0, s>>>(a.part, G, a.st, 0, nullptr);
 }
 void launch_ir_residual(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* f, double* x,
-                        float* r32, double* part, int zero_x, SolveState* st, int set_fnorm, double* hist_entry) {
+                        float* r32, double* part, int zero_x, SolveState* st, int set_fnorm, double* hist_entry,
+                        double rscale) {
     count_launches(1);
-    k_ir_residual<<<G, NT, 0, s>>>(g, op, f, x, r32, part, zero_x);
+    if (set_fnorm) k_ir_residual<true><<<G, NT, 0, s>>>(g, op, f, x, r32, part, zero_x, rscale);
+    else k_ir_residual<false><<<G, NT, 0, s>>>(g, op, f, x, r32, part, zero_x, rscale);
     count_launches(1);
     k_finish_rel<<<1, NT, 0, s>>>(part, G, st, set_fnorm, hist_entry);
 }
@@ -467,9 +510,9 @@ void launch_warm_scale(const Geo& g, int G, cudaStream_t s, const Op64& op, cons
     k_warm_dots<<<G, NT, 0, s>>>(g, op, f, x, part);
     k_warm_scale<<<G, NT, 0, s>>>(g.N, x, part, G);
 }
-void launch_ir_correct(int N, int G, cudaStream_t s, double* x, const float* e) {
+void launch_ir_correct(int N, int G, cudaStream_t s, double* x, const float* e, double escale) {
     count_launches(1);
-    k_ir_correct<<<G, NT, 0, s>>>(N, x, e);
+    k_ir_correct<<<G, NT, 0, s>>>(N, x, e, escale);
 }
 void launch_reduce_rel(double* part, int G, cudaStream_t s, SolveState* st, double* hist_entry) {
     count_launches(1);

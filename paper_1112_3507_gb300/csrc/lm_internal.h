@@ -60,8 +60,14 @@ struct lm_grid {
     SolveState* st_host = nullptr;  // pinned mirror
     double* hist_dev = nullptr;
     int hist_cap = 0;
-    int* bad = nullptr;
-    int* bad_host = nullptr;
+    lm::AsmFlags* asm_fl = nullptr;         // assembly report (device) and its pinned mirror
+    lm::AsmFlags* asm_fl_host = nullptr;
+    // The float32 copy of rho^{n+1} holds rho / rho_scale (a power of two,
+    // 1 unless rho leaves the band the float32 face formulas are safe in);
+    // the float32 levels carry 2 / (h^2 rho_scale) so their faces are
+    // unchanged.  fp32_ok: the float32 operator is representable at all.
+    double rho_scale = 1.0;
+    bool fp32_ok = true;
     double* dscal_host = nullptr;
 
     bool have_coefs = false, have_rhs = false, have_x0 = false;
@@ -100,5 +106,6 @@ int net_set_params(lm_net* N, const float* host, int n);
 bool net_usable(const lm_grid* g);
 template <typename TV, typename TO>
 int net_apply(lm_grid* g, const TV* v, TO* dst, cudaStream_t s);
-Lev32 make_level(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho);
+Lev32 make_level(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho,
+                 double rho_scale = 1.0);
 }  // namespace lm

@@ -51,9 +51,21 @@ struct Lev32 {
     const float* rho;
 };
 
+// What the assembly reports besides the coefficients: the range of rho^{n+1}
+// (float64 bit patterns, monotone in the value for positive numbers), a
+// positivity/finiteness failure, and a c~ outside float32 range.
+struct AsmFlags {
+    unsigned long long rho_max;
+    unsigned long long rho_min;
+    int bad;        // rho, c_s^2, dt or c~ not strictly positive and finite
+    int bad32;      // c~ overflows or underflows float32
+};
+
 // fp64
 void launch_assemble(const Geo& g, int G, cudaStream_t s, const double* a_in, const double* rho_new,
-                     const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, int* bad);
+                     const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, AsmFlags* fl);
+// x *= scale (float32; scale a power of two, so the scaling is exact)
+void launch_scale32(int N, int G, cudaStream_t s, float* x, float scale);
 void launch_jacobi_diag(const Geo& g, int G, cudaStream_t s, const Op64& op, double* dinv);
 void launch_apply64(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* x, double* y,
                     double* part);
@@ -62,10 +74,11 @@ void launch_pcg_restart(const PcgArgs& a, int G, cudaStream_t s, int k);
 void launch_pcg_iter(const PcgArgs& a, int G, cudaStream_t s, int k);
 void launch_true_residual(const PcgArgs& a, int G, cudaStream_t s);
 void launch_ir_residual(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* f, double* x,
-                        float* r32, double* part, int zero_x, SolveState* st, int set_fnorm, double* hist_entry);
+                        float* r32, double* part, int zero_x, SolveState* st, int set_fnorm, double* hist_entry,
+                        double rscale = 1.0);
 void launch_warm_scale(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* f, double* x,
                        double* part);
-void launch_ir_correct(int N, int G, cudaStream_t s, double* x, const float* e);
+void launch_ir_correct(int N, int G, cudaStream_t s, double* x, const float* e, double escale = 1.0);
 void launch_reduce_rel(double* part, int G, cudaStream_t s, SolveState* st, double* hist_entry);
 void launch_reduce_slot(const double* part, int slot, int G, cudaStream_t s, double* out);
 void launch_fcg64_iter_a(int N, int G, cudaStream_t s, const float* z, const double* q, double* part, int first,

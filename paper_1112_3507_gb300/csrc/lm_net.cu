@@ -766,7 +766,7 @@ namespace lm {
 
 template <typename TV>
 __global__ void __launch_bounds__(NT) k_feat_sums(int N, const TV* __restrict__ v, const float* __restrict__ rho,
-                                                  const float* __restrict__ ct, Red red) {
+                                                  const float* __restrict__ ct, double irs, Red red) {
     __shared__ double sm[4 * 32];
     double a[4] = {0.0, 0.0, 0.0, 0.0};
     for (int i = blockIdx.x * NT + threadIdx.x; i < N; i += gridDim.x * NT) {
@@ -781,7 +781,8 @@ __global__ void __launch_bounds__(NT) k_feat_sums(int N, const TV* __restrict__ 
         const double rms = sqrt(red.scal[8] / N);
         red.scal[12] = rms > 0.0 ? 1.0 / rms : 0.0;                                 // 1 / rms
         red.scal[13] = red.scal[9] / N;                                            // mean rho
-        red.scal[14] = rms / (red.scal[10] / N + (red.scal[11] / N) * 9.869604401089358);  // scale s
+        // rho holds rho / rho_scale: mean(1/rho) = mean(1/rho_stored) / rho_scale
+        red.scal[14] = rms / (red.scal[10] / N + (red.scal[11] / N) * irs * 9.869604401089358);  // scale s
     }
 }
 
@@ -812,9 +813,10 @@ template <typename TV>
 int features(lm_grid* g, const TV* v, float* feat, cudaStream_t s) {
     const Red red{g->part, g->scal, g->ctr};
     count_launches(2);
-    k_feat_sums<TV><<<g->G, NT, 0, s>>>(g->N, v, g->rho32, g->ct32, red);
+    k_feat_sums<TV><<<g->G, NT, 0, s>>>(g->N, v, g->rho32, g->ct32, 1.0 / g->rho_scale, red);
+    // channel 2 is log(1/(c~ rho h^2)) of the true rho = rho_stored * rho_scale
     k_feat<TV><<<blocks_for(g->N), 256, 0, s>>>(g->N, v, g->rho32, g->ct32, g->scal,
-                                                (float)(1.0 / (g->h[2] * g->h[2])), feat);
+                                                (float)(1.0 / (g->h[2] * g->h[2]) / g->rho_scale), feat);
     return cudaGetLastError() == cudaSuccess ? LM_OK : LM_ERR_CUDA;
 }
 

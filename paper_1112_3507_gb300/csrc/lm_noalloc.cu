@@ -30,6 +30,7 @@
 #include "../../include/lowmach.h"
 #include "lm_common.cuh"
 #include "lm_kernels.h"
+#include "lm_tiles.cuh"
 
 constexpr int LM_NOALLOC_ITEMS = 16;                                        // cells per thread
 constexpr int LM_NOALLOC_CELLS_PER_BLOCK = lm::NT * LM_NOALLOC_ITEMS;       // 4096
@@ -65,29 +66,6 @@ int partials_address(double** out) {
     return LM_OK;
 }
 
-// (A x)_i = c~_i x_i + sum over faces g_f (x_i - x_nb); faces as stored by the
-// assembly: each cell's minus-face conductance per axis, 0 on walls.
-__device__ __forceinline__ double noalloc_apply_at(int idx, const lm::Geo& g, const double* __restrict__ ct,
-                                                   const double* __restrict__ gx, const double* __restrict__ gy,
-                                                   const double* __restrict__ gz, const double* __restrict__ x) {
-    int i, j, k;
-    lm::cell_coords(idx, g, i, j, k);
-    const double xc = x[idx];
-    double y = ct[idx] * xc;
-    lm::Nbr n = lm::nbr_x(idx, i, g);
-    y += gx[idx] * (xc - x[n.im]);
-    y += gx[n.ip] * (xc - x[n.ip]);
-    if (g.ny > 1) {
-        n = lm::nbr_y(idx, j, g);
-        y += gy[idx] * (xc - x[n.im]);
-        y += gy[n.ip] * (xc - x[n.ip]);
-    }
-    n = lm::nbr_z(idx, k, g);
-    y += gz[idx] * (xc - x[n.im]);
-    y += gz[n.ip] * (xc - x[n.ip]);
-    return y;
-}
-
 // Block b applies A to its LM_NOALLOC_CELLS_PER_BLOCK cells and writes its
 // partial sum of x_i (A x)_i to partials[b].
 __global__ void __launch_bounds__(lm::NT) k_apply_dot_noalloc(lm::Geo g, const double* __restrict__ ct,
@@ -102,7 +80,8 @@ __global__ void __launch_bounds__(lm::NT) k_apply_dot_noalloc(lm::Geo g, const d
     for (int s = 0; s < LM_NOALLOC_ITEMS; ++s) {
         const int idx = base + s * lm::NT + threadIdx.x;
         if (idx < g.N) {
-            const double v = noalloc_apply_at(idx, g, ct, gx, gy, gz, x);
+            // the grid-based apply's stencil on the caller's coefficients
+            const double v = lm::apply64_at(idx, g, lm::Op64{ct, gx, gy, gz, nullptr}, x);
             y[idx] = v;
             acc[0] += x[idx] * v;
         }

@@ -98,6 +98,7 @@ _SIGNATURES = {
     "lm_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(SolveOpts),
                                        ctypes.POINTER(SolveResult)]),
     "lm_autotune_set_cache": (ctypes.c_int, [ctypes.c_char_p]),
+    "lm_probe_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "lm_apply_dot_noalloc": (ctypes.c_int, [ctypes.c_int, _I64_3, _I3, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
@@ -437,3 +438,11 @@ def apply_dot_noalloc(ndim, n, bc, ctilde, gx, gy, gz, x, y, dot_out, stream=Non
         ptrs.append(ptr)
     return _check(lib().lm_apply_dot_noalloc(int(ndim), _I64_3(*n), _I3(*bc), *ptrs, _stream_ptr(stream)),
                   "lm_apply_dot_noalloc")
+
+
+def probe_rate(which: int, steps: int = 20000, stream=None) -> float:
+    """lm_probe_rate: measured operations per second of the current device
+    (0 = float64 FMA, 1 = float32 FMA, 2 = float64 <-> float32 conversions)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().lm_probe_rate(int(which), int(steps), ctypes.byref(out), _stream_ptr(stream)), "lm_probe_rate")
+    return out.value

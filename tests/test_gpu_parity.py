@@ -108,7 +108,14 @@ def test_apply_fp64_and_dot(name):
         xd, yd = _dev(x), torch.empty(p.size, dtype=torch.float64, device="cuda")
         dot = g.apply(xd, yd, prec=lm().PREC_FP64, with_dot=True)
         y = yd.cpu().numpy()
-    assert np.linalg.norm(y - y_ref) <= 1e-14 * np.linalg.norm(y_ref)
+    # per element, against the magnitude of the row's terms (the scale of
+    # the rounding error of any summation order of those terms)
+    xs = x.reshape(op.shape)
+    mag = np.abs(op.ct * xs)
+    for a in range(3):
+        mag = mag + op.g_minus[a] * np.abs(xs - np.roll(xs, 1, axis=2 - a))
+        mag = mag + op.g_plus(a) * np.abs(xs - np.roll(xs, -1, axis=2 - a))
+    assert np.all(np.abs(y - y_ref) <= 1e-14 * mag.ravel())
     assert dot == pytest.approx(float(np.vdot(x, y_ref)), rel=1e-12)
 
 

@@ -66,6 +66,12 @@ def test_reference_arm_does_no_work_off_rank_0(monkeypatch, capsys):
     assert capsys.readouterr().out == ""
 
 
+def bench_host_cores():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench.host_cores()
+
+
 def test_reference_arm_prints_the_contract_line():
     """bench.py --impl reference times the CPU oracle and prints one JSON line
     with the GPU arm's metric and unit (run on the smallest workload)."""
@@ -77,5 +83,6 @@ def test_reference_arm_prints_the_contract_line():
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "GDOF/s" and line["value"] > 0
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["cores"] == line["cpu_baseline"]["host_cores"] == bench_host_cores()
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["steps"] == 2

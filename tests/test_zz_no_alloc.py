@@ -27,28 +27,54 @@ def lm():
     return lowmach
 
 
-@pytest.mark.parametrize("make", [lambda: I.config_convection_3d(24, seed=11),
-                                  lambda: I.config_plain_2d(64, seed=12)])
-def test_noalloc_apply_matches_grid_apply(lm, make):
-    p = make()
-    g = lm.Grid.for_problem(p)
-    try:
-        g.set_problem(p)
-        ct, gx, gy, gz = g.coefficients()
-        rng = np.random.default_rng(13)
-        for call in range(2):                       # two calls in a row, different inputs
-            x = torch.as_tensor(rng.standard_normal(p.size), device="cuda")
-            y_ref = torch.empty_like(x)
-            dot_ref = g.apply(x, y_ref, prec=lm.PREC_FP64, with_dot=True)
-            y = torch.full_like(x, np.nan)
-            dot = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
-            lm.apply_dot_noalloc(p.ndim, p.n, p.bc, ct, gx, gy, gz, x, y, dot)
-            torch.cuda.synchronize()
-            y_ref_h, y_h = y_ref.cpu().numpy(), y.cpu().numpy()
-            assert np.linalg.norm(y_h - y_ref_h) <= 1e-14 * np.linalg.norm(y_ref_h), call
-            assert float(dot.item()) == pytest.approx(dot_ref, rel=1e-12), call
-    finally:
-        g.close()
+def _stencil_magnitude(op, x):
+    """sum over the terms of (A x)_i of their magnitudes: |c~_i x_i| + sum_f g_f |x_i - x_nb|,
+    the scale of the rounding error of any evaluation order of row i."""
+    x = x.reshape(op.shape)
+    m = np.abs(op.ct * x)
+    for a in range(3):
+        ax = 2 - a
+        m = m + op.g_minus[a] * np.abs(x - np.roll(x, 1, axis=ax))
+        m = m + op.g_plus(a) * np.abs(x - np.roll(x, -1, axis=ax))
+    return m.ravel()
+
+
+def test_noalloc_apply_matches_grid_apply_and_oracle(lm):
+    """Two grids in a row, the larger first: the scratch keeps the partials
+    of the 24^3 call when the 64 x 64 call runs, and that call must read
+    only its own.  Each grid gets two calls, the second on a non-default
+    stream; y and x^T A x are compared with the grid-based lm_apply and with
+    the oracle's operator, element by element."""
+    from oracle import poisson as P
+    side = torch.cuda.Stream()
+    for p in (I.config_convection_3d(24, seed=11), I.config_plain_2d(64, seed=12)):
+        op = P.operator_from_problem(p)
+        g = lm.Grid.for_problem(p)
+        try:
+            g.set_problem(p)
+            ct, gx, gy, gz = g.coefficients()
+            rng = np.random.default_rng(13)
+            for call, stream in enumerate((None, side)):   # two calls in a row, different inputs
+                xh = rng.standard_normal(p.size)
+                x = torch.as_tensor(xh, device="cuda")
+                y_ref = torch.empty_like(x)
+                dot_ref = g.apply(x, y_ref, prec=lm.PREC_FP64, with_dot=True)
+                y = torch.full_like(x, np.nan)
+                dot = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
+                torch.cuda.synchronize()
+                lm.apply_dot_noalloc(p.ndim, p.n, p.bc, ct, gx, gy, gz, x, y, dot,
+                                     stream=stream.cuda_stream if stream is not None else None)
+                torch.cuda.synchronize()
+                y_h = y.cpu().numpy()
+                # same stencil code as lm_apply: identical values
+                np.testing.assert_array_equal(y_h, y_ref.cpu().numpy())
+                assert float(dot.item()) == pytest.approx(dot_ref, rel=1e-12), call
+                # against the oracle's operator, per element
+                y_or = op.apply(xh).ravel()
+                assert np.all(np.abs(y_h - y_or) <= 1e-14 * _stencil_magnitude(op, xh)), call
+                assert float(dot.item()) == pytest.approx(float(np.vdot(xh, y_or)), rel=1e-12), call
+        finally:
+            g.close()
 
 
 def test_noalloc_rejects_grids_beyond_the_scratch(lm):
