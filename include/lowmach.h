@@ -294,6 +294,60 @@ int  lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* opts,
  * Clears the in-memory table. */
 int  lm_autotune_set_cache(const char* path);
 
+/* ---- building blocks of a z-slab decomposed solve ------------------------- */
+/* The paper runs its pressure solve domain-decomposed on a CPU cluster
+ * (Sec. 2.5, the parallel solver and its strong-scaling table); here a rank
+ * (one GPU) owns the planes [z0, z1) of the global grid in an extended
+ * local lm_grid whose first and last planes are ghost copies of the
+ * neighbours' boundary planes (a wall in z on the local grid; its wall
+ * faces touch ghost planes only).  A host driver (the package's shard
+ * module) exchanges ghost planes and float64 scalars between ranks and
+ * sequences the entry points below; all arithmetic on grid data runs in
+ * these kernels.  Device pointers, ordered on `stream`. */
+
+/* Halo pack (unpack = 0) or unpack (unpack = 1) of the z-boundary planes of
+ * a cell array `a` (elem_bytes 4 or 8, plane_elems = nx*ny values a plane):
+ * buf = [planes lo_first .. lo_first + nplanes) then [planes hi_first ..
+ * hi_first + nplanes); a side whose first plane is negative is skipped
+ * (its part of buf untouched).  One launch for both sides.
+ * LM_ERR_INVALID_ARG for bad sizes or both sides skipped. */
+int  lm_halo_pack(const void* a, int elem_bytes, int64_t plane_elems, int64_t lo_first, int64_t hi_first,
+                  int nplanes, void* buf, int unpack, void* stream);
+
+/* out = alpha x + beta y (y may be NULL: out = alpha x), n values; x, y,
+ * out in float64 (LM_PREC_FP64) or float32 (LM_PREC_FP32) each, arithmetic
+ * in float64; out may alias x or y. */
+int  lm_vec_axpby(int64_t n, double alpha, const void* x, int x_prec, double beta, const void* y, int y_prec,
+                  void* out, int out_prec, void* stream);
+
+/* *out (host) = sum a_i b_i over n values, float64 accumulation in a fixed
+ * order (bitwise reproducible); scratch: caller-allocated device buffer of
+ * at least 1025 doubles.  Synchronises the stream. */
+int  lm_vec_dot(int64_t n, const void* a, int a_prec, const void* b, int b_prec, double* scratch, double* out,
+                void* stream);
+
+/* z = d .* r (float64, n values). */
+int  lm_vec_mul(int64_t n, const double* d, const double* r, double* z, void* stream);
+
+/* The inverse Jacobi diagonal 1/(c~ + sum of the cell's face conductances)
+ * of the grid's float64 operator (N values), the preconditioner of the
+ * plain float64 PCG (Sec. 2.5 uses incomplete Cholesky). */
+int  lm_jacobi_inverse_diagonal(lm_grid* g, double* dinv, void* stream);
+
+/* The V-cycle's transfers between level 0 and level 1 (lm_mg_level_shape):
+ * fc = R (f - A32 x), the restriction (mean over the children) of the
+ * float32 residual; x += P ec, the piecewise-constant prolongation of a
+ * level-1 vector.  Float32 device vectors. */
+int  lm_mg_restrict_residual(lm_grid* g, const float* x, const float* f, float* fc, void* stream);
+int  lm_mg_prolong_add(lm_grid* g, const float* ec, float* x, void* stream);
+
+/* The float32 coefficients of multigrid level `level`: c~ and rho /
+ * *rho_scale (the float32 copy of rho is kept divided by a power of two,
+ * reported in *rho_scale), as the hierarchy holds them (levels >= 1: means
+ * over the children).  ct, rho: device arrays of the level's cell count (or
+ * NULL). */
+int  lm_mg_level_coefficients(lm_grid* g, int level, float* ct, float* rho, double* rho_scale, void* stream);
+
 /* ---- measurement ---------------------------------------------------------- */
 
 /* Arithmetic-rate probe of the current device, the measured roof of the

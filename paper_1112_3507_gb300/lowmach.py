@@ -98,6 +98,17 @@ _SIGNATURES = {
     "lm_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(SolveOpts),
                                        ctypes.POINTER(SolveResult)]),
     "lm_autotune_set_cache": (ctypes.c_int, [ctypes.c_char_p]),
+    "lm_halo_pack": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                     _P, ctypes.c_int, _P]),
+    "lm_vec_axpby": (ctypes.c_int, [ctypes.c_int64, ctypes.c_double, _P, ctypes.c_int, ctypes.c_double, _P,
+                                     ctypes.c_int, _P, ctypes.c_int, _P]),
+    "lm_vec_dot": (ctypes.c_int, [ctypes.c_int64, _P, ctypes.c_int, _P, ctypes.c_int, _P,
+                                   ctypes.POINTER(ctypes.c_double), _P]),
+    "lm_vec_mul": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P]),
+    "lm_jacobi_inverse_diagonal": (ctypes.c_int, [_P, _P, _P]),
+    "lm_mg_restrict_residual": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "lm_mg_prolong_add": (ctypes.c_int, [_P, _P, _P, _P]),
+    "lm_mg_level_coefficients": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "lm_probe_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "lm_apply_dot_noalloc": (ctypes.c_int, [ctypes.c_int, _I64_3, _I3, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
