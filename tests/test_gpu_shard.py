@@ -154,8 +154,8 @@ SHARD_PROBLEMS = {
 @pytest.mark.parametrize("name", list(SHARD_PROBLEMS))
 @pytest.mark.parametrize("world", [1, 2, 3])
 def test_distributed_solve_on_gpu(name, world):
-    """shard.pcg_jacobi and shard.mg_fcg with GpuSlab ranks: the float64
-    solutions match the oracle's direct solve to 1e-10, and the distributed
+    """shard.mg_fcg (and, on the 2D grid, shard.pcg_jacobi) with GpuSlab
+    ranks: the float64 solutions match the oracle's direct solve to 1e-10, and the distributed
     V-cycle preconditions as well as the single-domain one (iteration count
     within one of the library's own float64 MG-FCG mode)."""
     from paper_1112_3507_gb300 import shard as S
@@ -166,12 +166,16 @@ def test_distributed_solve_on_gpu(name, world):
         g.set_problem(p)
         r_single = g.solve(mode="fp64-mg", rtol=1e-12, max_iter=200, nu1=2, nu2=2)
 
+    jacobi = name.startswith("plain2d") and world == 2      # the slow plain PCG on the small grid only
+
     def rank(r, comm):
         geo = S.SlabGeometry(p.n, p.h, p.bc, r, world)
         ops = S.GpuSlab(geo, p.rho_old, p.rho_new, p.cs2, p.dt, p.f)
         try:
-            kj, _ = S.pcg_jacobi(ops, comm, rtol=1e-12, max_iter=20000)
-            x1 = ops.solution().cpu().numpy().copy()
+            x1 = None
+            if jacobi:
+                S.pcg_jacobi(ops, comm, rtol=1e-12, max_iter=20000)
+                x1 = ops.solution().cpu().numpy().copy()
             km, _ = S.mg_fcg(ops, comm, rtol=1e-12, max_iter=200, nu1=2, nu2=2)
             x2 = ops.solution().cpu().numpy().copy()
             rel = S.true_residual(ops, comm)
@@ -180,9 +184,10 @@ def test_distributed_solve_on_gpu(name, world):
         return x1, x2, km, rel
 
     res = _run_threads(world, rank)
-    x1 = np.concatenate([t[0] for t in res])
     x2 = np.concatenate([t[1] for t in res])
-    assert np.linalg.norm(x1 - xs) <= 1e-10 * np.linalg.norm(xs)
+    if jacobi:
+        x1 = np.concatenate([t[0] for t in res])
+        assert np.linalg.norm(x1 - xs) <= 1e-10 * np.linalg.norm(xs)
     assert np.linalg.norm(x2 - xs) <= 1e-10 * np.linalg.norm(xs)
     assert res[0][3] <= 2e-12
     assert abs(res[0][2] - r_single["iters"]) <= 1
