@@ -269,27 +269,45 @@ int  lm_net_features(lm_grid* g, const double* v, float* feat, double* scale, vo
 /* Solve `count` independent 2D grids (distinct lm_grid handles, each with
  * coefficients and rhs set) in the mixed-precision mode of LM_MIXED_MG_IR,
  * all at once: every phase of the solve is one launch over the tiles of all
- * grids, grids that have converged skip their tiles, and the launch sequence
- * of one refinement step (opts->inner_max_iter inner iterations) is captured
- * as a CUDA graph and replayed up to opts->max_outer times.  The sweep
+ * grids, grids that have converged skip their tiles, and one refinement
+ * step is captured as a CUDA graph whose inner flexible-CG iterations form
+ * a device-side while loop (a conditional graph node that repeats while
+ * some grid still iterates, at most opts->inner_max_iter times); the graph
+ * is replayed up to opts->max_outer times.  The sweep
  * z-chunk of every level shape is chosen by the autotuner (see
  * lm_autotune_set_cache).  The captured plan is cached per (grids,
  * coefficient versions, inner_max_iter, use_x0) and reused by later calls.
  * Grids whose coefficients changed since their last solve get their
  * multigrid hierarchies refreshed first, their coarsest-level inverses all
  * formed in one launch.
- * Requirements: 2D grids (ndim 2), nu1 = nu2 = 1 (lm_default_opts sets 2 and 3:
- * set both to 1 for a batch), an exactly solved coarsest
- * level (grids whose halvings reach <= 64 cells), even periodic extents.
+ * Requirements: 2D grids (ndim 2), 1 <= nu1, nu2 <= 8, an exactly solved
+ * coarsest level (grids whose halvings reach <= 64 cells), even periodic
+ * extents.
  * results[i] receives grid i's status, inner iterations (iters = vcycles),
  * refinement steps and final float64 relative residual; `seconds` is the
  * device time of the whole batch.  Returns LM_OK or the first failing
  * grid's status; LM_ERR_INVALID_ARG / LM_ERR_STATE before any work. */
 int  lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* opts, lm_solve_result* results);
 
+/* Coefficient assembly of `count` grids at once: lm_set_coefficients of
+ * each (step (v) of Sec. 2.4; Eqs. cpoiss, kappapoiss) in one launch over
+ * all of them and one wait for their positivity reports.  rho_old[i],
+ * rho_new[i], cs2[i]: device pointers to grid i's N_i values (float64);
+ * dt[i]: host.  Each grid is left as lm_set_coefficients would leave it;
+ * returns LM_OK or the first failing grid's status (LM_ERR_NOT_POSITIVE for
+ * a non-positive or non-finite input; that grid then holds no coefficients).
+ * The hierarchies of the grids are refreshed by the next lm_batch_solve, one
+ * launch per level over all of them. */
+int  lm_batch_set_coefficients(lm_grid* const* grids, int count, const double* const* rho_old,
+                               const double* const* rho_new, const double* const* cs2, const double* dt,
+                               void* stream);
+
 /* Autotuner cache: a JSON object {"<gpu>|rbgs2d-zm|<nx>x<nz>|bc<x><z>|f32": kz,
- * ...} of the fastest sweep z-chunk per level shape, read on first use and
- * rewritten when new shapes are timed.  Default path: $LM_AUTOTUNE_CACHE or
+ * "<gpu>|rbgs2d-batch|d<depth>|<hash>": kz, ...}: the fastest sweep z-chunk
+ * (rows per tile) per level shape for one grid, and per multigrid depth of a
+ * batch (timed on the batched sweep over every grid's tiles of that depth;
+ * <hash> = FNV-1a of the batch's level shapes and boundary conditions),
+ * read on first use and rewritten when new entries are timed.  Default path: $LM_AUTOTUNE_CACHE or
  * $HOME/.cache/lowmach_autotune.json.  NULL or "" restores the default.
  * Clears the in-memory table. */
 int  lm_autotune_set_cache(const char* path);

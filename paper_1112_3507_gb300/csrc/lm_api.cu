@@ -620,7 +620,15 @@ int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double
     CK(cudaStreamSynchronize(s));
     g->mg_built = false;
     g->have_dinv = false;
-    const AsmFlags fl = *g->asm_fl_host;
+    return lm::grid_finish_assembly(g, *g->asm_fl_host, s);
+}
+
+}  // namespace
+
+// After an assembly: the positivity verdict and the float32 range handling.
+int lm::grid_finish_assembly(lm_grid* g, const AsmFlags& fl, cudaStream_t s) {
+    g->mg_built = false;
+    g->have_dinv = false;
     if (fl.bad) {
         g->have_coefs = false;
         return LM_ERR_NOT_POSITIVE;
@@ -653,8 +661,6 @@ int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double
     g->have_coefs = true;
     return LM_OK;
 }
-
-}  // namespace
 
 int lm::grid_build_mg(lm_grid* g, cudaStream_t s, bool defer_inverse) { return build_mg(g, s, defer_inverse); }
 lm::Lev32 lm::make_level(const int n[3], const int bc[3], const double h[3], const float* ct, const float* rho,

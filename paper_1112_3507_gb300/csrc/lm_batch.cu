@@ -47,6 +47,7 @@ struct BLev {
     int hx, hy, hz;     // halving to the next level
     int kz;             // sweep z-chunk (autotuned)
     float* xa;          // pre-smoothed iterate
+    float* xb;          // sweep scratch (sweeps beyond the first of a pre- or post-smoothing chain)
     float* xo;          // V-cycle output (level 0: the grid's z)
     const float* f;     // right-hand side (level 0: the grid's r32)
     float* fc;          // the next level's right-hand side
@@ -120,8 +121,11 @@ __global__ void __launch_bounds__(NT) kb_ir_residual(const BTask* __restrict__ T
     }
 }
 
-// e = 0; ||r32|| of the inner problem; re-arm the inner state
-__global__ void __launch_bounds__(NT) kb_inner_init(const BTask* __restrict__ T, const BGrid* __restrict__ Gs) {
+// e = 0; ||r32|| of the inner problem; re-arm the inner state; block 0
+// zeroes the inner-iteration counter of the refinement step
+__global__ void __launch_bounds__(NT) kb_inner_init(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
+                                                    int* __restrict__ inner_it) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *inner_it = 0;
     const BTask t = T[blockIdx.x];
     const BGrid& G = Gs[t.g];
     if (G.st->done) return;
@@ -140,27 +144,32 @@ __global__ void __launch_bounds__(NT) kb_inner_init(const BTask* __restrict__ T,
     }
 }
 
-__global__ void __launch_bounds__(128, 8) kb_rbgs_pre(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
-                                                      const BLev* __restrict__ Ls) {
-    const BTask t = T[blockIdx.x];
-    if (inner_off(Gs[t.g])) return;
-    const BLev& V = Ls[t.l];
-    if (V.L.g.nx % 256 == 0 && V.L.g.nz >= 2)        // whole 256-cell rows: the z-march (same tiles)
-        zm2d_tile<0, true, false>(V.L, nullptr, nullptr, V.C, 0, 0, V.f, V.xa, V.kz, t.bx, t.by);
-    else
-        rbgs_tile<128, 1, false, 0, true, false>(V.L, nullptr, nullptr, V.C, 0, 0, 0, V.f, V.xa, V.kz, t.bx, t.by, 0);
+// The level buffer a batched sweep reads or writes: 1 xa, 2 xb, 3 xo.
+__device__ __forceinline__ float* lev_buf(const BLev& V, int sel) {
+    return sel == 1 ? V.xa : sel == 2 ? V.xb : V.xo;
 }
 
-__global__ void __launch_bounds__(128, 8) kb_rbgs_post(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
-                                                       const BLev* __restrict__ Ls) {
+// One red-black sweep of every grid's level (task t.l) from buffer `src`
+// into buffer `dst`: ZERO, the first pre-smoothing sweep (from zero, red
+// first); PROLONG, the first post-smoothing sweep (from xa plus the coarse
+// correction, black first); otherwise a plain sweep in the chain's order.
+// (CHECK false: every grid's tiles run, whatever the solve states -- the
+// autotuner's timing launches.)
+template <int FIRST, bool ZERO, bool PROLONG, bool CHECK = true>
+__global__ void __launch_bounds__(128, 8) kb_rbgs(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
+                                                  const BLev* __restrict__ Ls, int src, int dst) {
     const BTask t = T[blockIdx.x];
-    if (inner_off(Gs[t.g])) return;
+    if (CHECK && inner_off(Gs[t.g])) return;
     const BLev& V = Ls[t.l];
-    if (V.L.g.nx % 256 == 0 && V.L.g.nz >= 2)
-        zm2d_tile<1, false, true>(V.L, V.xa, V.ec, V.C, V.hx, V.hz, V.f, V.xo, V.kz, t.bx, t.by);
+    const float* xin = ZERO ? nullptr : lev_buf(V, src);
+    float* xout = lev_buf(V, dst);
+    if (V.L.g.nx % 256 == 0 && V.L.g.nz >= 2)        // whole 256-cell rows: the z-march (same tiles)
+        zm2d_tile<FIRST, ZERO, PROLONG>(V.L, xin, PROLONG ? V.ec : nullptr, V.C, PROLONG ? V.hx : 0,
+                                        PROLONG ? V.hz : 0, V.f, xout, V.kz, t.bx, t.by);
     else
-        rbgs_tile<128, 1, false, 1, false, true>(V.L, V.xa, V.ec, V.C, V.hx, V.hy, V.hz, V.f, V.xo, V.kz, t.bx,
-                                                 t.by, 0);
+        rbgs_tile<128, 1, false, FIRST, ZERO, PROLONG>(V.L, xin, PROLONG ? V.ec : nullptr, V.C, PROLONG ? V.hx : 0,
+                                                        PROLONG ? V.hy : 0, PROLONG ? V.hz : 0, V.f, xout, V.kz,
+                                                        t.bx, t.by, 0);
 }
 
 __global__ void __launch_bounds__(256) kb_resid_restrict(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
@@ -186,10 +195,12 @@ __global__ void kb_coarse(const BTask* __restrict__ T, const BGrid* __restrict__
     coarse_solve_block(V.L.g.N, V.ainv, V.f, V.xo);
 }
 
-__global__ void __launch_bounds__(NT) kb_dot_zq(const BTask* __restrict__ T, const BGrid* __restrict__ Gs) {
+// z.q_old (not on the first inner iteration of a refinement step, *inner_it == 0)
+__global__ void __launch_bounds__(NT) kb_dot_zq(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
+                                                const int* __restrict__ inner_it) {
     const BTask t = T[blockIdx.x];
     const BGrid& G = Gs[t.g];
-    if (inner_off(G)) return;
+    if (inner_off(G) || *inner_it == 0) return;
     __shared__ double sm[32];
     const FF a = dot32_range(G.N, G.z32, G.q32, t.lblk, t.nblk);
     double v[1] = {ff_value(a)};
@@ -198,11 +209,30 @@ __global__ void __launch_bounds__(NT) kb_dot_zq(const BTask* __restrict__ T, con
 }
 
 __global__ void __launch_bounds__(NT) kb_beta_p(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
-                                                int first) {
+                                                const int* __restrict__ inner_it) {
     const BTask t = T[blockIdx.x];
     const BGrid& G = Gs[t.g];
     if (inner_off(G)) return;
-    fcg_beta_p_range(G.N, G.z32, G.p32, G.red.scal, first, t.lblk, t.nblk);
+    fcg_beta_p_range(G.N, G.z32, G.p32, G.red.scal, *inner_it == 0, t.lblk, t.nblk);
+}
+
+// End of one inner iteration of the device-side loop: count it, and keep
+// looping while some grid is still iterating (neither converged overall nor
+// at its inner tolerance) and the step's iteration limit is not reached.
+__global__ void __launch_bounds__(256) kb_inner_cond(const BGrid* __restrict__ Gs, int count,
+                                                     int* __restrict__ inner_it, int inner_max,
+                                                     cudaGraphConditionalHandle loop) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int g = threadIdx.x; g < count; g += blockDim.x)
+        if (!inner_off(Gs[g])) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int it = *inner_it + 1;
+        *inner_it = it;
+        cudaGraphSetConditional(loop, (any && it < inner_max) ? 1u : 0u);
+    }
 }
 
 __global__ void __launch_bounds__(256) kb_apply(const BTask* __restrict__ T, const BGrid* __restrict__ Gs,
@@ -254,6 +284,42 @@ __global__ void kb_gather(const BGrid* __restrict__ Gs, int count, SolveState* _
     if (g >= count) return;
     out[g] = *Gs[g].st;
     out[count + g] = *Gs[g].st_in;
+}
+
+// ---- batched set-up ------------------------------------------------------------
+
+// Task t of a batched assembly: blocks lblk of nblk over grid g's cells.
+__global__ void __launch_bounds__(NT) kb_assemble(const BTask* __restrict__ T, const AsmArgs* __restrict__ A) {
+    const BTask t = T[blockIdx.x];
+    assemble_range(A[t.g], t.lblk * NT + threadIdx.x, t.nblk * NT);
+}
+
+// flags of every grid to "nothing seen yet" (before), and gathered into one buffer (after)
+__global__ void kb_asm_flags(const AsmArgs* __restrict__ A, int count, AsmFlags* __restrict__ out, int gather) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= count) return;
+    if (gather) {
+        out[g] = *A[g].fl;
+    } else {
+        AsmFlags f{};
+        f.rho_max = 0ull;
+        f.rho_min = ~0ull;
+        *A[g].fl = f;
+    }
+}
+
+// One coarsening step (level l -> l + 1) of many grids: task t is block
+// (bx, by, bz) of the coarse level of item t.g.
+struct BCoarsen {
+    Lev32 F;
+    Geo C;
+    int hx, hy, hz;
+    float *ct_c, *rho_c;
+};
+__global__ void __launch_bounds__(256) kb_coarsen(const BTask* __restrict__ T, const BCoarsen* __restrict__ items) {
+    const BTask t = T[blockIdx.x];
+    const BCoarsen& it = items[t.g];
+    coarsen_cell(it.F, it.C, it.hx, it.hy, it.hz, it.ct_c, it.rho_c, t.bx, t.by, t.bz);
 }
 
 }  // namespace lm
@@ -375,12 +441,119 @@ int tune_sweep_kz(const MgLevel& M, const float* fin, float* scratch, cudaStream
     return best;
 }
 
+int hdiv(int a, int b) { return (a + b - 1) / b; }
+
+// Batched z-chunk: the chunk of the sweeps at multigrid depth d of a batch,
+// timed on the batched sweep itself (every grid's tiles of that depth in one
+// launch: the per-grid choice above fills the GPU with one grid's blocks,
+// which a batch does not need) over the candidates 4..64, and remembered
+// per depth and batch composition (an FNV-1a hash of the level shapes and
+// boundary conditions).  Sets the chunk of every level at that depth.
+int tune_batch_kz(lm_grid* const* grids, int count, std::vector<BLev>& hl, const std::vector<int>& lev0,
+                  const std::vector<int>& lstop, int max_depth, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load();
+    bool changed = false;
+    BLev* dL = nullptr;
+    BTask* dT = nullptr;
+    size_t tcap = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = LM_OK;
+    for (int d = 0; d < max_depth && rc == LM_OK; ++d) {
+        unsigned long long h = 1469598103934665603ULL;
+        auto mix = [&](long long v) {
+            for (int b = 0; b < 8; ++b) {
+                h ^= (unsigned long long)((v >> (8 * b)) & 0xff);
+                h *= 1099511628211ULL;
+            }
+        };
+        int nlev = 0, maxnz = 0;
+        for (int i = 0; i < count; ++i) {
+            if (d >= lstop[i]) continue;
+            const Geo& g = hl[lev0[i] + d].L.g;
+            mix(g.nx), mix(g.nz), mix(g.bcx * 2 + g.bcz);
+            ++nlev;
+            maxnz = std::max(maxnz, g.nz);
+        }
+        if (!nlev) continue;
+        char key[256];
+        snprintf(key, sizeof key, "%s|rbgs2d-batch|d%d|%016llx", gpu_name().c_str(), d, h);
+        int best = -1;
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            best = it->second;
+        } else {
+            if (!dL) {
+                if (cudaMalloc(&dL, sizeof(BLev) * hl.size()) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+                    cudaEventCreate(&e1) != cudaSuccess) {
+                    rc = LM_ERR_CUDA;
+                    break;
+                }
+            }
+            float best_ms = 1e30f;
+            for (int kz : {4, 8, 16, 32, 64}) {
+                if (kz > maxnz && kz != 4) continue;
+                std::vector<BTask> tasks;
+                for (int i = 0; i < count; ++i) {
+                    if (d >= lstop[i]) continue;
+                    BLev& V = hl[lev0[i] + d];
+                    V.kz = kz;
+                    const int gx = hdiv(V.L.g.nx, 256), gy = hdiv(V.L.g.nz, kz);
+                    for (int by = 0; by < gy; ++by)
+                        for (int bx = 0; bx < gx; ++bx) tasks.push_back(BTask{i, lev0[i] + d, bx, by, 0, 0, 0});
+                }
+                if (tasks.size() > tcap) {
+                    cudaFree(dT);
+                    dT = nullptr;
+                    if (cudaMalloc(&dT, sizeof(BTask) * tasks.size()) != cudaSuccess) {
+                        rc = LM_ERR_CUDA;
+                        break;
+                    }
+                    tcap = tasks.size();
+                }
+                cudaMemcpy(dL, hl.data(), sizeof(BLev) * hl.size(), cudaMemcpyHostToDevice);
+                cudaMemcpy(dT, tasks.data(), sizeof(BTask) * tasks.size(), cudaMemcpyHostToDevice);
+                const unsigned nb = (unsigned)tasks.size();
+                count_launches(4);
+                kb_rbgs<0, true, false, false><<<nb, 128, 0, s>>>(dT, nullptr, dL, 0, 1);
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 3; ++r) kb_rbgs<0, true, false, false><<<nb, 128, 0, s>>>(dT, nullptr, dL, 0, 1);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = LM_ERR_CUDA;
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = kz;
+                }
+            }
+            if (best > 0) {
+                g_tune[key] = best;
+                changed = true;
+            }
+        }
+        if (best > 0)
+            for (int i = 0; i < count; ++i)
+                if (d < lstop[i]) hl[lev0[i] + d].kz = best;
+    }
+    if (changed) tune_save();
+    cudaFree(dL);
+    cudaFree(dT);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess && rc == LM_OK) rc = LM_ERR_CUDA;
+    return rc;
+}
+
 // ---- plan -----------------------------------------------------------------------
 
 struct Plan {
     std::vector<lm_grid*> grids;
     std::vector<unsigned> versions;
-    int inner_max = 0, first = 0, count = 0;
+    int inner_max = 0, first = 0, count = 0, nu1 = 1, nu2 = 1;
     BGrid* dgrids = nullptr;
     BLev* dlevs = nullptr;
     int* dlev0 = nullptr;
@@ -395,7 +568,10 @@ struct Plan {
     CoarseCycle* dcc = nullptr;          // per-grid one-block coarse cycles (null: per-level launches)
     size_t cc_smem = 0;                  // their dynamic shared memory (the largest chain's)
     int max_depth = 0;
-    long long n_first = 0, n_step = 0;   // kernels per graph launch
+    long long n_first = 0, n_step = 0;   // kernels per graph launch (n_step: outside the inner loop)
+    long long n_iter = 0;                // kernels per inner iteration of the device-side loop
+    int* dinner = nullptr;               // inner iterations run in the last refinement step (device)
+    int* hinner = nullptr;
 
     ~Plan() {
         if (g_first) cudaGraphExecDestroy(g_first);
@@ -410,6 +586,8 @@ struct Plan {
         cudaFree(dinv_tasks);
         cudaFree(dgather);
         cudaFreeHost(hgather);
+        cudaFree(dinner);
+        cudaFreeHost(hinner);
     }
 };
 
@@ -420,13 +598,13 @@ struct TaskList {
     int off = 0, n = 0;
 };
 
-int hdiv(int a, int b) { return (a + b - 1) / b; }
-
 int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStream_t s, Plan** out) {
     Plan* P = new Plan();
     P->grids.assign(grids, grids + count);
     for (int i = 0; i < count; ++i) P->versions.push_back(grids[i]->version);
     P->inner_max = o->inner_max_iter;
+    P->nu1 = o->nu1;
+    P->nu2 = o->nu2;
     P->first = !o->use_x0;
     P->count = count;
     {   // every grid's coarsest inverse, one block per row of it
@@ -505,6 +683,7 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
                 V.kz = tune_sweep_kz(M, l == 0 ? g->r32 : M.f, M.xa, s, &changed);
             }
             V.xa = M.xa;
+            V.xb = M.xb;
             V.xo = l == 0 ? g->z32 : M.xo;
             V.f = l == 0 ? g->r32 : M.f;
             V.ainv = M.ainv;
@@ -559,14 +738,15 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
                 cc.f[k] = (lc + k == 0) ? g->r32 : Mk.f;
             }
             cc.ainv = g->mg.back().ainv;
-            cc.nu1 = 1;
-            cc.nu2 = 1;
+            cc.nu1 = o->nu1;
+            cc.nu2 = o->nu2;
         }
         for (const CoarseCycle& cc : hcc) P->cc_smem = std::max(P->cc_smem, cc_smem_bytes(cc));
         BCK(cudaFuncSetAttribute(kb_coarse_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC_SMEM_MAX));
         BCK(cudaMalloc(&P->dcc, sizeof(CoarseCycle) * count));
         BCK(cudaMemcpy(P->dcc, hcc.data(), sizeof(CoarseCycle) * count, cudaMemcpyHostToDevice));
     }
+    if (int rc = tune_batch_kz(grids, count, hl, lev0, lstop, P->max_depth, s)) return rc;
     std::vector<TaskList> tpre(P->max_depth), trr(P->max_depth);
     for (int d = 0; d < P->max_depth; ++d) {
         tpre[d].off = (int)tasks.size();
@@ -603,34 +783,94 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
     BCK(cudaMemcpy(P->dlev0, lev0.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(P->dtasks, tasks.data(), sizeof(BTask) * tasks.size(), cudaMemcpyHostToDevice));
     BCK(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+    BCK(cudaMalloc(&P->dinner, sizeof(int)));
+    BCK(cudaMallocHost(&P->hinner, sizeof(int)));
+    BCK(cudaMemset(P->dinner, 0, sizeof(int)));
+    cudaStream_t body_stream = nullptr;
+    BCK(cudaStreamCreateWithFlags(&body_stream, cudaStreamNonBlocking));
 
     const BTask* T = P->dtasks;
     const BGrid* Gs = P->dgrids;
     const BLev* Ls = P->dlevs;
     long long nk = 0;
-    auto launch_step = [&](cudaStream_t cs) {
-        // one refinement step: inner flexible CG (fixed length, converged grids idle), correction, residual
-        kb_inner_init<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs);
-        nk += 4;   // inner init, correction, residual, gather
-        for (int it = 0; it < P->inner_max; ++it) {
-            for (int d = 0; d < P->max_depth; ++d) nk += (tpre[d].n ? 2 : 0) + (trr[d].n ? 1 : 0);
-            nk += 1 + (it > 0) + 3;
-            for (int d = 0; d < P->max_depth; ++d) {
-                if (tpre[d].n) kb_rbgs_pre<<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls);
-                if (trr[d].n) kb_resid_restrict<<<trr[d].n, dim3(32, 8), 0, cs>>>(T + trr[d].off, Gs, Ls);
+    // one inner flexible-CG iteration over all grids (converged grids idle),
+    // ending with the loop's condition
+    auto launch_iteration = [&](cudaStream_t cs, cudaGraphConditionalHandle loop) {
+        // pre-smoothing: nu1 red-black sweeps, the last one into xa (the
+        // residual's and the first post-sweep's input); post-smoothing: nu2
+        // black-red sweeps from xa + P ec, through xb / xa, the last into xo
+        const int nu1 = P->nu1, nu2 = P->nu2;
+        for (int d = 0; d < P->max_depth; ++d) {
+            if (tpre[d].n) {
+                for (int k = 0; k < nu1; ++k) {
+                    const int dst = ((nu1 - 1 - k) % 2 == 0) ? 1 : 2, src = dst == 1 ? 2 : 1;
+                    if (k == 0) kb_rbgs<0, true, false><<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls, 0, dst);
+                    else kb_rbgs<0, false, false><<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls, src, dst);
+                }
+                nk += nu1;
             }
-            if (P->dcc) kb_coarse_cycle<<<count, CC_THREADS, P->cc_smem, cs>>>(P->dcc, Gs);
-            else kb_coarse<<<tco.n, 64, 0, cs>>>(T + tco.off, Gs, Ls);
-            for (int d = P->max_depth - 1; d >= 0; --d)
-                if (tpre[d].n) kb_rbgs_post<<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls);
-            if (it > 0) kb_dot_zq<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs);
-            kb_beta_p<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs, it == 0);
-            kb_apply<<<tap.n, dim3(32, 8), 0, cs>>>(T + tap.off, Gs, Ls, P->dlev0);
-            kb_update<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs);
+            if (trr[d].n) {
+                kb_resid_restrict<<<trr[d].n, dim3(32, 8), 0, cs>>>(T + trr[d].off, Gs, Ls);
+                ++nk;
+            }
         }
+        if (P->dcc) kb_coarse_cycle<<<count, CC_THREADS, P->cc_smem, cs>>>(P->dcc, Gs);
+        else kb_coarse<<<tco.n, 64, 0, cs>>>(T + tco.off, Gs, Ls);
+        for (int d = P->max_depth - 1; d >= 0; --d)
+            if (tpre[d].n) {
+                int src = 1;
+                for (int k = 0; k < nu2; ++k) {
+                    const int dst = k == nu2 - 1 ? 3 : (k % 2 == 0 ? 2 : 1);
+                    if (k == 0) kb_rbgs<1, false, true><<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls, src, dst);
+                    else kb_rbgs<1, false, false><<<tpre[d].n, 128, 0, cs>>>(T + tpre[d].off, Gs, Ls, src, dst);
+                    src = dst;
+                }
+                nk += nu2;
+            }
+        kb_dot_zq<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs, P->dinner);
+        kb_beta_p<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs, P->dinner);
+        kb_apply<<<tap.n, dim3(32, 8), 0, cs>>>(T + tap.off, Gs, Ls, P->dlev0);
+        kb_update<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs);
+        kb_inner_cond<<<1, 256, 0, cs>>>(Gs, count, P->dinner, P->inner_max, loop);
+        nk += 6;
+    };
+    // One refinement step: the inner flexible CG as a device-side while loop
+    // (a conditional node of the graph: it repeats its body while some grid
+    // still iterates, so the step launches only the iterations the slowest
+    // grid needs), then the correction and the new float64 residual.
+    auto launch_step = [&](cudaStream_t cs) -> cudaError_t {
+        kb_inner_init<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs, P->dinner);
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+        if (e != cudaSuccess) return e;
+        cudaGraphConditionalHandle loop;
+        if ((e = cudaGraphConditionalHandleCreate(&loop, cg, 1, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = loop;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        if ((e = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp)) != cudaSuccess) return e;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return e;
+        nk = 0;
+        launch_iteration(body_stream, loop);
+        P->n_iter = nk;
+        if ((e = cudaStreamEndCapture(body_stream, &body)) != cudaSuccess) return e;
+        if ((e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+            cudaSuccess)
+            return e;
         kb_ir_correct<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs);
         kb_ir_residual<<<t1d.n, NT, 0, cs>>>(T + t1d.off, Gs, 0, 0);
         kb_gather<<<hdiv(count, 64), 64, 0, cs>>>(Gs, count, P->dgather);
+        nk = 4;    // inner init, correction, residual, gather
+        return cudaSuccess;
     };
     auto launch_first = [&](cudaStream_t cs) {
         nk += 2;
@@ -641,19 +881,25 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
         cudaGraph_t graph = nullptr;
         BCK(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
         nk = 0;
+        cudaError_t e = cudaSuccess;
         if (pass == 0) launch_first(P->cap);
-        else launch_step(P->cap);
+        else e = launch_step(P->cap);
         (pass == 0 ? P->n_first : P->n_step) = nk;
-        BCK(cudaStreamEndCapture(P->cap, &graph));
+        const cudaError_t e2 = cudaStreamEndCapture(P->cap, &graph);
+        BCK(e);
+        BCK(e2);
         BCK(cudaGraphInstantiate(pass == 0 ? &P->g_first : &P->g_step, graph, 0));
         cudaGraphDestroy(graph);
     }
+    cudaStreamDestroy(body_stream);
     *out = P;
     return LM_OK;
 }
 
 bool plan_matches(const Plan* P, lm_grid* const* grids, int count, const lm_solve_opts* o) {
-    if (P->count != count || P->inner_max != o->inner_max_iter || P->first != !o->use_x0) return false;
+    if (P->count != count || P->inner_max != o->inner_max_iter || P->first != !o->use_x0 || P->nu1 != o->nu1 ||
+        P->nu2 != o->nu2)
+        return false;
     for (int i = 0; i < count; ++i)
         if (P->grids[i] != grids[i] || P->versions[i] != grids[i]->version) return false;
     return true;
@@ -671,6 +917,102 @@ void drop_plans_of(const lm_grid* g) {
     }
 }
 
+// Device tables of the batched set-up, grown as needed and reused by later
+// calls (one set per process; calls are serialised by its mutex).
+struct SetupTables {
+    std::mutex mu;
+    BTask* dtask = nullptr;
+    size_t ntask_cap = 0;
+    void* ditems = nullptr;
+    size_t items_cap = 0;
+    AsmFlags* dflags = nullptr;
+    AsmFlags* hflags = nullptr;
+    int flags_cap = 0;
+    void* hitems = nullptr;
+    size_t hitems_cap = 0;
+};
+SetupTables g_setup;
+
+int ensure_tables(size_t ntask, size_t item_bytes, int nflags) {
+    SetupTables& S = g_setup;
+    if (ntask > S.ntask_cap) {
+        cudaFree(S.dtask);
+        S.dtask = nullptr;
+        S.ntask_cap = 0;
+        BCK(cudaMalloc(&S.dtask, sizeof(BTask) * ntask));
+        S.ntask_cap = ntask;
+    }
+    if (item_bytes > S.items_cap) {
+        cudaFree(S.ditems);
+        cudaFreeHost(S.hitems);
+        S.ditems = S.hitems = nullptr;
+        S.items_cap = 0;
+        BCK(cudaMalloc(&S.ditems, item_bytes));
+        BCK(cudaMallocHost(&S.hitems, item_bytes));
+        S.items_cap = item_bytes;
+    }
+    if (nflags > S.flags_cap) {
+        cudaFree(S.dflags);
+        cudaFreeHost(S.hflags);
+        S.dflags = nullptr;
+        S.hflags = nullptr;
+        S.flags_cap = 0;
+        BCK(cudaMalloc(&S.dflags, sizeof(AsmFlags) * nflags));
+        BCK(cudaMallocHost(&S.hflags, sizeof(AsmFlags) * nflags));
+        S.flags_cap = nflags;
+    }
+    return LM_OK;
+}
+
+// Coarse coefficients of every grid whose hierarchy exists but is stale,
+// level by level, one launch per level over all of them.
+int batch_refresh(lm_grid* const* grids, int count, cudaStream_t s) {
+    std::vector<lm_grid*> todo;
+    size_t depth = 0;
+    for (int i = 0; i < count; ++i)
+        if (!grids[i]->mg_built && grids[i]->mg.size() > 1 && grids[i]->fp32_ok) {
+            todo.push_back(grids[i]);
+            depth = std::max(depth, grids[i]->mg.size() - 1);
+        }
+    if (todo.empty()) return LM_OK;
+    std::lock_guard<std::mutex> lk(g_setup.mu);
+    for (size_t d = 0; d < depth; ++d) {
+        std::vector<BCoarsen> items;
+        std::vector<BTask> tasks;
+        for (lm_grid* g : todo) {
+            if (d + 1 >= g->mg.size()) continue;
+            const MgLevel& F = g->mg[d];
+            const MgLevel& C = g->mg[d + 1];
+            const int it = (int)items.size();
+            items.push_back(BCoarsen{F.L, C.L.g, F.halved[0], F.halved[1], F.halved[2], C.ct, C.rho});
+            const Geo& cg = C.L.g;
+            const int gx = hdiv(cg.nx, 32);
+            const int gy = cg.ny > 1 ? hdiv(cg.ny, 8) : hdiv(cg.nz, 8);
+            const int gz = cg.ny > 1 ? cg.nz : 1;
+            for (int bz = 0; bz < gz; ++bz)
+                for (int by = 0; by < gy; ++by)
+                    for (int bx = 0; bx < gx; ++bx) tasks.push_back(BTask{it, 0, bx, by, bz, 0, 0});
+        }
+        if (tasks.empty()) continue;
+        if (int rc = ensure_tables(tasks.size(), sizeof(BCoarsen) * items.size(), 0)) return rc;
+        // the previous level's launch may still read the tables: wait before rewriting them
+        BCK(cudaStreamSynchronize(s));
+        std::memcpy(g_setup.hitems, items.data(), sizeof(BCoarsen) * items.size());
+        BCK(cudaMemcpyAsync(g_setup.ditems, g_setup.hitems, sizeof(BCoarsen) * items.size(), cudaMemcpyHostToDevice,
+                            s));
+        BCK(cudaMemcpyAsync(g_setup.dtask, tasks.data(), sizeof(BTask) * tasks.size(), cudaMemcpyHostToDevice, s));
+        count_launches(1);
+        kb_coarsen<<<(unsigned)tasks.size(), dim3(32, 8), 0, s>>>(g_setup.dtask, (const BCoarsen*)g_setup.ditems);
+        BCK(cudaGetLastError());
+    }
+    BCK(cudaStreamSynchronize(s));
+    for (lm_grid* g : todo) {
+        g->mg_built = true;
+        if (g->mg.back().ainv) g->inv_pending = true;
+    }
+    return LM_OK;
+}
+
 }  // namespace
 
 void lm::batch_forget_grid(const lm_grid* g) { drop_plans_of(g); }
@@ -685,9 +1027,51 @@ int lm_autotune_set_cache(const char* path) {
     return LM_OK;
 }
 
+int lm_batch_set_coefficients(lm_grid* const* grids, int count, const double* const* rho_old,
+                              const double* const* rho_new, const double* const* cs2, const double* dt,
+                              void* stream) {
+    if (!grids || count < 1 || !rho_old || !rho_new || !cs2 || !dt) return LM_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (!grids[i] || !rho_old[i] || !rho_new[i] || !cs2[i]) return LM_ERR_INVALID_ARG;
+        if (!(dt[i] > 0.0 && std::isfinite(dt[i]))) return LM_ERR_NOT_POSITIVE;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_setup.mu);
+    std::vector<BTask> tasks;
+    for (int i = 0; i < count; ++i) {
+        const int nb = std::max(1, std::min(1024, hdiv(grids[i]->N, NT * 8)));
+        for (int b = 0; b < nb; ++b) tasks.push_back(BTask{i, 0, 0, 0, 0, b, nb});
+    }
+    if (int rc = ensure_tables(tasks.size(), sizeof(AsmArgs) * count, count)) return rc;
+    BCK(cudaStreamSynchronize(s));                 // an earlier call's launches may still read the tables
+    AsmArgs* h = (AsmArgs*)g_setup.hitems;
+    for (int i = 0; i < count; ++i) {
+        lm_grid* g = grids[i];
+        h[i] = asm_args(g->geo, rho_old[i], rho_new[i], cs2[i], dt[i], 0, g->h,
+                        Op64Out{g->ct, g->gx, g->gy, g->gz, g->dinv, g->ct32, g->rho32}, g->asm_fl);
+    }
+    const AsmArgs* dA = (const AsmArgs*)g_setup.ditems;
+    BCK(cudaMemcpyAsync(g_setup.ditems, h, sizeof(AsmArgs) * count, cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(g_setup.dtask, tasks.data(), sizeof(BTask) * tasks.size(), cudaMemcpyHostToDevice, s));
+    count_launches(3);
+    kb_asm_flags<<<hdiv(count, 64), 64, 0, s>>>(dA, count, nullptr, 0);
+    kb_assemble<<<(unsigned)tasks.size(), NT, 0, s>>>(g_setup.dtask, dA);
+    kb_asm_flags<<<hdiv(count, 64), 64, 0, s>>>(dA, count, g_setup.dflags, 1);
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(g_setup.hflags, g_setup.dflags, sizeof(AsmFlags) * count, cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    int worst = LM_OK;
+    for (int i = 0; i < count; ++i) {
+        const int rc = grid_finish_assembly(grids[i], g_setup.hflags[i], s);
+        if (rc && !worst) worst = rc;
+    }
+    return worst;
+}
+
 int lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* o, lm_solve_result* results) {
     if (!grids || count < 1 || !o || !results) return LM_ERR_INVALID_ARG;
-    if (!(o->rtol > 0.0) || o->inner_max_iter < 1 || o->max_outer < 1 || o->nu1 != 1 || o->nu2 != 1)
+    if (!(o->rtol > 0.0) || o->inner_max_iter < 1 || o->max_outer < 1 || o->nu1 < 1 || o->nu2 < 1 || o->nu1 > 8 ||
+        o->nu2 > 8)
         return LM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)o->cuda_stream;
     for (int i = 0; i < count; ++i) {
@@ -703,6 +1087,9 @@ int lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* o, lm_
         for (int j = 0; j < i; ++j)
             if (grids[j] == g) return LM_ERR_INVALID_ARG;
     }
+    // grids whose coefficients changed since their hierarchy was built: the
+    // coarse coefficients of all of them, one launch per level
+    if (int rc = batch_refresh(grids, count, s)) return rc;
     for (int i = 0; i < count; ++i) {
         const int rc = grid_build_mg(grids[i], s, true);
         if (rc) return rc;
@@ -726,7 +1113,7 @@ int lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* o, lm_
         bool pending = false;
         for (int i = 0; i < count; ++i) pending = pending || grids[i]->inv_pending;
         if (pending) {
-            launch_coarse_inverse_many(P->dinv_items, P->dinv_tasks, P->n_inv_tasks, s);
+            launch_coarse_inverse_grids(P->dinv_items, count, s);
             BCK(cudaGetLastError());
             for (int i = 0; i < count; ++i) grids[i]->inv_pending = false;
         }
@@ -746,11 +1133,12 @@ int lm_batch_solve(lm_grid* const* grids, int count, const lm_solve_opts* o, lm_
     for (;;) {
         BCK(cudaMemcpyAsync(P->hgather, P->dgather, sizeof(SolveState) * 2 * count, cudaMemcpyDeviceToHost, s));
         BCK(cudaStreamSynchronize(s));
+        if (outer > 0) count_launches(P->n_step + P->n_iter * (long long)*P->hinner);
         bool all = true;
         for (int i = 0; i < count; ++i) all = all && P->hgather[i].done;
         if (all || outer >= o->max_outer) break;
         BCK(cudaGraphLaunch(P->g_step, s));
-        count_launches(P->n_step);
+        BCK(cudaMemcpyAsync(P->hinner, P->dinner, sizeof(int), cudaMemcpyDeviceToHost, s));
         ++outer;
     }
     BCK(cudaEventRecord(e1, s));

@@ -531,20 +531,7 @@ __global__ void __launch_bounds__(NT) k_axpy_ratio32(int N, const double* __rest
 // Mean of the children's c~ and rho (coarse coefficients); one thread per coarse cell.
 __global__ void __launch_bounds__(256) k_coarsen(Lev32 F, Geo C, int hx, int hy, int hz, float* __restrict__ ct_c,
                                                  float* __restrict__ rho_c) {
-    int I, J, K;
-    if (!map_cell(C, blockIdx.x, blockIdx.y, blockIdx.z, I, J, K)) return;
-    float sc = 0.f, sr = 0.f;
-    for (int c = 0; c <= hz; ++c)
-        for (int b = 0; b <= hy; ++b)
-            for (int a = 0; a <= hx; ++a) {
-                const int idx = ((I << hx) + a) + F.g.nx * (((J << hy) + b) + F.g.ny * ((K << hz) + c));
-                sc += F.ct[idx];
-                sr += F.rho[idx];
-            }
-    const float inv = 1.f / (float)((1 << hx) << hy << hz);
-    const int t = I + C.nx * (J + C.ny * K);
-    ct_c[t] = sc * inv;
-    rho_c[t] = sr * inv;
+    coarsen_cell(F, C, hx, hy, hz, ct_c, rho_c, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 __global__ void __launch_bounds__(256) k_resid_restrict(Lev32 F, Geo C, int hx, int hy, int hz,
@@ -1222,6 +1209,94 @@ __global__ void __launch_bounds__(256) k_coarse_inverse_many(const CoarseInv* __
     coarse_inverse_row(it.L, it.ainv, t & 255);
 }
 
+// The whole inverse of one grid's dense coarsest operator (n <= 64) in one
+// block: the factorisation of coarse_inverse_row done once, then thread t
+// solves L y = e_t (y_i = 0 above row t) and L^T z = y for column t of A^-1
+// (= row t, A^-1 being symmetric).  For many grids at once this does 1/n of
+// the per-row kernel's float64 factorisation work.
+constexpr size_t COARSE_INV_SMEM = sizeof(double) * (2 * 64 * 64 + 64) + sizeof(int) * (64 * 65 / 2);
+__device__ __forceinline__ void coarse_inverse_block(const Lev32& L, float* __restrict__ ainv) {
+    extern __shared__ double cinv_smem[];           // COARSE_INV_SMEM bytes
+    double* A = cinv_smem;
+    double* Y = A + 64 * 64;                        // Y[i * 64 + t]: entry i of thread t's column
+    double* rinv = Y + 64 * 64;
+    int* tri = reinterpret_cast<int*>(rinv + 64);
+    const Geo& g = L.g;
+    const int n = g.N, tid = threadIdx.x;
+    for (int e = tid; e < n * n; e += blockDim.x) {
+        A[e] = 0.0;
+        const int i = e / n, j = e - i * n;
+        if (i >= j) tri[(n - 1 - j) * (n - j) / 2 + (i - j)] = (i << 8) | j;
+    }
+    __syncthreads();
+    if (tid < n) {
+        const int idx = tid;
+        const int i = idx % g.nx, j = (idx / g.nx) % g.ny, k = idx / (g.nx * g.ny);
+        const double rc = L.rho[idx];
+        double d = L.ct[idx];
+        auto add = [&](bool has, int nb, float c2) {
+            if (!has) return;
+            const double w = (double)c2 / (rc + (double)L.rho[nb]);
+            d += w;
+            A[idx * n + nb] -= w;
+        };
+        Nbr nb = nbr_x(idx, i, g);
+        add(face_minus(i, g.nx, g.bcx), nb.im, L.c2x);
+        add(face_plus(i, g.nx, g.bcx), nb.ip, L.c2x);
+        nb = nbr_y(idx, j, g);
+        add(face_minus(j, g.ny, g.bcy), nb.im, L.c2y);
+        add(face_plus(j, g.ny, g.bcy), nb.ip, L.c2y);
+        nb = nbr_z(idx, k, g);
+        add(face_minus(k, g.nz, g.bcz), nb.im, L.c2z);
+        add(face_plus(k, g.nz, g.bcz), nb.ip, L.c2z);
+        A[idx * n + idx] += d;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {                   // right-looking Cholesky, as in coarse_inverse_row
+        const int i = k + tid;
+        if (i < n) {
+            const double p = A[k * n + k];
+            const float pf = (float)p;
+            double r;
+            if (pf > 1e-30f && pf < 1e30f) {
+                const double r0 = (double)rsqrtf(pf);
+                r = r0 * fma(-0.5 * p * r0, r0, 1.5);
+            } else {
+                r = 1.0 / sqrt(p);
+            }
+            if (i == k) rinv[k] = r;
+            else A[i * n + k] *= r;
+        }
+        __syncthreads();
+        const int m = n - 1 - k;
+        for (int e = tid; e < m * (m + 1) / 2; e += blockDim.x) {
+            const int t = tri[e], ti = t >> 8, tj = t & 255;
+            A[ti * n + tj] -= A[ti * n + k] * A[tj * n + k];
+        }
+        __syncthreads();
+    }
+    if (tid < n) {
+        const int t = tid;
+        for (int i = t; i < n; ++i) {               // L y = e_t
+            double sum = i == t ? 1.0 : 0.0;
+            for (int j = t; j < i; ++j) sum -= A[i * n + j] * Y[j * 64 + t];
+            Y[i * 64 + t] = sum * rinv[i];
+        }
+        for (int i = n - 1; i >= 0; --i) {          // L^T z = y (z over y, in place)
+            double sum = i >= t ? Y[i * 64 + t] : 0.0;
+            for (int j = i + 1; j < n; ++j) sum -= A[j * n + i] * Y[j * 64 + t];
+            Y[i * 64 + t] = sum * rinv[i];
+        }
+        for (int i = 0; i < n; ++i) ainv[t * n + i] = (float)Y[i * 64 + t];
+    }
+}
+
+// One block per grid: the inverses of many grids' coarsest levels.
+__global__ void __launch_bounds__(256) k_coarse_inverse_grids(const CoarseInv* __restrict__ items) {
+    const CoarseInv& it = items[blockIdx.x];
+    coarse_inverse_block(it.L, it.ainv);
+}
+
 __global__ void k_coarse_solve(int n, const float* __restrict__ ainv, const float* __restrict__ f,
                                float* __restrict__ x) {
     coarse_solve_block(n, ainv, f, x);
@@ -1700,6 +1775,12 @@ void launch_coarse_inverse_many(const CoarseInv* items, const int* task, int nta
     if (ntask <= 0) return;
     count_launches(1);
     k_coarse_inverse_many<<<ntask, 256, 0, s>>>(items, task);
+}
+void launch_coarse_inverse_grids(const CoarseInv* items, int count, cudaStream_t s) {
+    if (count <= 0) return;
+    cudaFuncSetAttribute(k_coarse_inverse_grids, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COARSE_INV_SMEM);
+    count_launches(1);
+    k_coarse_inverse_grids<<<count, 256, COARSE_INV_SMEM, s>>>(items);
 }
 void launch_coarse_inverse(const Lev32& L, cudaStream_t s, float* ainv) {
     count_launches(1);

@@ -15,63 +15,8 @@ namespace lm {
 
 // ---- coefficient assembly (step (v); Eqs. cpoiss, kappapoiss) -------------
 
-__global__ void __launch_bounds__(NT) k_assemble(Geo g, const double* __restrict__ a_in,
-                                                 const double* __restrict__ rho_new,
-                                                 const double* __restrict__ cs2, double dt, int raw,
-                                                 double c2x, double c2y, double c2z, Op64Out out,
-                                                 AsmFlags* __restrict__ fl) {
-    const int stride = gridDim.x * blockDim.x;
-    unsigned long long rmax = 0ull, rmin = ~0ull;        // range of the valid rho^{n+1}
-    bool bad32 = false;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
-        const double rn = rho_new[idx];
-        double c;
-        bool ok = rn > 0.0 && isfinite(rn);
-        if (raw) {
-            c = a_in[idx];
-        } else {
-            const double ro = a_in[idx], c2 = cs2[idx];
-            ok = ok && ro > 0.0 && isfinite(ro) && c2 > 0.0 && isfinite(c2);
-            c = __drcp_rn((dt * dt) * ro * c2);                // Eq. cpoiss: 1/(...) rounded to nearest
-        }
-        ok = ok && c > 0.0 && isfinite(c);
-        if (!ok) atomicOr(&fl->bad, 1);
-        if (rn > 0.0 && isfinite(rn)) {
-            const unsigned long long b = (unsigned long long)__double_as_longlong(rn);
-            rmax = b > rmax ? b : rmax;
-            rmin = b < rmin ? b : rmin;
-        }
-        int i, j, k;
-        cell_coords(idx, g, i, j, k);
-        // g_f = kappa_f / h^2 with kappa_f = 2/(rho_L + rho_R) (Eq. kappapoiss, harmonic
-        // mean), evaluated as (2/h^2) * RN(1/(rho_L + rho_R)): a correctly rounded
-        // float64 reciprocal per face (cheaper than a division on GB300's float64
-        // pipe); exact scaling, so bit-identical to 2/(rho_L + rho_R)/h^2 when h is
-        // a power of two, within 2 ulp otherwise
-        const double gxm = face_minus(i, g.nx, g.bcx) ? c2x * __drcp_rn(rn + rho_new[nbr_x(idx, i, g).im]) : 0.0;
-        const double gym = face_minus(j, g.ny, g.bcy) ? c2y * __drcp_rn(rn + rho_new[nbr_y(idx, j, g).im]) : 0.0;
-        const double gzm = face_minus(k, g.nz, g.bcz) ? c2z * __drcp_rn(rn + rho_new[nbr_z(idx, k, g).im]) : 0.0;
-        out.ct[idx] = c;
-        out.gx[idx] = gxm;
-        out.gy[idx] = gym;
-        out.gz[idx] = gzm;
-        const float c32 = (float)c;
-        bad32 = bad32 || !(c32 > 0.f) || isinf(c32);
-        out.ct32[idx] = c32;
-        out.rho32[idx] = (float)rn;
-    }
-    // the block's range and float32 flag: one atomic per warp
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long a = __shfl_xor_sync(0xffffffffu, rmax, o), b = __shfl_xor_sync(0xffffffffu, rmin, o);
-        rmax = a > rmax ? a : rmax;
-        rmin = b < rmin ? b : rmin;
-    }
-    bad32 = __any_sync(0xffffffffu, bad32);
-    if ((threadIdx.x & 31) == 0) {
-        if (rmax) atomicMax(&fl->rho_max, rmax);
-        if (rmin != ~0ull) atomicMin(&fl->rho_min, rmin);
-        if (bad32) atomicOr(&fl->bad32, 1);
-    }
+__global__ void __launch_bounds__(NT) k_assemble(AsmArgs a) {
+    assemble_range(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 __global__ void __launch_bounds__(NT) k_scale32(int N, float* __restrict__ x, float scale) {
@@ -455,8 +400,7 @@ __global__ void __launch_bounds__(NT) k_set_fnorm(const double* part, int slot, 
 void launch_assemble(const Geo& g, int G, cudaStream_t s, const double* a_in, const double* rho_new,
                      const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, AsmFlags* fl) {
     count_launches(1);
-    k_assemble<<<G, NT, 0, s>>>(g, a_in, rho_new, cs2, dt, raw, 2.0 / (h[0] * h[0]), 2.0 / (h[1] * h[1]),
-                                2.0 / (h[2] * h[2]), out, fl);
+    k_assemble<<<G, NT, 0, s>>>(asm_args(g, a_in, rho_new, cs2, dt, raw, h, out, fl));
 }
 void launch_scale32(int N, int G, cudaStream_t s, float* x, float scale) {
     count_launches(1);

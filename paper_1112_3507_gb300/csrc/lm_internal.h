@@ -97,6 +97,9 @@ namespace lm {
 // multigrid hierarchy (idempotent); defer_inverse leaves the coarsest inverse
 // to the caller (inv_pending), which computes many grids' in one launch
 int grid_build_mg(lm_grid* g, cudaStream_t s, bool defer_inverse = false);
+// the end of an assembly (host): positivity verdict, float32 range of rho,
+// hierarchy invalidation; fl = the assembly's report, already on the host
+int grid_finish_assembly(lm_grid* g, const AsmFlags& fl, cudaStream_t s);
 void batch_forget_grid(const lm_grid* g);            // drop cached batch plans that use g
 int net_forward(lm_net* N, const float* x, float* y, int B, int H, int W, cudaStream_t s);
 int net_backward(lm_net* N, const float* gy, cudaStream_t s);

@@ -61,6 +61,24 @@ struct AsmFlags {
     int bad32;      // c~ overflows or underflows float32
 };
 
+// Everything the assembly of one grid reads and writes.
+struct AsmArgs {
+    Geo g;
+    const double* a_in;      // rho^n (or c~ when raw)
+    const double* rho_new;
+    const double* cs2;
+    double dt;
+    int raw;
+    double c2x, c2y, c2z;    // 2 / h^2 per axis
+    Op64Out out;
+    AsmFlags* fl;
+};
+inline AsmArgs asm_args(const Geo& g, const double* a_in, const double* rho_new, const double* cs2, double dt,
+                        int raw, const double h[3], const Op64Out& out, AsmFlags* fl) {
+    return AsmArgs{g, a_in, rho_new, cs2, dt, raw, 2.0 / (h[0] * h[0]), 2.0 / (h[1] * h[1]), 2.0 / (h[2] * h[2]),
+                   out, fl};
+}
+
 // fp64
 void launch_assemble(const Geo& g, int G, cudaStream_t s, const double* a_in, const double* rho_new,
                      const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, AsmFlags* fl);
@@ -148,6 +166,8 @@ struct CoarseInv {
 };
 // rows (task & 255) of items[task >> 8] for every task: many grids' inverses in one launch
 void launch_coarse_inverse_many(const CoarseInv* items, const int* task, int ntask, cudaStream_t s);
+// one block per item: each grid's whole inverse (the factorisation done once per grid)
+void launch_coarse_inverse_grids(const CoarseInv* items, int count, cudaStream_t s);
 void launch_coarse_solve(int n, cudaStream_t s, const float* ainv, const float* f, float* x);
 
 }  // namespace lm

@@ -31,6 +31,70 @@ __device__ __forceinline__ double apply64_at(int idx, const Geo& g, const Op64& 
     return y;
 }
 
+// Coefficient assembly (step (v); Eqs. cpoiss, kappapoiss) of the cells
+// start, start + stride, ... of one grid, with the range of rho^{n+1} and
+// the failure flags reduced per warp into a.fl (every lane of a warp must
+// call this; the launches use whole warps).
+__device__ __forceinline__ void assemble_range(const AsmArgs& a, int start, int stride) {
+    const Geo& g = a.g;
+    const double *a_in = a.a_in, *rho_new = a.rho_new, *cs2 = a.cs2;
+    const double dt = a.dt, c2x = a.c2x, c2y = a.c2y, c2z = a.c2z;
+    const int raw = a.raw;
+    const Op64Out& out = a.out;
+    AsmFlags* fl = a.fl;
+    unsigned long long rmax = 0ull, rmin = ~0ull;        // range of the valid rho^{n+1}
+    bool bad32 = false;
+    for (int idx = start; idx < g.N; idx += stride) {
+        const double rn = rho_new[idx];
+        double c;
+        bool ok = rn > 0.0 && isfinite(rn);
+        if (raw) {
+            c = a_in[idx];
+        } else {
+            const double ro = a_in[idx], c2 = cs2[idx];
+            ok = ok && ro > 0.0 && isfinite(ro) && c2 > 0.0 && isfinite(c2);
+            c = __drcp_rn((dt * dt) * ro * c2);                // Eq. cpoiss: 1/(...) rounded to nearest
+        }
+        ok = ok && c > 0.0 && isfinite(c);
+        if (!ok) atomicOr(&fl->bad, 1);
+        if (rn > 0.0 && isfinite(rn)) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(rn);
+            rmax = b > rmax ? b : rmax;
+            rmin = b < rmin ? b : rmin;
+        }
+        int i, j, k;
+        cell_coords(idx, g, i, j, k);
+        // g_f = kappa_f / h^2 with kappa_f = 2/(rho_L + rho_R) (Eq. kappapoiss, harmonic
+        // mean), evaluated as (2/h^2) * RN(1/(rho_L + rho_R)): a correctly rounded
+        // float64 reciprocal per face (cheaper than a division on GB300's float64
+        // pipe); exact scaling, so bit-identical to 2/(rho_L + rho_R)/h^2 when h is
+        // a power of two, within 2 ulp otherwise
+        const double gxm = face_minus(i, g.nx, g.bcx) ? c2x * __drcp_rn(rn + rho_new[nbr_x(idx, i, g).im]) : 0.0;
+        const double gym = face_minus(j, g.ny, g.bcy) ? c2y * __drcp_rn(rn + rho_new[nbr_y(idx, j, g).im]) : 0.0;
+        const double gzm = face_minus(k, g.nz, g.bcz) ? c2z * __drcp_rn(rn + rho_new[nbr_z(idx, k, g).im]) : 0.0;
+        out.ct[idx] = c;
+        out.gx[idx] = gxm;
+        out.gy[idx] = gym;
+        out.gz[idx] = gzm;
+        const float c32 = (float)c;
+        bad32 = bad32 || !(c32 > 0.f) || isinf(c32);
+        out.ct32[idx] = c32;
+        out.rho32[idx] = (float)rn;
+    }
+    // the block's range and float32 flag: one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, rmax, o), b = __shfl_xor_sync(0xffffffffu, rmin, o);
+        rmax = a > rmax ? a : rmax;
+        rmin = b < rmin ? b : rmin;
+    }
+    bad32 = __any_sync(0xffffffffu, bad32);
+    if ((threadIdx.x & 31) == 0) {
+        if (rmax) atomicMax(&fl->rho_max, rmax);
+        if (rmin != ~0ull) atomicMin(&fl->rho_min, rmin);
+        if (bad32) atomicOr(&fl->bad32, 1);
+    }
+}
+
 // ---- float32 operator -------------------------------------------------------
 // g = (2/h^2) / (rho_a + rho_b); the sum is commutative, so both cells of a
 // face compute the same bits and the operator stays exactly symmetric.
@@ -156,6 +220,27 @@ __device__ __forceinline__ bool map_cell(const Geo& g, int bx, int by, int bz, i
         k = by * 8 + threadIdx.y;
     }
     return i < g.nx && j < g.ny && k < g.nz;
+}
+
+// Coarse c~ and rho of the coarse cell a thread of block (bx, by, bz) of a
+// (32, 8) block maps to (map_cell): the means over its children.
+__device__ __forceinline__ void coarsen_cell(const Lev32& F, const Geo& C, int hx, int hy, int hz,
+                                             float* __restrict__ ct_c, float* __restrict__ rho_c, int bx, int by,
+                                             int bz) {
+    int I, J, K;
+    if (!map_cell(C, bx, by, bz, I, J, K)) return;
+    float sc = 0.f, sr = 0.f;
+    for (int c = 0; c <= hz; ++c)
+        for (int b = 0; b <= hy; ++b)
+            for (int a = 0; a <= hx; ++a) {
+                const int idx = ((I << hx) + a) + F.g.nx * (((J << hy) + b) + F.g.ny * ((K << hz) + c));
+                sc += F.ct[idx];
+                sr += F.rho[idx];
+            }
+    const float inv = 1.f / (float)((1 << hx) << hy << hz);
+    const int t = I + C.nx * (J + C.ny * K);
+    ct_c[t] = sc * inv;
+    rho_c[t] = sr * inv;
 }
 
 __device__ __forceinline__ float apply32_at(int idx, int i, int j, int k, const Lev32& L,
@@ -662,11 +747,24 @@ __device__ __forceinline__ void zm2d_tile(const Lev32& L, const float* __restric
             }
         }
     };
+    // L2 prefetch of the tile's row segments (256 cells, contiguous) PF_PLANES
+    // steps ahead: x and rho of row P are fetched at step P - 2, f and c~ of
+    // row P first read at step P - 1; array a = 0..3 by thread a
+    auto prefetch = [&](int a, int P) {
+        if (P > (a < 2 ? k1 + 1 : k1) || (ZERO && a == 0)) return;
+        const int zo = zoff(P);
+        if (zo < 0) return;
+        const float* base = a == 0 ? xin : a == 1 ? L.rho : a == 2 ? f : L.ct;
+        prefetch_l2(base + zo + i0, TX * sizeof(float));
+    };
+    if (tid < 4)
+        for (int d = 1; d <= PF_PLANES; ++d) prefetch(tid, (tid < 2 ? k0 : k0 - 1) + d);
     load_a(k0 - 1, z0, true);
     float fb = 0.f, cb = 1.f;
     bool okB = false;
     int eB = 0;
     for (int p = k0 - 1; p <= k1 + 1; ++p) {
+        if (tid < 4) prefetch(tid, (tid < 2 ? p + 2 : p + 1) + PF_PLANES);
         if (p <= k1) store(op1);
         if (p + 1 <= k1) fetch(z2, zp2);
         float fA[QA], cA[QA];

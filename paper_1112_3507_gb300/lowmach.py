@@ -98,6 +98,9 @@ _SIGNATURES = {
     "lm_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(SolveOpts),
                                        ctypes.POINTER(SolveResult)]),
     "lm_autotune_set_cache": (ctypes.c_int, [ctypes.c_char_p]),
+    "lm_batch_set_coefficients": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
+                                                  ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                                  ctypes.POINTER(ctypes.c_double), _P]),
     "lm_halo_pack": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                      _P, ctypes.c_int, _P]),
     "lm_vec_axpby": (ctypes.c_int, [ctypes.c_int64, ctypes.c_double, _P, ctypes.c_int, ctypes.c_double, _P,
@@ -414,13 +417,30 @@ def autotune_set_cache(path=None):
     return _check(lib().lm_autotune_set_cache(path.encode() if path else None), "lm_autotune_set_cache")
 
 
+def batch_set_coefficients(grids, rho_old, rho_new, cs2, dts, stream=None):
+    """lm_batch_set_coefficients: lists (one entry per grid) of CUDA float64 tensors and host dt values."""
+    n = len(grids)
+    ptrs = []
+    for arrs in (rho_old, rho_new, cs2):
+        row = []
+        for g, t in zip(grids, arrs):
+            p, on_dev, keep = _field(t, g.N)
+            if not on_dev:
+                raise ValueError("lm_batch_set_coefficients takes device tensors")
+            row.append(p.value)
+        ptrs.append((_P * n)(*row))
+    handles = (_P * n)(*[g._g for g in grids])
+    dt = (ctypes.c_double * n)(*[float(v) for v in dts])
+    return _check(lib().lm_batch_set_coefficients(handles, n, ptrs[0], ptrs[1], ptrs[2], dt, _stream_ptr(stream)),
+                  "lm_batch_set_coefficients")
+
+
 def batch_solve(grids, rtol=1e-8, stream=None, allow=(LM_OK,), **kw):
     """lm_batch_solve over a list of Grid objects; returns one result dict per grid."""
     o = SolveOpts()
     lib().lm_default_opts(ctypes.byref(o))
     o.mode = MIXED_MG_IR
     o.rtol = float(rtol)
-    o.nu1 = o.nu2 = 1          # the batched schedule runs one sweep before and after each coarse correction
     o.inner_rtol = 1e-3
     for k, v in kw.items():
         if not hasattr(o, k):

@@ -116,7 +116,105 @@ def test_batch_rejects_bad_inputs(lm):
             lm.batch_solve([g2, g2])
         assert e.value.code == lm.LM_ERR_INVALID_ARG
         with pytest.raises(lm.LowMachError):
-            lm.batch_solve([g2], nu1=2, nu2=2)
+            lm.batch_solve([g2], nu1=0, nu2=2)
+        with pytest.raises(lm.LowMachError):
+            lm.batch_solve([g2], nu1=2, nu2=9)
     finally:
         g2.close()
         g3.close()
+
+
+@pytest.mark.parametrize("nu", [(2, 3), (1, 2), (3, 1)])
+def test_batch_any_smoothing_counts(lm, tmp_path, nu):
+    """The library's default smoothing (nu1 = 2, nu2 = 3) and other counts in
+    the batched V-cycle: solutions match the direct solves; the one-block
+    coarse cycles and the whole-row sweeps take the same counts."""
+    lm.autotune_set_cache(str(tmp_path / "t.json"))
+    problems = I.config_batch(count=5, seed=7, scale=4)
+    grids = _batch(lm, problems)
+    try:
+        res = lm.batch_solve(grids, rtol=1e-11, max_outer=12, inner_max_iter=12, nu1=nu[0], nu2=nu[1])
+        for p, g, r in zip(problems, grids, res):
+            assert r["status"] == 0 and r["rel_residual"] <= 1e-11, r
+            op = P.operator_from_problem(p)
+            xs = P.solve_direct(op, p.f).ravel()
+            assert np.linalg.norm(g.solution() - xs) <= 1e-8 * np.linalg.norm(xs), p.name
+    finally:
+        for g in grids:
+            g.close()
+
+
+def test_batch_set_coefficients_matches_per_grid(lm):
+    """lm_batch_set_coefficients (one launch for all grids) leaves every grid
+    with the coefficients lm_set_coefficients gives, bit for bit; a grid with
+    a non-positive density is reported and left without coefficients."""
+    problems = I.config_batch(count=6, seed=11, scale=8)
+    ga, gb = _batch(lm, problems), [lm.Grid.for_problem(p) for p in problems]
+    try:
+        tens = [[torch.as_tensor(a.ravel(), device="cuda") for a in (p.rho_old, p.rho_new, p.cs2)] for p in problems]
+        lm.batch_set_coefficients(gb, [t[0] for t in tens], [t[1] for t in tens], [t[2] for t in tens],
+                                  [p.dt for p in problems])
+        for a, b in zip(ga, gb):
+            for x, y in zip(a.coefficients(), b.coefficients()):
+                assert torch.equal(x, y)
+        bad = [t[1].clone() for t in tens]
+        bad[2][5] = -1.0
+        with pytest.raises(lm.LowMachError) as e:
+            lm.batch_set_coefficients(gb, [t[0] for t in tens], bad, [t[2] for t in tens], [p.dt for p in problems])
+        assert e.value.code == lm.LM_ERR_NOT_POSITIVE
+        with pytest.raises(lm.LowMachError) as e:
+            gb[2].coefficients()
+        assert e.value.code == lm.LM_ERR_STATE
+        gb[0].coefficients()                       # the other grids were assembled
+    finally:
+        for g in ga + gb:
+            g.close()
+
+
+def test_batch_refresh_after_new_coefficients(lm, tmp_path):
+    """Solve, assemble new coefficients for every grid in one launch, solve
+    again: the hierarchies are refreshed level by level over all grids and
+    the coarsest inverses one block per grid; both solves match the oracle."""
+    lm.autotune_set_cache(str(tmp_path / "t.json"))
+    first = I.config_batch(count=5, seed=13, scale=8)
+    second = I.config_batch(count=5, seed=14, scale=8)
+    shapes = [p.n for p in first]
+    second = [I.make_problem(p.n[0], p.n[2], ma=q.ma if q.ma else 0.01, contrast=12.0, noise=0.01, seed=60 + i)
+              for i, (p, q) in enumerate(zip(first, second))]
+    assert [p.n for p in second] == shapes
+    grids = _batch(lm, first)
+    try:
+        for probs in (first, second):
+            tens = [[torch.as_tensor(a.ravel(), device="cuda") for a in (p.rho_old, p.rho_new, p.cs2, p.f)]
+                    for p in probs]
+            lm.batch_set_coefficients(grids, [t[0] for t in tens], [t[1] for t in tens], [t[2] for t in tens],
+                                      [p.dt for p in probs])
+            for g, t in zip(grids, tens):
+                g.set_rhs(t[3])
+            res = lm.batch_solve(grids, rtol=1e-11, max_outer=12, inner_max_iter=12)
+            for p, g, r in zip(probs, grids, res):
+                assert r["status"] == 0, r
+                xs = P.solve_direct(P.operator_from_problem(p), p.f).ravel()
+                assert np.linalg.norm(g.solution() - xs) <= 1e-8 * np.linalg.norm(xs)
+    finally:
+        for g in grids:
+            g.close()
+
+
+def test_batch_full_size_1024_grid_matches_oracle(lm, tmp_path):
+    """A 1024 x 1024 grid of the 64-solve workload's largest size class,
+    batched with smaller ones, against the oracle's direct solve."""
+    lm.autotune_set_cache(str(tmp_path / "t.json"))
+    problems = [I.make_problem(1024, 1024, ma=0.003, contrast=20.0, noise=0.01, seed=71, rtol=1e-8),
+                I.make_problem(256, 512, ma=0.05, contrast=8.0, noise=0.01, seed=72, rtol=1e-8),
+                I.make_problem(128, 128, ma=0.001, contrast=30.0, noise=0.01, seed=73, rtol=1e-8)]
+    grids = _batch(lm, problems)
+    try:
+        res = lm.batch_solve(grids, rtol=1e-11, max_outer=12, inner_max_iter=15)
+        for p, g, r in zip(problems, grids, res):
+            assert r["status"] == 0 and r["rel_residual"] <= 1e-11, r
+            xs = P.solve_direct(P.operator_from_problem(p), p.f).ravel()
+            assert np.linalg.norm(g.solution() - xs) <= 1e-8 * np.linalg.norm(xs), p.name
+    finally:
+        for g in grids:
+            g.close()
