@@ -472,8 +472,11 @@ struct lm_net {
     float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     bf16 *wb = nullptr, *wt = nullptr;   // BF16 weights and their flipped transposes
     // activations (bf16) and gradients (float) for batch x H x W
-    int B = 0, H = 0, W = 0;
-    std::vector<void*> bufs;
+    int B = 0, H = 0, W = 0;        // the shape the buffers hold (B images at most)
+    int Bf = 0;                     // images of the last forward pass
+    std::vector<void*> bufs;        // forward activations (inference)
+    std::vector<void*> gbufs;       // gradient buffers, allocated on the first backward pass
+    bool grads_ready = false;
     bf16 *x = nullptr, *in_[4] = {}, *a1[4] = {}, *e[4] = {}, *cat[3] = {}, *da1[3] = {}, *d[3] = {};
     float* y = nullptr;
     float *gd0 = nullptr, *gbuf1 = nullptr, *gbuf2 = nullptr, *genc[4] = {}, *gdl[4] = {};
@@ -499,14 +502,46 @@ int blocks_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 1
 
 void free_acts(lm_net* N) {
     for (void* p : N->bufs) cudaFree(p);
+    for (void* p : N->gbufs) cudaFree(p);
     N->bufs.clear();
+    N->gbufs.clear();
+    N->grads_ready = false;
     N->B = N->H = N->W = 0;
 }
 
 template <class T>
-int nalloc(lm_net* N, T** p, size_t count) {
+int nalloc(lm_net* N, T** p, size_t count, bool grad = false) {
     NCK(cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)));
-    N->bufs.push_back(*p);
+    (grad ? N->gbufs : N->bufs).push_back(*p);
+    return LM_OK;
+}
+
+// The backward pass's buffers for the current batch shape (only training
+// needs them: an inference of a 512^3 grid as 512 images would otherwise
+// hold several times its activations in gradients).
+int ensure_grads(lm_net* N) {
+    if (N->grads_ready) return LM_OK;
+    int rc;
+    const size_t P0 = (size_t)N->B * N->H * N->W;
+    for (int l = 0; l < 4; ++l) {
+        const size_t Pl = P0 >> (2 * l);
+        const int cl = N->ch[l];
+        if ((rc = nalloc(N, &N->genc[l], Pl * cl, true)) || (rc = nalloc(N, &N->gdl[l], Pl * cl, true))) return rc;
+    }
+    size_t gmax = 0;
+    for (int l = 0; l < 4; ++l) {
+        const size_t Pl = P0 >> (2 * l);
+        gmax = std::max(gmax, Pl * (size_t)(N->ch[l] + (l < 3 ? N->ch[l + 1] : 0)));
+        gmax = std::max(gmax, Pl * (size_t)(l == 0 ? N->cin : N->ch[l - 1]));
+    }
+    if ((rc = nalloc(N, &N->gd0, P0 * N->ch[0], true)) || (rc = nalloc(N, &N->gbuf1, gmax, true)) ||
+        (rc = nalloc(N, &N->gbuf2, gmax, true)) || (rc = nalloc(N, &N->gbf, gmax, true)))
+        return rc;
+    N->part_n = 0;
+    for (const auto& c : N->convs) N->part_n = std::max(N->part_n, (size_t)9 * c.cin * c.cout);
+    N->part_n *= 256;   // up to 256 pixel groups
+    if ((rc = nalloc(N, &N->part, N->part_n, true))) return rc;
+    N->grads_ready = true;
     return LM_OK;
 }
 
@@ -520,9 +555,7 @@ int ensure_acts(lm_net* N, int B, int H, int W) {
         const size_t Pl = P0 >> (2 * l);
         const int cl = N->ch[l], cprev = l == 0 ? N->cin : N->ch[l - 1];
         if (l > 0 && (rc = nalloc(N, &N->in_[l], Pl * cprev))) return rc;
-        if ((rc = nalloc(N, &N->a1[l], Pl * cl)) || (rc = nalloc(N, &N->e[l], Pl * cl)) ||
-            (rc = nalloc(N, &N->genc[l], Pl * cl)) || (rc = nalloc(N, &N->gdl[l], Pl * cl)))
-            return rc;
+        if ((rc = nalloc(N, &N->a1[l], Pl * cl)) || (rc = nalloc(N, &N->e[l], Pl * cl))) return rc;
         if (l < 3) {
             const int cc = N->ch[l + 1] + cl;
             if ((rc = nalloc(N, &N->cat[l], Pl * cc)) || (rc = nalloc(N, &N->da1[l], Pl * cl)) ||
@@ -531,19 +564,7 @@ int ensure_acts(lm_net* N, int B, int H, int W) {
         }
     }
     N->in_[0] = N->x;
-    size_t gmax = 0;
-    for (int l = 0; l < 4; ++l) {
-        const size_t Pl = P0 >> (2 * l);
-        gmax = std::max(gmax, Pl * (size_t)(N->ch[l] + (l < 3 ? N->ch[l + 1] : 0)));
-        gmax = std::max(gmax, Pl * (size_t)(l == 0 ? N->cin : N->ch[l - 1]));
-    }
-    if ((rc = nalloc(N, &N->y, P0)) || (rc = nalloc(N, &N->gd0, P0 * N->ch[0])) || (rc = nalloc(N, &N->gbuf1, gmax)) ||
-        (rc = nalloc(N, &N->gbuf2, gmax)) || (rc = nalloc(N, &N->gbf, gmax)))
-        return rc;
-    N->part_n = 0;
-    for (const auto& c : N->convs) N->part_n = std::max(N->part_n, (size_t)9 * c.cin * c.cout);
-    N->part_n *= 256;   // up to 256 pixel groups
-    if ((rc = nalloc(N, &N->part, N->part_n))) return rc;
+    if ((rc = nalloc(N, &N->y, P0))) return rc;
     N->B = B;
     N->H = H;
     N->W = W;
@@ -598,6 +619,7 @@ int net_forward(lm_net* N, const float* xin, float* yout, int B, int H, int W, c
     if (H % 8 || W % 8 || B < 1) return LM_ERR_INVALID_ARG;
     int rc = ensure_acts(N, B, H, W);
     if (rc) return rc;
+    N->Bf = B;
     const long long P0 = (long long)B * H * W;
     count_launches(1);
     k_to_bf16<<<blocks_for(P0 * N->cin), 256, 0, s>>>(xin, N->x, P0 * N->cin);
@@ -630,7 +652,8 @@ int net_forward(lm_net* N, const float* xin, float* yout, int B, int H, int W, c
 }
 
 int net_backward(lm_net* N, const float* gy, cudaStream_t s) {
-    const int B = N->B, H = N->H, W = N->W;
+    if (int rc = ensure_grads(N)) return rc;
+    const int B = N->Bf, H = N->H, W = N->W;     // the images of the last forward pass
     const long long P0 = (long long)B * H * W;
     // flipped transposes of the current weights for the backward-data convolutions
     for (const auto& c : N->convs) {
@@ -786,23 +809,35 @@ __global__ void __launch_bounds__(NT) k_feat_sums(int N, const TV* __restrict__ 
     }
 }
 
+// Pixel of cell idx in the network's image batch: a grid of nx x ny x nz
+// cells is ny images (one per x-z slice j) of nz rows and nx columns, so a
+// 3D grid is read slice by slice by the 2D network; for a 2D grid (ny = 1)
+// the pixel index is the cell index.
+__device__ __forceinline__ int net_pixel(int idx, int nx, int ny, int nz) {
+    const int i = idx % nx, t = idx / nx, j = t % ny, k = t / ny;
+    return (j * nz + k) * nx + i;
+}
+
 template <typename TV>
 __global__ void k_feat(int N, const TV* __restrict__ v, const float* __restrict__ rho, const float* __restrict__ ct,
-                       const double* __restrict__ scal, float ihz2, float* __restrict__ feat) {
+                       const double* __restrict__ scal, float ihz2, float* __restrict__ feat, int nx, int ny, int nz) {
     const float irms = (float)scal[12], mrho = (float)scal[13];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const float r = rho[i];
-        feat[3 * i + 0] = (float)v[i] * irms;
-        feat[3 * i + 1] = logf(r / mrho);
-        feat[3 * i + 2] = 0.1f * logf(ihz2 / (ct[i] * r));
+        const int q = net_pixel(i, nx, ny, nz);
+        feat[3 * q + 0] = (float)v[i] * irms;
+        feat[3 * q + 1] = logf(r / mrho);
+        feat[3 * q + 2] = 0.1f * logf(ihz2 / (ct[i] * r));
     }
 }
 
-// out = s * y (precision of the destination)
+// out = s * y (precision of the destination), y in image order
 template <typename TO>
-__global__ void k_scale_out(int N, const float* __restrict__ y, const double* __restrict__ scal, TO* __restrict__ out) {
+__global__ void k_scale_out(int N, const float* __restrict__ y, const double* __restrict__ scal, TO* __restrict__ out,
+                            int nx, int ny, int nz) {
     const double s = scal[14];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) out[i] = (TO)(s * y[i]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        out[i] = (TO)(s * y[net_pixel(i, nx, ny, nz)]);
 }
 
 }  // namespace lm
@@ -816,7 +851,8 @@ int features(lm_grid* g, const TV* v, float* feat, cudaStream_t s) {
     k_feat_sums<TV><<<g->G, NT, 0, s>>>(g->N, v, g->rho32, g->ct32, 1.0 / g->rho_scale, red);
     // channel 2 is log(1/(c~ rho h^2)) of the true rho = rho_stored * rho_scale
     k_feat<TV><<<blocks_for(g->N), 256, 0, s>>>(g->N, v, g->rho32, g->ct32, g->scal,
-                                                (float)(1.0 / (g->h[2] * g->h[2]) / g->rho_scale), feat);
+                                                (float)(1.0 / (g->h[2] * g->h[2]) / g->rho_scale), feat, g->n[0],
+                                                g->n[1], g->n[2]);
     return cudaGetLastError() == cudaSuccess ? LM_OK : LM_ERR_CUDA;
 }
 
@@ -833,18 +869,21 @@ uint64_t fnv1a(const unsigned char* p, size_t n) {
 
 namespace lm {
 
-bool net_usable(const lm_grid* g) { return g->net && g->ndim == 2 && g->n[0] % 8 == 0 && g->n[2] % 8 == 0; }
+bool net_usable(const lm_grid* g) { return g->net && g->n[0] % 8 == 0 && g->n[2] % 8 == 0; }
 
-// dst = s * NN(features(v)) on grid g (2D), dst float or double
+// dst = s * NN(features(v)) on grid g, dst float or double: a 2D grid is one
+// image; a 3D grid is a batch of ny images, its x-z slices, through the same
+// 2D network (the network sees no coupling across y; the flexible-CG
+// iteration around it does)
 template <typename TV, typename TO>
 int net_apply(lm_grid* g, const TV* v, TO* dst, cudaStream_t s) {
     lm_net* N = g->net;
     int rc = features<TV>(g, v, g->feat, s);
     if (rc) return rc;
-    rc = net_forward(N, g->feat, g->nny, 1, g->n[2], g->n[0], s);
+    rc = net_forward(N, g->feat, g->nny, g->n[1], g->n[2], g->n[0], s);
     if (rc) return rc;
     count_launches(1);
-    k_scale_out<TO><<<blocks_for(g->N), 256, 0, s>>>(g->N, g->nny, g->scal, dst);
+    k_scale_out<TO><<<blocks_for(g->N), 256, 0, s>>>(g->N, g->nny, g->scal, dst, g->n[0], g->n[1], g->n[2]);
     return cudaGetLastError() == cudaSuccess ? LM_OK : LM_ERR_CUDA;
 }
 template int net_apply<double, double>(lm_grid*, const double*, double*, cudaStream_t);
@@ -967,7 +1006,6 @@ int lm_net_load(const char* path, lm_net** out) {
 int lm_net_features(lm_grid* g, const double* v, float* feat, double* scale, void* stream) {
     if (!g || !v || !feat) return LM_ERR_INVALID_ARG;
     if (!g->have_coefs) return LM_ERR_STATE;
-    if (g->ndim != 2) return LM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int rc = features<double>(g, v, feat, s);
     if (rc) return rc;

@@ -95,3 +95,49 @@ def test_training_gains_over_the_untrained_network(lm, untrained):
     print("energy-norm warm-start error (seed, trained, untrained):", got)
     assert all(et < eu for _, et, eu in got), got
     assert np.mean([et for _, et, _ in got]) < 0.9, got
+
+
+@pytest.mark.parametrize("make", [lambda: I.config_semiconvection_3d(32),
+                                  lambda: I.config_convection_3d(32, seed=3)])
+@pytest.mark.parametrize("net_precond", [0, 1])
+def test_learned_mixed_3d_matches_oracle(lm, make, net_precond):
+    """The learned mode on 3D grids (the two-component semiconvection recipe
+    of the 512^3 workload, downsized, and the convection recipe): the 2D
+    network runs on every x-z slice, its warm start enters the refinement
+    (the initial residual is that of the warm start, not of x = 0), and the
+    solution matches the oracle's to 1e-8."""
+    p = make()
+    op = P.operator_from_problem(p)
+    xs = P.solve_direct(op, p.f).ravel()
+    with lm.Grid.for_problem(p) as g:
+        g.set_problem(p)
+        g.load_network(WEIGHTS)
+        r = g.solve(mode="learned", rtol=1e-12, net_precond=net_precond, max_outer=30)
+        x = g.solution()
+        hist = g.residual_history()
+    assert r["status"] == 0 and r["rel_residual"] <= 1e-12
+    assert hist[0] != 1.0
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+def test_network_input_of_a_3d_grid_is_its_slices(lm):
+    """A 3D grid is ny images of its x-z slices: with two identical slices the
+    network input of each equals that of the 2D grid of one slice."""
+    import dataclasses
+    p2 = I.config_training_2d(30001, n=64)
+    rep = lambda a: np.repeat(a, 2, axis=1)                  # (nz, 1, nx) -> (nz, 2, nx)
+    p3 = dataclasses.replace(p2, n=(p2.n[0], 2, p2.n[2]), ndim=3, rho_old=rep(p2.rho_old), rho_new=rep(p2.rho_new),
+                             cs2=rep(p2.cs2), f=rep(p2.f))
+    out = {}
+    for p in (p2, p3):
+        with lm.Grid.for_problem(p) as g:
+            g.set_problem(p)
+            v = torch.as_tensor(p.f.ravel(), device="cuda")
+            feat = torch.empty(3 * p.size, dtype=torch.float32, device="cuda")
+            out[p.ndim] = (g.features(v, feat), feat.cpu().numpy())
+    s2, f2 = out[2]
+    s3, f3 = out[3]
+    assert s3 == pytest.approx(s2, rel=1e-12)
+    f3 = f3.reshape(2, p2.n[2], p2.n[0], 3)
+    np.testing.assert_allclose(f3[0], f2.reshape(p2.n[2], p2.n[0], 3), rtol=1e-6, atol=1e-6)
+    np.testing.assert_array_equal(f3[0], f3[1])
