@@ -366,6 +366,55 @@ int  lm_mg_prolong_add(lm_grid* g, const float* ec, float* x, void* stream);
  * NULL). */
 int  lm_mg_level_coefficients(lm_grid* g, int level, float* ct, float* rho, double* rho_scale, void* stream);
 
+/* ---- the steps either side of the solve (Sec. 2, steps (iv)-(viii)) ------- */
+/* One fractional step's pressure projection around lm_solve, float64.
+ * Vector fields (momenta) are three arrays of N values, x then y then z
+ * components, consecutive (the y component of a 2D grid is carried along
+ * unchanged); face arrays hold, per axis, each cell's minus face (the face
+ * with its -1 neighbour), 3N values.  Pressures at faces follow Eq. pbnd,
+ * cell gradients Eq. nablaP; on a wall axis (LM_BC_NEUMANN) the wall face
+ * has no velocity and the wall cell's pressure; periodic axes wrap.  n, h,
+ * bc: host arrays as in lm_grid_create; all fields device pointers. */
+
+/* f (Eq. fpoiss) = (P^n - dt u^n.grad P^n) / (dt^2 rho^n c_s^2) - div u* / dt
+ * - source, with u^n = mom_old / rho_old, u* on the faces = ((rho u)*_L +
+ * (rho u)*_R) / (rho^{n+1}_L + rho^{n+1}_R) (written to uface_star) and
+ * source the viscous and conductive part of Eq. fpoiss (NULL: inviscid).
+ * Then lm_set_coefficients(rho_old, rho_new, cs2_old, dt) and lm_set_rhs(f)
+ * pose Eq. Poiss for lm_solve. */
+int  lm_projection_rhs(int ndim, const int64_t n[3], const double h[3], const int bc[3], double dt,
+                       const double* p_old, const double* rho_old, const double* cs2_old, const double* mom_old,
+                       const double* mom_star, const double* rho_new, const double* source, double* f,
+                       double* uface_star, void* stream);
+
+/* With the predicted pressure p_pred (lm_get_solution): mom_new = mom_star -
+ * dt grad P (Eq. momupdate, rho^{n+1} in Eq. pbnd); uface_new = uface_star -
+ * dt (P_R - P_L)/h * 2/(rho_L + rho_R) (step (vii)); e_new = e_star - dt
+ * (P div u^{n+1} + u^{n+1}.grad P) (step (viii)), u^{n+1} = mom_new / rho_new.
+ * uface_new must not overlap uface_star; mom_new / e_new may alias mom_star
+ * / e_star. */
+int  lm_projection_update(int ndim, const int64_t n[3], const double h[3], const int bc[3], double dt,
+                          const double* p_pred, const double* rho_new, const double* mom_star,
+                          const double* uface_star, const double* e_star, double* mom_new, double* uface_new,
+                          double* e_new, void* stream);
+
+/* ---- the viscous terms' dissipative stencil (Sec. 4) --------------------- */
+
+/* out = beta u + alpha sum_a (U_aa): the dissipative fourth-order second
+ * derivative of Sec. 4 (face derivatives of Eq. fv-approach2 differenced,
+ * i.e. the five-point stencil of Eq. dissipativestencil4,
+ * (-U_{i-2} + 16 U_{i-1} - 30 U_i + 16 U_{i+1} - U_{i+2}) / (12 h^2)), summed
+ * over the axes with more than one cell (directional splitting).  A
+ * periodic axis wraps; a wall axis (LM_BC_NEUMANN) carries no flux through
+ * the wall (mirror ghosts U_{-1-k} = U_k).  With beta = 1, alpha = nu dt it
+ * is one explicit Euler step of u_t = nu Delta u, monotone while
+ * nu dt / h^2 <= 3 / (8 d) in d dimensions.  n, h, bc: host arrays as in
+ * lm_grid_create; u, out: device arrays of n[0]*n[1]*n[2] values of
+ * precision prec (LM_PREC_FP64 or LM_PREC_FP32), not overlapping.
+ * LM_ERR_INVALID_ARG for bad sizes, precision or aliasing. */
+int  lm_diffusion4(int ndim, const int64_t n[3], const double h[3], const int bc[3], int prec, double alpha,
+                   const void* u, double beta, void* out, void* stream);
+
 /* ---- measurement ---------------------------------------------------------- */
 
 /* Arithmetic-rate probe of the current device, the measured roof of the

@@ -15,6 +15,9 @@ Modules
              written level by level.
   unet       the learned warm start's network layers in float64 (forward and
              hand-derived backward).
+  diffusion  the dissipative fourth-order second-derivative stencil of the
+             viscous terms (Sec. 4, Eq. dissipativestencil4) in flux form,
+             and the non-dissipative nine-point stencil it replaces.
 
 Pins (what fixes each function to something other than itself) live in
 tests/test_oracle_*.py.  Functions whose result has no such pin say

@@ -338,6 +338,32 @@ __global__ void k_pool(const bf16* __restrict__ in, bf16* __restrict__ out, int 
     }
 }
 
+// k_pool on 8 channels at a time (C a multiple of 8): 16-byte loads and stores
+__global__ void k_pool8(const uint4* __restrict__ in, uint4* __restrict__ out, int B, int H, int Wd, int C8) {
+    const int Ho = H / 2, Wo = Wd / 2;
+    const long long n = (long long)B * Ho * Wo * C8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C8);
+        const long long q = i / C8;
+        const int xo = (int)(q % Wo);
+        const long long r = q / Wo;
+        const int yo = (int)(r % Ho), b = (int)(r / Ho);
+        const uint4* s = in + (((size_t)b * H + 2 * yo) * Wd + 2 * xo) * C8 + c;
+        const uint4 v[4] = {s[0], s[C8], s[(size_t)Wd * C8], s[(size_t)Wd * C8 + C8]};
+        uint4 o;
+        const bf16* a0 = reinterpret_cast<const bf16*>(&v[0]);
+        const bf16* a1 = reinterpret_cast<const bf16*>(&v[1]);
+        const bf16* a2 = reinterpret_cast<const bf16*>(&v[2]);
+        const bf16* a3 = reinterpret_cast<const bf16*>(&v[3]);
+        bf16* ob = reinterpret_cast<bf16*>(&o);
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            ob[e] = __float2bfloat16(0.25f * (__bfloat162float(a0[e]) + __bfloat162float(a1[e]) +
+                                              __bfloat162float(a2[e]) + __bfloat162float(a3[e])));
+        out[i] = o;
+    }
+}
+
 // gacc += pool_bwd(g): each fine pixel receives a quarter of its parent's gradient
 __global__ void k_pool_bwd_add(const float* __restrict__ g, float* __restrict__ gacc, int B, int H, int Wd, int C) {
     const long long n = (long long)B * H * Wd * C;
@@ -359,6 +385,25 @@ __global__ void k_up_cat(const bf16* __restrict__ d, const bf16* __restrict__ sk
         const long long q = i / C;
         const int x = q % Wd, y = (q / Wd) % H, b = q / ((long long)Wd * H);
         cat[i] = c < Cu ? d[(((size_t)b * (H / 2) + y / 2) * (Wd / 2) + x / 2) * Cu + c] : skip[q * Cs + (c - Cu)];
+    }
+}
+
+// k_up_cat on 8 channels at a time (Cu, Cs multiples of 8): 16-byte copies
+__global__ void k_up_cat8(const uint4* __restrict__ d, const uint4* __restrict__ skip, uint4* __restrict__ cat, int B,
+                          int H, int Wd, int Cu8, int Cs8) {
+    const int C8 = Cu8 + Cs8;
+    const long long n = (long long)B * H * Wd * C8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C8);
+        const long long q = i / C8;
+        if (c < Cu8) {
+            const int x = (int)(q % Wd);
+            const long long r = q / Wd;
+            const int y = (int)(r % H), b = (int)(r / H);
+            cat[i] = d[(((size_t)b * (H / 2) + y / 2) * (Wd / 2) + x / 2) * Cu8 + c];
+        } else {
+            cat[i] = skip[q * Cs8 + (c - Cu8)];
+        }
     }
 }
 
@@ -627,9 +672,13 @@ int net_forward(lm_net* N, const float* xin, float* yout, int B, int H, int W, c
         const int Hl = H >> l, Wl = W >> l;
         if (l > 0) {
             count_launches(1);
-            k_pool<<<blocks_for((long long)B * Hl * Wl * N->ch[l - 1]), 256, 0, s>>>(N->e[l - 1], N->in_[l], B,
-                                                                                   H >> (l - 1), W >> (l - 1),
-                                                                                   N->ch[l - 1]);
+            const int cp = N->ch[l - 1];
+            if (cp % 8 == 0)
+                k_pool8<<<blocks_for((long long)B * Hl * Wl * (cp / 8)), 256, 0, s>>>(
+                    (const uint4*)N->e[l - 1], (uint4*)N->in_[l], B, H >> (l - 1), W >> (l - 1), cp / 8);
+            else
+                k_pool<<<blocks_for((long long)B * Hl * Wl * cp), 256, 0, s>>>(N->e[l - 1], N->in_[l], B, H >> (l - 1),
+                                                                              W >> (l - 1), cp);
         }
         conv_fwd(N, N->convs[2 * l], N->in_[l], N->a1[l], B, Hl, Wl, s);
         conv_fwd(N, N->convs[2 * l + 1], N->a1[l], N->e[l], B, Hl, Wl, s);
@@ -638,8 +687,12 @@ int net_forward(lm_net* N, const float* xin, float* yout, int B, int H, int W, c
     for (int l = 2; l >= 0; --l) {
         const int Hl = H >> l, Wl = W >> l, cu = N->ch[l + 1], cs = N->ch[l];
         count_launches(1);
-        k_up_cat<<<blocks_for((long long)B * Hl * Wl * (cu + cs)), 256, 0, s>>>(dprev, N->e[l], N->cat[l], B, Hl, Wl,
-                                                                                cu, cs);
+        if (cu % 8 == 0 && cs % 8 == 0)
+            k_up_cat8<<<blocks_for((long long)B * Hl * Wl * ((cu + cs) / 8)), 256, 0, s>>>(
+                (const uint4*)dprev, (const uint4*)N->e[l], (uint4*)N->cat[l], B, Hl, Wl, cu / 8, cs / 8);
+        else
+            k_up_cat<<<blocks_for((long long)B * Hl * Wl * (cu + cs)), 256, 0, s>>>(dprev, N->e[l], N->cat[l], B, Hl,
+                                                                                    Wl, cu, cs);
         const int k = 8 + 2 * (2 - l);
         conv_fwd(N, N->convs[k], N->cat[l], N->da1[l], B, Hl, Wl, s);
         conv_fwd(N, N->convs[k + 1], N->da1[l], N->d[l], B, Hl, Wl, s);

@@ -112,6 +112,10 @@ _SIGNATURES = {
     "lm_mg_restrict_residual": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "lm_mg_prolong_add": (ctypes.c_int, [_P, _P, _P, _P]),
     "lm_mg_level_coefficients": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "lm_projection_rhs": (ctypes.c_int, [ctypes.c_int, _I64_3, _D3, _I3, ctypes.c_double] + [_P] * 10),
+    "lm_projection_update": (ctypes.c_int, [ctypes.c_int, _I64_3, _D3, _I3, ctypes.c_double] + [_P] * 9),
+    "lm_diffusion4": (ctypes.c_int, [ctypes.c_int, _I64_3, _D3, _I3, ctypes.c_int, ctypes.c_double, _P,
+                                      ctypes.c_double, _P, _P]),
     "lm_probe_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "lm_apply_dot_noalloc": (ctypes.c_int, [ctypes.c_int, _I64_3, _I3, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
@@ -477,3 +481,55 @@ def probe_rate(which: int, steps: int = 20000, stream=None) -> float:
     out = ctypes.c_double(0.0)
     _check(lib().lm_probe_rate(int(which), int(steps), ctypes.byref(out), _stream_ptr(stream)), "lm_probe_rate")
     return out.value
+
+
+def diffusion4(u, out, n, h, bc, alpha=1.0, beta=0.0, stream=None):
+    """lm_diffusion4: out = beta u + alpha (sum over axes of the dissipative
+    fourth-order second derivative); u, out CUDA tensors (float64 or float32)."""
+    n = tuple(int(v) for v in n)
+    N = n[0] * n[1] * n[2]
+    import torch
+    prec = PREC_FP64 if u.dtype == torch.float64 else PREC_FP32
+    dt = np.float64 if prec == PREC_FP64 else np.float32
+    up, du, ku = _field(u, N, dt)
+    op, do, ko = _field(out, N, dt)
+    if not (du and do):
+        raise ValueError("lm_diffusion4 takes device tensors")
+    ndim = 2 if n[1] == 1 else 3
+    return _check(lib().lm_diffusion4(ndim, _I64_3(*n), _D3(*h), _I3(*bc), prec, float(alpha), up, float(beta), op,
+                                      _stream_ptr(stream)), "lm_diffusion4")
+
+
+def _dev_ptr(t, size, name):
+    if t is None:
+        return None
+    p, on_dev, keep = _field(t, size)
+    if not on_dev:
+        raise ValueError(f"{name}: device tensors only")
+    return p
+
+
+def projection_rhs(n, h, bc, dt, p_old, rho_old, cs2_old, mom_old, mom_star, rho_new, f, uface_star, source=None,
+                   stream=None):
+    """lm_projection_rhs on CUDA float64 tensors (momenta and faces: 3N values)."""
+    n = tuple(int(v) for v in n)
+    N = n[0] * n[1] * n[2]
+    args = [_dev_ptr(t, s_, "lm_projection_rhs") for t, s_ in
+            ((p_old, N), (rho_old, N), (cs2_old, N), (mom_old, 3 * N), (mom_star, 3 * N), (rho_new, N), (source, N),
+             (f, N), (uface_star, 3 * N))]
+    ndim = 2 if n[1] == 1 else 3
+    return _check(lib().lm_projection_rhs(ndim, _I64_3(*n), _D3(*h), _I3(*bc), float(dt), *args, _stream_ptr(stream)),
+                  "lm_projection_rhs")
+
+
+def projection_update(n, h, bc, dt, p_pred, rho_new, mom_star, uface_star, e_star, mom_new, uface_new, e_new,
+                      stream=None):
+    """lm_projection_update on CUDA float64 tensors (momenta and faces: 3N values)."""
+    n = tuple(int(v) for v in n)
+    N = n[0] * n[1] * n[2]
+    args = [_dev_ptr(t, s_, "lm_projection_update") for t, s_ in
+            ((p_pred, N), (rho_new, N), (mom_star, 3 * N), (uface_star, 3 * N), (e_star, N), (mom_new, 3 * N),
+             (uface_new, 3 * N), (e_new, N))]
+    ndim = 2 if n[1] == 1 else 3
+    return _check(lib().lm_projection_update(ndim, _I64_3(*n), _D3(*h), _I3(*bc), float(dt), *args,
+                                             _stream_ptr(stream)), "lm_projection_update")
