@@ -52,8 +52,9 @@ DEFAULT_MODE = {"train2d": "learned"}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from an ncu
 # capture of the same kernel build on this workload, keyed (workload, kernel)
 NCU_TRAFFIC: dict = {
-    # plain level-0 sweep of the 256^3 workload: 293.7 MB read + 46.4 MB written
-    ("convection256", "k_rbgs_row"): 340.05e6,
+    # plain level-0 sweep of the 256^3 workload (the L2-prefetching whole-row
+    # kernel): 296.9 MB read + 48.3 MB written (profiles/k_rbgs_row_convection256_level0.md)
+    ("convection256", "k_rbgs_row"): 345.13e6,
 }
 
 

@@ -222,17 +222,23 @@ __global__ void __launch_bounds__(NT) k_finish_rel(double* part, int G, SolveSta
 // products of its dot products neither underflow nor overflow) for the
 // inner solve; partial r.r (slot 1) and, with FNORM, f.f (slot 4).
 // zero_x: x := 0 first (r = f).
-template <bool FNORM>
+// SC: 0 no scaling; 1 the float32 value scaled (a float multiply by a power
+// of two, exact while the unscaled residual is a normal float32 -- the
+// launcher asks for it when the residual's expected size is well inside
+// float32 range; it saves a float64 multiply a cell on GB300's slow float64
+// pipe); 2 scaled in float64 before rounding.
+template <bool FNORM, int SC>
 __global__ void __launch_bounds__(NT) k_ir_residual(Geo g, Op64 op, const double* __restrict__ f,
                                                     double* __restrict__ x, float* __restrict__ r32,
                                                     double* __restrict__ part, int zero_x, double rscale) {
     __shared__ double sm[64];
     double acc[2] = {0.0, 0.0};
+    const float rs32 = (float)rscale;
     const int stride = gridDim.x * blockDim.x;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < g.N; idx += stride) {
         const double fi = f[idx];
         const double ri = zero_x ? fi : fi - apply64_at(idx, g, op, x);
-        r32[idx] = (float)(ri * rscale);
+        r32[idx] = SC == 2 ? (float)(ri * rscale) : (SC == 1 ? (float)ri * rs32 : (float)ri);
         acc[0] += ri * ri;
         if (FNORM) acc[1] += fi * fi;
     }
@@ -443,8 +449,16 @@ void launch_ir_residual(const Geo& g, int G, cudaStream_t s, const Op64& op, con
                         float* r32, double* part, int zero_x, SolveState* st, int set_fnorm, double* hist_entry,
                         double rscale) {
     count_launches(1);
-    if (set_fnorm) k_ir_residual<true><<<G, NT, 0, s>>>(g, op, f, x, r32, part, zero_x, rscale);
-    else k_ir_residual<false><<<G, NT, 0, s>>>(g, op, f, x, r32, part, zero_x, rscale);
+    // rscale near 1/rms(r): the residual's size is about 1/rscale, a normal
+    // float32 (with room for small entries) when rscale is within 2^+-90
+    const int sc = rscale == 1.0 ? 0 : (rscale >= 0x1p-90 && rscale <= 0x1p90 ? 1 : 2);
+#define LM_IRR(F, SC) k_ir_residual<F, SC><<<G, NT, 0, s>>>(g, op, f, x, r32, part, zero_x, rscale)
+    if (set_fnorm) {
+        if (sc == 0) LM_IRR(true, 0); else if (sc == 1) LM_IRR(true, 1); else LM_IRR(true, 2);
+    } else {
+        if (sc == 0) LM_IRR(false, 0); else if (sc == 1) LM_IRR(false, 1); else LM_IRR(false, 2);
+    }
+#undef LM_IRR
     count_launches(1);
     k_finish_rel<<<1, NT, 0, s>>>(part, G, st, set_fnorm, hist_entry);
 }
