@@ -18,6 +18,11 @@ Modules
   diffusion  the dissipative fourth-order second-derivative stencil of the
              viscous terms (Sec. 4, Eq. dissipativestencil4) in flux form,
              and the non-dissipative nine-point stencil it replaces.
+  projection the steps either side of the solve (Sec. 2, steps (iv)-(viii)):
+             right-hand side of Eq. fpoiss, dual-cell pressure gradient
+             (Eqs. pbnd, nablaP), momentum, face-velocity and energy updates.
+  fem        the operator in Q1 finite elements (Sec. 2.5): element
+             matrices, harmonic-mean element kappa, lumped c~ term.
 
 Pins (what fixes each function to something other than itself) live in
 tests/test_oracle_*.py.  Functions whose result has no such pin say

@@ -314,3 +314,28 @@ def analytic_exp_problem(n: int, perturb: str | None = None, seed: int = 5, eps:
     bc = (BC_NEUMANN, BC_PERIODIC, BC_PERIODIC)
     return dict(n=(n, 1, n), h=(1.0 / n, 1.0, 1.0 / n), bc=bc, ctilde=ct, kappa=kap, f=f,
                 exact=exact, g_low=-1.0, g_high=math.e)
+
+
+def analytic_exp_problem_nodes(n: int, perturb: str | None = None, seed: int = 5, eps: float = 1e-2,
+                               nper: int | None = None):
+    """The Sec. 2.5.2 stability test on a grid of points for the finite-element
+    operator: n points x_i = i / (n - 1) across [0,1] in x (the walls are
+    points), `nper` points (default n - 1) around the periodic axis.  Same
+    fields and noise as analytic_exp_problem, sampled at the points."""
+    nper = n - 1 if nper is None else nper
+    x = np.arange(n) / (n - 1)
+    shape3 = (nper, 1, n)
+    ct = np.ones(shape3)
+    kap = np.ones(shape3)
+    f = np.zeros(shape3)
+    xi = 2.0 * uniform01(_stream(seed, 17), n * nper).reshape(shape3) - 1.0
+    if perturb == "f":
+        f = f + eps * xi
+    elif perturb == "kappa":
+        kap = kap * (1.0 + eps * xi)
+    elif perturb == "c":
+        ct = ct * (1.0 + eps * xi)
+    exact = np.broadcast_to(np.exp(x)[None, None, :], shape3).copy()
+    bc = (BC_NEUMANN, BC_PERIODIC, BC_PERIODIC)
+    return dict(n=(n, 1, nper), h=(1.0 / (n - 1), 1.0, 1.0 / nper), bc=bc, ctilde=ct, kappa=kap, f=f,
+                exact=exact, g_low=-1.0, g_high=math.e)
