@@ -395,6 +395,12 @@ def run_batch(args):
     t_step = e0.elapsed_time(e1) * 1e-3 / args.steps
     res = results[-1]
     assert all(r["status"] == 0 and r["rel_residual"] <= 1e-8 for r in res)
+    if args.only_steps:                 # profiling runs: the timed batches and nothing else
+        print(json.dumps({"only_steps": True, "ms_per_batch": t_step * 1e3,
+                          "gpu_launches_per_batch": launches / args.steps}), flush=True)
+        for g in grids:
+            g.close()
+        return
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -629,6 +635,42 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_kernel(args):
+    """A few launches of one kernel, nothing else: the command the ncu captures
+    of the sweep, the float32 apply and the network are taken on."""
+    import torch
+
+    from paper_1112_3507_gb300 import lowmach as lm
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    if args.kernel == "net":
+        net = lm.Net.load(WEIGHTS)
+        B, H, W = 16, 256, 256
+        x = torch.randn(B * H * W * 3, device="cuda")
+        y = torch.empty(B * H * W, device="cuda")
+        for _ in range(3):
+            net.forward(x, y, B, H, W)
+        torch.cuda.synchronize()
+        net.close()
+    else:
+        if WORKLOADS[args.workload]["kind"] == "batch":
+            raise SystemExit("--kernel runs on a single-grid workload")
+        p = make_problem(args.workload, 1)
+        g = lm.Grid.for_problem(p)
+        g.set_problem(p)
+        x = torch.randn(p.size, dtype=torch.float32, device="cuda")
+        f = torch.randn_like(x)
+        y = torch.empty_like(x)
+        for _ in range(4):
+            if args.kernel == "sweep":
+                g.mg_sweep(x, f, y, 0, stream=stream)
+            else:
+                g.apply(x, y, prec=lm.PREC_FP32, stream=stream)
+        torch.cuda.synchronize()
+        g.close()
+    print(json.dumps({"kernel": args.kernel, "workload": args.workload, "status": "ok"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -642,9 +684,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true",
                     help="run warm-up and timed solves only (for profiler launch lists)")
+    ap.add_argument("--kernel", choices=["sweep", "apply32", "net"], default=None,
+                    help="profiling runs: a few launches of one kernel on the workload's finest grid "
+                         "(sweep: lm_mg_sweep, apply32: lm_apply in float32; net: U-Net forward on "
+                         "16 images of 256^2), then exit")
     args = ap.parse_args()
-    args.max_iter = args.max_iter
-    if args.impl == "reference":
+    if args.kernel:
+        run_kernel(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif WORKLOADS[args.workload]["kind"] == "batch":
         run_batch(args)
