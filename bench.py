@@ -47,6 +47,9 @@ WORKLOADS = {
                                                    "rtol 1e-8, learned warm start + preconditioner"),
     "semiconvection512": dict(kind="semi3d", n=512, desc="3D 512^3 two-component semiconvection (R_rho 1.1, "
                                                          "1% T and helium perturbations), Ma=0.001, rtol 1e-8"),
+    "fe256": dict(kind="fe3d", n=256, desc="3D 256^3 points, Q1 finite elements (cubic, h = 1/255), convection "
+                                           "recipe coefficients (rho contrast 20 + 1% noise, Ma=0.01), x/y "
+                                           "periodic, z walls, rtol 1e-8"),
 }
 DEFAULT_MODE = {"train2d": "learned"}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from an ncu
@@ -74,7 +77,7 @@ WEIGHTS = os.path.join(ROOT, "paper_1112_3507_gb300", "weights", "unet_16_32_48_
 def make_problem(name: str, seed: int = 1):
     from paper_1112_3507_gb300 import inputs as I
     w = WORKLOADS[name]
-    if w["kind"] == "conv3d":
+    if w["kind"] in ("conv3d", "fe3d"):
         return I.config_convection_3d(w["n"], seed=seed)
     if w["kind"] == "semi3d":
         return I.config_semiconvection_3d(w["n"], seed=7)
@@ -300,6 +303,10 @@ def cpu_block(r: dict, name: str) -> dict:
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if WORKLOADS[args.workload]["kind"] == "fe3d":
+        print(json.dumps({"impl": "reference", "unavailable": "the CPU arm times the cell-centred oracle's "
+                          "Jacobi-PCG; the finite-element workload has no timed oracle arm"}), flush=True)
         return
     r = oracle_subprocess("bench.oracle_report(%r, %d, %d, %d, 'all')" % (args.workload, args.oracle_iters,
                                                                             args.steps, args.warmup))
@@ -635,6 +642,148 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_fe(args):
+    """The operator in Q1 finite elements on 256^3 points: one step = the
+    coefficients from the state (lm_fe_set_state), the load vector V f
+    (lm_fe_mass_times) and the mixed solve (lm_fe_solve) to 1e-8."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1112_3507_gb300 import lowmach as lm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    n = WORKLOADS[args.workload]["n"]
+    probs = [make_problem(args.workload, seed=1 + k) for k in range(3)]
+    p = probs[0]
+    N = p.size
+    h = (1.0 / (n - 1),) * 3              # cubic elements; the walled z axis spans [0, 1]
+    g = lm.FEGrid(p.n, h, p.bc)
+    dev_in = [[torch.as_tensor(a.ravel(), device=dev) for a in (q.rho_old, q.rho_new, q.cs2, q.f)] for q in probs]
+    b = torch.empty(N, dtype=torch.float64, device=dev)
+    x = torch.zeros(N, dtype=torch.float64, device=dev)
+
+    def step(k, mode="mixed"):
+        ro, rn, c2, f = dev_in[k % len(probs)]
+        g.set_state(ro, rn, c2, probs[k % len(probs)].dt, stream)
+        g.mass_times(f, b, stream)
+        return g.solve(b, x, mode=mode, rtol=p.rtol, stream=stream, max_iter=args.max_iter,
+                       allow=(0,) if mode == "mixed" else (0, -3))
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    launches0 = lm.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    results = []
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        results.append(step(k))
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = lm.kernel_launches() - launches0
+    barrier()
+    clk = clocks.stop()
+    elapsed = job_time(sum(a.elapsed_time(c) for a, c in ev) * 1e-3, world, dev)
+    assert all(r["status"] == 0 and r["rel_residual"] <= p.rtol for r in results), results
+    res = results[-1]
+    t_solve = elapsed / args.steps
+
+    # end to end: pinned host inputs copied in and the solution copied out inside the timed region
+    host = [[torch.from_numpy(np.ascontiguousarray(a.ravel())).pin_memory() for a in (q.rho_old, q.rho_new,
+                                                                                      q.cs2, q.f)]
+            for q in probs]
+    xout = torch.empty(N, dtype=torch.float64).pin_memory()
+
+    def e2e_step(k):
+        for d, hsrc in zip(dev_in[k % len(probs)], host[k % len(probs)]):
+            d.copy_(hsrc, non_blocking=True)
+        r = step(k)
+        xout.copy_(x, non_blocking=True)
+        return r
+
+    e2e_step(0)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        e2e_step(k)
+    torch.cuda.synchronize()
+    e2e_t = job_time(time.perf_counter() - t0, world, dev)
+
+    # the float64 Jacobi-PCG on the same system
+    torch.cuda.synchronize()
+    b0 = time.perf_counter()
+    rj = step(0, mode="jacobi")
+    torch.cuda.synchronize()
+    t_jac = time.perf_counter() - b0
+
+    # roofline of the float32 finite-element apply (k_fe3_32), timed alone
+    x32 = torch.randn(N, dtype=torch.float32, device=dev)
+    y32 = torch.empty_like(x32)
+    reps = 20
+    t_ap = time_kernel(torch, lambda: g.apply(x32, y32, prec=lm.PREC_FP32, stream=stream), reps, stream)
+    x64 = torch.randn(N, dtype=torch.float64, device=dev)
+    y64 = torch.empty_like(x64)
+    t_ap64 = time_kernel(torch, lambda: g.apply(x64, y64, prec=lm.PREC_FP64, stream=stream), reps, stream)
+    fp64_rate = lm.probe_rate(0, 20000, stream)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    ap_bytes = 16                         # read x, kappa_e, V c~; write y (float32)
+    achieved = ap_bytes * N / t_ap / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": job_value(N, args.steps, world, elapsed), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (float32 flexible CG, float64 residual/refinement)", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "points": N, "mode": "mixed",
+                       "problems": len(probs), "rtol": p.rtol, "l2": "inputs exceed L2 (4 x %.0f MB)" % (N * 8 / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "time_to_tol_ms": t_solve * 1e3,
+            "solve": {"iters": res["iters"], "outer_iters": res["outer_iters"], "vcycles": res["vcycles"],
+                      "rel_residual": res["rel_residual"]},
+            "fp64_jacobi_pcg": {"time_to_tol_ms": t_jac * 1e3, "iters": rj["iters"], "status": rj["status"],
+                                "rel_residual": rj["rel_residual"]},
+            "speedup_vs_fp64_pcg": t_jac / t_solve,
+            "e2e": {"value": job_value(N, args.steps, world, e2e_t), "unit": UNIT,
+                    "h2d_bytes_per_step": 4 * 8 * N, "d2h_bytes_per_step": 8 * N},
+            "roofline": {"kernel": "k_fe3_32 (float32 Q1 finite-element apply, row f1)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "bytes_per_point": ap_bytes, "launch_us": t_ap * 1e6,
+                         "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
+                                         else "fallback 6800 GB/s (of fallback)"),
+                         "also": {"k_fe_apply64": fp64_roof(t_ap64, N, 32, 60, peak, fp64_rate,
+                                                            "y = B x in float64 on cubic elements: 20 "
+                                                            "neighbours, about 60 float64 operations a point")}},
+            "cpu_baseline": None,
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_kernel(args):
     """A few launches of one kernel, nothing else: the command the ncu captures
     of the sweep, the float32 apply and the network are taken on."""
@@ -652,6 +801,17 @@ def run_kernel(args):
             net.forward(x, y, B, H, W)
         torch.cuda.synchronize()
         net.close()
+    elif args.kernel == "fe32":
+        p = make_problem("fe256", 1)
+        n = WORKLOADS["fe256"]["n"]
+        g = lm.FEGrid(p.n, (1.0 / (n - 1),) * 3, p.bc)
+        g.set_state(p.rho_old, p.rho_new, p.cs2, p.dt)
+        x = torch.randn(p.size, dtype=torch.float32, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(4):
+            g.apply(x, y, prec=lm.PREC_FP32, stream=stream)
+        torch.cuda.synchronize()
+        g.close()
     else:
         if WORKLOADS[args.workload]["kind"] == "batch":
             raise SystemExit("--kernel runs on a single-grid workload")
@@ -684,10 +844,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true",
                     help="run warm-up and timed solves only (for profiler launch lists)")
-    ap.add_argument("--kernel", choices=["sweep", "apply32", "net"], default=None,
+    ap.add_argument("--kernel", choices=["sweep", "apply32", "net", "fe32"], default=None,
                     help="profiling runs: a few launches of one kernel on the workload's finest grid "
                          "(sweep: lm_mg_sweep, apply32: lm_apply in float32; net: U-Net forward on "
-                         "16 images of 256^2), then exit")
+                         "16 images of 256^2; fe32: lm_fe_apply in float32 on the fe256 points), then exit")
     args = ap.parse_args()
     if args.kernel:
         run_kernel(args)
@@ -695,6 +855,8 @@ def main():
         run_reference(args)
     elif WORKLOADS[args.workload]["kind"] == "batch":
         run_batch(args)
+    elif WORKLOADS[args.workload]["kind"] == "fe3d":
+        run_fe(args)
     else:
         run_ours(args)
 

@@ -415,6 +415,75 @@ int  lm_projection_update(int ndim, const int64_t n[3], const double h[3], const
 int  lm_diffusion4(int ndim, const int64_t n[3], const double h[3], const int bc[3], int prec, double alpha,
                    const void* u, double beta, void* out, void* stream);
 
+/* ---- the operator in Q1 finite elements (Sec. 2.5) ----------------------- */
+
+/* The paper discretizes Eq. GeneralizedPoisson with finite elements (Sec.
+ * 2.5: the system matrix is then symmetric positive definite).  Here:
+ * multilinear (Q1) elements on the points x_i = i h of every axis, stored
+ * like the cell grids (x fastest, 2D grids are (x, z) with n[1] = 1).  A
+ * periodic axis of n points is a ring of n elements; a walled axis
+ * (LM_BC_NEUMANN) has n - 1 elements and its end points on the walls, where
+ * the homogeneous Neumann condition is the natural one of the weak form.
+ * Element kappa_e is the harmonic mean of kappa = 1/rho over the element's
+ * corners; the c~ term is mass-lumped.  The system is
+ *
+ *     B x = b,   B = diag(V c~) + sum_e kappa_e K_ref,
+ *
+ * V_i the point's share of its elements (h per axis, h/2 at a wall end;
+ * lm_fe_lumped_mass), K_ref the Q1 element stiffness, b the load vector:
+ * V f for a right-hand side f, plus g times the wall share of each wall
+ * point for inhomogeneous Neumann data g.  The handle owns every buffer it
+ * uses, including a cell-centred grid on the same points whose multigrid
+ * V-cycle preconditions the mixed solve. */
+typedef struct lm_fe lm_fe;
+
+/* n[0] and n[2] >= 2 points; ndim 2: n[1] == 1; ndim 3: n[1] >= 2.  Errors:
+ * LM_ERR_INVALID_ARG, LM_ERR_OUT_OF_MEMORY. */
+int  lm_fe_create(int ndim, const int64_t n[3], const double h[3], const int bc[3], lm_fe** out);
+void lm_fe_destroy(lm_fe* fe);
+
+/* c~ and rho at the points (N values each; host or device per on_device,
+ * read on `stream`; host buffers may be reused on return).  Forms kappa_e,
+ * V c~, the inverse diagonal and their float32 copies, and the
+ * preconditioner's cell-centred coefficients.  LM_ERR_NOT_POSITIVE when a
+ * value is not strictly positive and finite (Sec. 2.5's conditions); the
+ * handle then holds no coefficients. */
+int  lm_fe_set_coefficients(lm_fe* fe, const double* ctilde, const double* rho, int on_device, void* stream);
+
+/* As lm_fe_set_coefficients, with c~ formed on the device from the state
+ * (step (v) of Sec. 2.4, Eq. cpoiss): c~ = 1 / (dt^2 rho^n c_s^2) from
+ * rho_old, cs2 and dt, kappa from rho_new.  LM_ERR_NOT_POSITIVE for dt <= 0
+ * or a c~ / rho that is not strictly positive and finite. */
+int  lm_fe_set_state(lm_fe* fe, const double* rho_old, const double* rho_new, const double* cs2, double dt,
+                     int on_device, void* stream);
+
+/* V (N doubles, host or device per on_device). */
+int  lm_fe_lumped_mass(lm_fe* fe, double* v, int on_device, void* stream);
+
+/* b = V f, the load vector of a right-hand side f (N doubles each, host or
+ * device per on_device; f and b may be the same array). */
+int  lm_fe_mass_times(lm_fe* fe, const double* f, double* b, int on_device, void* stream);
+
+/* y = B x on the device in precision prec (float64: double arrays; float32:
+ * float arrays, LM_ERR_INVALID_ARG when a coefficient leaves the float32
+ * range); with dot_out, also *dot_out = x^T B x (synchronises the stream).
+ * x and y must not overlap.  LM_ERR_STATE before lm_fe_set_coefficients. */
+int  lm_fe_apply(lm_fe* fe, int prec, const void* x, void* y, double* dot_out, void* stream);
+
+/* Solve B x = b to ||b - B x||_2 <= opts->rtol ||b||_2 (float64 true
+ * residual).  opts->mode: LM_FP64_JACOBI_PCG (float64 conjugate gradients,
+ * Jacobi preconditioner) or LM_MIXED_MG_IR (float64 iterative refinement;
+ * inner float32 flexible CG preconditioned by a damped Jacobi step on B, the
+ * cell-centred V-cycle (opts->nu1, nu2) on the residual divided by V, and a
+ * second Jacobi step; it needs an even number of points on every periodic
+ * axis and float32-representable coefficients, else LM_ERR_INVALID_ARG).
+ * b and x: N doubles on host or device per on_device;
+ * x is the initial guess when opts->use_x0 and receives the solution (also
+ * on LM_ERR_NO_CONVERGENCE / LM_ERR_BREAKDOWN).  Synchronises
+ * opts->cuda_stream; res->seconds is the device time of the solve. */
+int  lm_fe_solve(lm_fe* fe, const double* b, double* x, int on_device, const lm_solve_opts* opts,
+                 lm_solve_result* res);
+
 /* ---- measurement ---------------------------------------------------------- */
 
 /* Arithmetic-rate probe of the current device, the measured roof of the

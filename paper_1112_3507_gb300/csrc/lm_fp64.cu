@@ -427,6 +427,18 @@ void launch_pcg_init(const PcgArgs& a, int G, cudaStream_t s, int use_x0) {
     count_launches(1);
     k_pcg_init_p<<<G, NT, 0, s>>>(a, 2, 0);
 }
+void launch_pcg_init_p(const PcgArgs& a, int G, cudaStream_t s, int rz_slot, int restart) {
+    count_launches(1);
+    k_pcg_init_p<<<G, NT, 0, s>>>(a, rz_slot, restart);
+}
+void launch_pcg_xr(const PcgArgs& a, int G, cudaStream_t s, int k) {
+    count_launches(1);
+    k_pcg_xr<<<G, NT, 0, s>>>(a, k);
+}
+void launch_pcg_p(const PcgArgs& a, int G, cudaStream_t s, int k) {
+    count_launches(1);
+    k_pcg_p<<<G, NT, 0, s>>>(a, k);
+}
 void launch_pcg_restart(const PcgArgs& a, int G, cudaStream_t s, int k) {
     count_launches(1);
     k_pcg_init_p<<<G, NT, 0, s>>>(a, 2 + (k & 1), 1);

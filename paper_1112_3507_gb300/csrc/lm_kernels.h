@@ -89,6 +89,12 @@ void launch_apply64(const Geo& g, int G, cudaStream_t s, const Op64& op, const d
                     double* part);
 void launch_pcg_init(const PcgArgs& a, int G, cudaStream_t s, int use_x0);
 void launch_pcg_restart(const PcgArgs& a, int G, cudaStream_t s, int k);
+// the operator-free steps of one Jacobi-PCG iteration, for operators applied
+// elsewhere: p = D^-1 r with r.z (after the residual), the x, r update after
+// q = A p with its p.q partials (slot 0), and the convergence test with the p update
+void launch_pcg_init_p(const PcgArgs& a, int G, cudaStream_t s, int rz_slot, int restart);
+void launch_pcg_xr(const PcgArgs& a, int G, cudaStream_t s, int k);
+void launch_pcg_p(const PcgArgs& a, int G, cudaStream_t s, int k);
 void launch_pcg_iter(const PcgArgs& a, int G, cudaStream_t s, int k);
 void launch_true_residual(const PcgArgs& a, int G, cudaStream_t s);
 void launch_ir_residual(const Geo& g, int G, cudaStream_t s, const Op64& op, const double* f, double* x,

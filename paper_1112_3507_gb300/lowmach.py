@@ -117,6 +117,15 @@ _SIGNATURES = {
     "lm_diffusion4": (ctypes.c_int, [ctypes.c_int, _I64_3, _D3, _I3, ctypes.c_int, ctypes.c_double, _P,
                                       ctypes.c_double, _P, _P]),
     "lm_probe_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
+    "lm_fe_create": (ctypes.c_int, [ctypes.c_int, _I64_3, _D3, _I3, ctypes.POINTER(_P)]),
+    "lm_fe_destroy": (None, [_P]),
+    "lm_fe_set_coefficients": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "lm_fe_set_state": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int, _P]),
+    "lm_fe_lumped_mass": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "lm_fe_mass_times": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "lm_fe_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "lm_fe_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(SolveOpts),
+                                    ctypes.POINTER(SolveResult)]),
     "lm_apply_dot_noalloc": (ctypes.c_int, [ctypes.c_int, _I64_3, _I3, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
@@ -348,6 +357,102 @@ class Grid:
             _check(lib().lm_mg_level_shape(self._g, l, out, ctypes.byref(nl)), "lm_mg_level_shape")
             shapes.append(tuple(out))
         return shapes
+
+
+class FEGrid:
+    """The operator in Q1 finite elements on n = (nx, ny, nz) points (ny = 1
+    for 2D), spacings h, one boundary condition per axis (lm_fe_*)."""
+
+    def __init__(self, n, h, bc, ndim: int | None = None):
+        n = tuple(int(v) for v in n)
+        if ndim is None:
+            ndim = 2 if n[1] == 1 else 3
+        self.n, self.h, self.bc, self.ndim = n, tuple(float(v) for v in h), tuple(int(b) for b in bc), ndim
+        self.N = n[0] * n[1] * n[2]
+        ptr = _P()
+        _check(lib().lm_fe_create(ndim, _I64_3(*n), _D3(*self.h), _I3(*self.bc), ctypes.byref(ptr)), "lm_fe_create")
+        self._h = ptr
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lm_fe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_coefficients(self, ctilde, rho, stream=None):
+        a, d1, k1 = _field(ctilde, self.N)
+        b, d2, k2 = _field(rho, self.N)
+        if d1 != d2:
+            raise ValueError("all fields must live on the same side (host or device)")
+        return _check(lib().lm_fe_set_coefficients(self._h, a, b, d1, _stream_ptr(stream)), "lm_fe_set_coefficients")
+
+    def set_state(self, rho_old, rho_new, cs2, dt, stream=None):
+        a, d1, k1 = _field(rho_old, self.N)
+        b, d2, k2 = _field(rho_new, self.N)
+        c, d3, k3 = _field(cs2, self.N)
+        if not d1 == d2 == d3:
+            raise ValueError("all fields must live on the same side (host or device)")
+        return _check(lib().lm_fe_set_state(self._h, a, b, c, float(dt), d1, _stream_ptr(stream)), "lm_fe_set_state")
+
+    def mass_times(self, f, out, stream=None):
+        a, d1, k1 = _field(f, self.N)
+        b, d2, k2 = _field(out, self.N)
+        if d1 != d2:
+            raise ValueError("f and out must live on the same side (host or device)")
+        _check(lib().lm_fe_mass_times(self._h, a, b, d1, _stream_ptr(stream)), "lm_fe_mass_times")
+        return out
+
+    def lumped_mass(self, out=None, stream=None):
+        if out is None:
+            out = np.empty(self.N, dtype=np.float64)
+        a, d, k = _field(out, self.N)
+        _check(lib().lm_fe_lumped_mass(self._h, a, d, _stream_ptr(stream)), "lm_fe_lumped_mass")
+        return out
+
+    def apply(self, x, y, prec=PREC_FP64, with_dot=False, stream=None):
+        dt = np.float64 if prec == PREC_FP64 else np.float32
+        xp, dx, kx = _field(x, self.N, dt)
+        yp, dy, ky = _field(y, self.N, dt)
+        if not (dx and dy):
+            raise ValueError("lm_fe_apply takes device tensors")
+        dot = ctypes.c_double(0.0)
+        _check(lib().lm_fe_apply(self._h, prec, xp, yp, ctypes.byref(dot) if with_dot else None,
+                                 _stream_ptr(stream)), "lm_fe_apply")
+        return dot.value if with_dot else None
+
+    def solve(self, b, x, mode="mixed", rtol=1e-8, stream=None, allow=(LM_OK,), **kw) -> dict:
+        """lm_fe_solve: B x = b; x (same side as b) is overwritten with the solution."""
+        o = SolveOpts()
+        lib().lm_default_opts(ctypes.byref(o))
+        o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        o.rtol = float(rtol)
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown solve option {k}")
+            setattr(o, k, v)
+        o.cuda_stream = _stream_ptr(stream)
+        bp, db, kb = _field(b, self.N)
+        if isinstance(x, np.ndarray) and (x.dtype != np.float64 or not x.flags.c_contiguous):
+            raise ValueError("x must be a contiguous float64 array")
+        xp, dx, kx = _field(x, self.N)
+        if db != dx:
+            raise ValueError("b and x must live on the same side (host or device)")
+        r = SolveResult()
+        code = lib().lm_fe_solve(self._h, bp, xp, db, ctypes.byref(o), ctypes.byref(r))
+        _check(code, "lm_fe_solve", ok=allow)
+        return dict(status=r.status, iters=r.iters, outer_iters=r.outer_iters, vcycles=r.vcycles,
+                    rel_residual=r.rel_residual, seconds=r.seconds)
 
 
 class Net:
