@@ -23,6 +23,9 @@ Modules
              (Eqs. pbnd, nablaP), momentum, face-velocity and energy updates.
   fem        the operator in Q1 finite elements (Sec. 2.5): element
              matrices, harmonic-mean element kappa, lumped c~ term.
+  fractional one whole fractional step around the solve (Sec. 2.4 steps
+             (i)-(ix)): MUSCL-upwinded advection, the projection steps, the
+             ideal-gas reset; the Gresho vortex's kinetic energy.
 
 Pins (what fixes each function to something other than itself) live in
 tests/test_oracle_*.py.  Functions whose result has no such pin say

@@ -339,3 +339,36 @@ def analytic_exp_problem_nodes(n: int, perturb: str | None = None, seed: int = 5
     bc = (BC_NEUMANN, BC_PERIODIC, BC_PERIODIC)
     return dict(n=(n, 1, nper), h=(1.0 / (n - 1), 1.0, 1.0 / nper), bc=bc, ctilde=ct, kappa=kap, f=f,
                 exact=exact, g_low=-1.0, g_high=math.e)
+
+
+def gresho_vortex(n: int, ma: float, gamma: float = 5.0 / 3.0, cfl: float = 0.5) -> dict:
+    """The Gresho vortex of Sec. 5.5.2 on a periodic n x n grid of cell
+    centres over [0,1]^2 (the paper's y is this layout's z; arrays are
+    (n, 1, n)): rho = 1, P0 = rho / (gamma Ma^2), the printed u_phi(r) and
+    P(r), the velocity the counter-clockwise rotation u_phi (-sin t, cos t)
+    with t = atan2(y - 1/2, x - 1/2), and total energy
+    e = P / (gamma - 1) + rho |u|^2 / 2.  dt is the sound-speed-induced step
+    cfl h / max(|u| + c_s) with c_s^2 = gamma P / rho."""
+    h = 1.0 / n
+    c = (np.arange(n) + 0.5) * h
+    zz, xx = np.meshgrid(c, c, indexing="ij")
+    dx, dz = xx - 0.5, zz - 0.5
+    r = np.sqrt(dx * dx + dz * dz)
+    t = np.arctan2(dz, dx)
+    rho = np.ones((n, 1, n))
+    p0 = 1.0 / (gamma * ma * ma)
+    inner, ring = r <= 0.2, (r > 0.2) & (r <= 0.4)
+    uphi = np.where(inner, 5.0 * r, np.where(ring, 2.0 - 5.0 * r, 0.0))
+    rr = np.maximum(r, 1e-300)
+    P = np.where(inner, p0 + 12.5 * r * r,
+                 np.where(ring, p0 + 12.5 * r * r + 4.0 * (1.0 - 5.0 * r - math.log(0.2) + np.log(rr)),
+                          p0 - 2.0 + 4.0 * math.log(2.0)))
+    ux = (-np.sin(t) * uphi)[:, None, :]
+    uz = (np.cos(t) * uphi)[:, None, :]
+    P = P[:, None, :]
+    mom = [rho * ux, np.zeros_like(rho), rho * uz]
+    e = P / (gamma - 1.0) + 0.5 * rho * (ux * ux + uz * uz)
+    cs = np.sqrt(gamma * P / rho)
+    dt = cfl * h / float(np.max(np.sqrt(ux * ux + uz * uz) + cs))
+    return dict(n=(n, 1, n), h=(h, 1.0, h), bc=(BC_PERIODIC, BC_PERIODIC, BC_PERIODIC), rho=rho, mom=mom, e=e,
+                P=P, gamma=gamma, dt=dt, ma=ma, name=f"gresho-{n}^2-Ma{ma}")
