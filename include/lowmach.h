@@ -398,6 +398,31 @@ int  lm_projection_update(int ndim, const int64_t n[3], const double h[3], const
                           const double* uface_star, const double* e_star, double* mom_new, double* uface_new,
                           double* e_new, void* stream);
 
+/* Steps (i)-(iii) of Sec. 2.4, the explicit advection: face velocities
+ * u_{i+1/2} = ((rho u)_i + (rho u)_{i+1}) / (rho_i + rho_{i+1}) (Eq. step1),
+ * the modified flux F~ = (rho, rho u, e, rho c) u_{i+1/2} with the advected
+ * quantity taken from the upwind side's MUSCL state (minmod-limited slope:
+ * the paper's CPM/MENO reconstruction is not given in its text), and
+ * q^{new} = q^n - dt d(F~)/dx summed over the axes with more than one cell.
+ * A wall face (LM_BC_NEUMANN) carries no flux and the cells next to a wall
+ * have zero slope; periodic axes wrap.  n, h, bc: host arrays as in
+ * lm_grid_create.  Device arrays of N = n[0] n[1] n[2] doubles: rho, e,
+ * rho_c (optional, the two-component flow's rho c; NULL with rho_c_new
+ * NULL), and mom, mom_star: three consecutive arrays (x, y, z components).
+ * Outputs rho_new, mom_star, e_star, rho_c_new must not overlap any input.
+ * Inviscid: the viscous flux of step (ii) is the caller's (lm_diffusion4).
+ * LM_ERR_INVALID_ARG for bad sizes, dt < 0 or overlapping arrays. */
+int  lm_advect(int ndim, const int64_t n[3], const double h[3], const int bc[3], double dt, const double* rho,
+               const double* mom, const double* e, const double* rho_c, double* rho_new, double* mom_star,
+               double* e_star, double* rho_c_new, void* stream);
+
+/* Step (ix) of Sec. 2.4 for an ideal gas: p = (gamma - 1)(e - |rho u|^2 /
+ * (2 rho)) and, when cs2 is not NULL, c_s^2 = gamma p / rho (the next step's
+ * c~, Eq. cpoiss).  Device arrays of n_cells doubles (mom: three consecutive
+ * arrays).  LM_ERR_INVALID_ARG for gamma <= 1 or a bad size. */
+int  lm_eos_ideal(int64_t n_cells, double gamma, const double* rho, const double* mom, const double* e, double* p,
+                  double* cs2, void* stream);
+
 /* ---- the viscous terms' dissipative stencil (Sec. 4) --------------------- */
 
 /* out = beta u + alpha sum_a (U_aa): the dissipative fourth-order second

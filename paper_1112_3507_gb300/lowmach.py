@@ -114,6 +114,8 @@ _SIGNATURES = {
     "lm_mg_level_coefficients": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "lm_projection_rhs": (ctypes.c_int, [ctypes.c_int, _I64_3, _D3, _I3, ctypes.c_double] + [_P] * 10),
     "lm_projection_update": (ctypes.c_int, [ctypes.c_int, _I64_3, _D3, _I3, ctypes.c_double] + [_P] * 9),
+    "lm_advect": (ctypes.c_int, [ctypes.c_int, _I64_3, _D3, _I3, ctypes.c_double] + [_P] * 9),
+    "lm_eos_ideal": (ctypes.c_int, [ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P, _P, _P]),
     "lm_diffusion4": (ctypes.c_int, [ctypes.c_int, _I64_3, _D3, _I3, ctypes.c_int, ctypes.c_double, _P,
                                       ctypes.c_double, _P, _P]),
     "lm_probe_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
@@ -586,6 +588,28 @@ def probe_rate(which: int, steps: int = 20000, stream=None) -> float:
     out = ctypes.c_double(0.0)
     _check(lib().lm_probe_rate(int(which), int(steps), ctypes.byref(out), _stream_ptr(stream)), "lm_probe_rate")
     return out.value
+
+
+def advect(n, h, bc, dt, rho, mom, e, rho_new, mom_star, e_star, rho_c=None, rho_c_new=None, stream=None):
+    """lm_advect (steps (i)-(iii)): device float64 tensors; mom and mom_star
+    hold the three components consecutively (3N values)."""
+    n = tuple(int(v) for v in n)
+    ndim = 2 if n[1] == 1 else 3
+    N = n[0] * n[1] * n[2]
+    names = ("rho", "mom", "e", "rho_c", "rho_new", "mom_star", "e_star", "rho_c_new")
+    sizes = (N, 3 * N, N, N, N, 3 * N, N, N)
+    ts = (rho, mom, e, rho_c, rho_new, mom_star, e_star, rho_c_new)
+    ptrs = [_dev_ptr(t, sz, nm) for t, sz, nm in zip(ts, sizes, names)]
+    return _check(lib().lm_advect(ndim, _I64_3(*n), _D3(*h), _I3(*bc), float(dt), *ptrs, _stream_ptr(stream)),
+                  "lm_advect")
+
+
+def eos_ideal(gamma, rho, mom, e, p, cs2=None, stream=None):
+    """lm_eos_ideal (step (ix)): device float64 tensors, mom 3N values."""
+    N = int(rho.numel())
+    return _check(lib().lm_eos_ideal(N, float(gamma), _dev_ptr(rho, N, "rho"), _dev_ptr(mom, 3 * N, "mom"),
+                                      _dev_ptr(e, N, "e"), _dev_ptr(p, N, "p"), _dev_ptr(cs2, N, "cs2"),
+                                      _stream_ptr(stream)), "lm_eos_ideal")
 
 
 def diffusion4(u, out, n, h, bc, alpha=1.0, beta=0.0, stream=None):
