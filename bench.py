@@ -47,6 +47,10 @@ WORKLOADS = {
                                                    "rtol 1e-8, learned warm start + preconditioner"),
     "semiconvection512": dict(kind="semi3d", n=512, desc="3D 512^3 two-component semiconvection (R_rho 1.1, "
                                                          "1% T and helium perturbations), Ma=0.001, rtol 1e-8"),
+    "gresho256": dict(kind="gresho2d", n=256, desc="Gresho vortex (Sec. 5.5.2), periodic 256^2, Ma=0.01, "
+                                                   "sound-speed-induced dt (CFL 0.5); one step = advection, "
+                                                   "projection rhs, coefficients, mixed solve to 1e-11 warm-started "
+                                                   "from P^n, projection update, EOS"),
     "fe256": dict(kind="fe3d", n=256, desc="3D 256^3 points, Q1 finite elements (cubic, h = 1/255), convection "
                                            "recipe coefficients (rho contrast 20 + 1% noise, Ma=0.01), x/y "
                                            "periodic, z walls, rtol 1e-8"),
@@ -64,7 +68,7 @@ NCU_TRAFFIC: dict = {
 def sweep_kernel(n):
     """Name of the sweep kernel the library picks for a finest level of n = (nx, ny, nz) cells."""
     nx, ny, nz = n
-    if ny > 1 and ny % 16 == 0 and nz >= 2 and nx in (128, 256):
+    if ny > 1 and ny % 16 == 0 and nz >= 2 and nx in (128, 256, 512):
         return "k_rbgs_row"
     if ny > 1 and nx % 32 == 0 and ny % 8 == 0 and nz >= 2:
         return "k_rbgs_zm"
@@ -304,9 +308,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if WORKLOADS[args.workload]["kind"] == "fe3d":
+    if WORKLOADS[args.workload]["kind"] in ("fe3d", "gresho2d"):
         print(json.dumps({"impl": "reference", "unavailable": "the CPU arm times the cell-centred oracle's "
-                          "Jacobi-PCG; the finite-element workload has no timed oracle arm"}), flush=True)
+                          "Jacobi-PCG solve; this workload has no timed oracle arm"}), flush=True)
         return
     r = oracle_subprocess("bench.oracle_report(%r, %d, %d, %d, 'all')" % (args.workload, args.oracle_iters,
                                                                             args.steps, args.warmup))
@@ -784,6 +788,117 @@ def run_fe(args):
         dist.destroy_process_group()
 
 
+def run_gresho(args):
+    """Time stepping of the Gresho vortex: W warm-up steps, then K timed
+    fractional steps of the resident state (CUDA events around each step on
+    the launching stream; every step ends with the solve's host check)."""
+    import torch
+
+    from paper_1112_3507_gb300 import inputs as I
+    from paper_1112_3507_gb300 import lowmach as lm
+    from paper_1112_3507_gb300.fractional import FractionalStep
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = WORKLOADS[args.workload]["n"]
+    g = I.gresho_vortex(n, 0.01, cfl=0.5 * args.dt_factor)
+    N = n * n
+    fs = FractionalStep(g["n"], g["h"], g["bc"], g["gamma"], rtol=1e-11)
+    fs.set_state(g["rho"], g["mom"], g["e"], stream)
+
+    def ke():
+        m = fs.mom.view(3, N)
+        return float(((m * m).sum(0) / fs.rho).sum()) * 0.5 * g["h"][0] * g["h"][2]
+
+    ke0 = ke()
+    for _ in range(args.warmup):
+        fs.step(g["dt"], stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = lm.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = []
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        iters.append(fs.step(g["dt"], stream)["iters"])
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = lm.kernel_launches() - launches0
+    clk = clocks.stop()
+    t_step = sum(a.elapsed_time(b) for a, b in ev) * 1e-3 / args.steps
+    ke1 = ke()
+
+    # phases of one step, each timed alone on the stream
+    dt = g["dt"]
+    ph = {
+        "advect": lambda: lm.advect(fs.n, fs.h, fs.bc, dt, fs.rho, fs.mom, fs.e, fs.rho1, fs.mom_s, fs.e_s,
+                                    stream=stream),
+        "projection_rhs": lambda: lm.projection_rhs(fs.n, fs.h, fs.bc, dt, fs.p, fs.rho, fs.cs2, fs.mom, fs.mom_s,
+                                                    fs.rho1, fs.f, fs.uf_s, stream=stream),
+        "coefficients": lambda: fs.grid.set_coefficients(fs.rho, fs.rho1, fs.cs2, dt, stream),
+        "projection_update": lambda: lm.projection_update(fs.n, fs.h, fs.bc, dt, fs.p, fs.rho1, fs.mom_s,
+                                                          fs.uf_s, fs.e_s, fs.mom1, fs.uf1, fs.e1, stream=stream),
+        "eos": lambda: lm.eos_ideal(fs.gamma, fs.rho1, fs.mom1, fs.e1, fs.p_pred, None, stream=stream),
+    }
+    phases = {k: time_kernel(torch, f, 10, stream) * 1e6 for k, f in ph.items()}
+    phases["solve_and_rest"] = t_step * 1e6 - sum(phases.values())
+
+    # the same steps with the float64 Jacobi-PCG solve
+    fj = FractionalStep(g["n"], g["h"], g["bc"], g["gamma"], mode="jacobi", rtol=1e-11)
+    fj.set_state(g["rho"], g["mom"], g["e"], stream)
+    fj.step(g["dt"], stream)
+    torch.cuda.synchronize()
+    j0 = time.perf_counter()
+    jit = [fj.step(g["dt"], stream)["iters"] for _ in range(5)]
+    torch.cuda.synchronize()
+    t_jac = (time.perf_counter() - j0) / 5
+    fj.close()
+
+    # end to end: host initial state in, K steps, final state out
+    host = [torch.from_numpy(np.ascontiguousarray(a.ravel())).pin_memory()
+            for a in (g["rho"], np.concatenate([m.ravel() for m in g["mom"]]), g["e"])]
+    outs = [torch.empty(N, dtype=torch.float64).pin_memory(), torch.empty(3 * N, dtype=torch.float64).pin_memory(),
+            torch.empty(N, dtype=torch.float64).pin_memory(), torch.empty(N, dtype=torch.float64).pin_memory()]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fs.rho.copy_(host[0], non_blocking=True)
+    fs.mom.copy_(host[1], non_blocking=True)
+    fs.e.copy_(host[2], non_blocking=True)
+    lm.eos_ideal(fs.gamma, fs.rho, fs.mom, fs.e, fs.p, fs.cs2, stream=stream)
+    for _ in range(args.steps):
+        fs.step(g["dt"], stream)
+    for o, d in zip(outs, (fs.rho, fs.mom, fs.e, fs.p)):
+        o.copy_(d, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_t = (time.perf_counter() - t0) / args.steps
+
+    fp64_rate = lm.probe_rate(0, 20000, stream)
+    adv_ops = 230                 # float64 operations a 2D cell in k_advect (two axes, five quantities)
+    line = {
+        "metric": METRIC, "value": N / t_step / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 step, f32+f64 solve", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "cells": N, "dt": g["dt"], "ma": 0.01,
+                   "dt_factor": args.dt_factor,
+                   "l2": "state resident in L2 (5 x %.1f MB)" % (N * 8 / 1e6)},
+        "solve_iters_per_step": float(np.mean(iters)), "kinetic_energy_ratio": ke1 / ke0,
+        "phases_us": phases,
+        "fp64_jacobi_pcg_step_ms": t_jac * 1e3, "fp64_jacobi_iters_per_step": float(np.mean(jit)),
+        "speedup_vs_fp64_pcg": t_jac / t_step,
+        "e2e": {"value": N / e2e_t / 1e9, "unit": UNIT, "h2d_bytes_per_step": 5 * 8 * N / args.steps,
+                "d2h_bytes_per_step": 6 * 8 * N / args.steps},
+        "roofline": {"kernel": "k_advect (float64 MUSCL advection, steps (i)-(iii))", "bound": "alu",
+                     "achieved": adv_ops * N / (phases["advect"] * 1e-6) / 1e12,
+                     "peak": fp64_rate / 1e12, "unit": "T float64 op/s",
+                     "frac": adv_ops * N / (phases["advect"] * 1e-6) / fp64_rate, "traffic": None,
+                     "peak_source": "lm_probe_rate float64 FMA/s, one operation an FMA (of measured)"},
+        "cpu_baseline": None, "clocks": clk, "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    fs.close()
+
+
 def run_kernel(args):
     """A few launches of one kernel, nothing else: the command the ncu captures
     of the sweep, the float32 apply and the network are taken on."""
@@ -844,6 +959,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true",
                     help="run warm-up and timed solves only (for profiler launch lists)")
+    ap.add_argument("--dt-factor", type=float, default=1.0,
+                    help="gresho256: the time step as a multiple of the sound-speed-induced one (CFL 0.5)")
     ap.add_argument("--kernel", choices=["sweep", "apply32", "net", "fe32"], default=None,
                     help="profiling runs: a few launches of one kernel on the workload's finest grid "
                          "(sweep: lm_mg_sweep, apply32: lm_apply in float32; net: U-Net forward on "
@@ -857,6 +974,8 @@ def main():
         run_batch(args)
     elif WORKLOADS[args.workload]["kind"] == "fe3d":
         run_fe(args)
+    elif WORKLOADS[args.workload]["kind"] == "gresho2d":
+        run_gresho(args)
     else:
         run_ours(args)
 

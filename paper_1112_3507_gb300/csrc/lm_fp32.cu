@@ -888,19 +888,22 @@ constexpr size_t rbgs_row_smem() {
     return sizeof(float2) * 5 * (TY + 4) * (32 * CPT + 4);
 }
 
-template <int CPT, int TY, int FIRST, bool ZERO, bool PROLONG>
+template <int CPT, int TY, int FIRST, bool ZERO, bool PROLONG, int SEG>
 __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* __restrict__ xin,
                                                         const float* __restrict__ ec, Geo C, int hx, int hy,
                                                         int hz, const float* __restrict__ f,
                                                         float* __restrict__ xout, int KZ) {
     constexpr int NX = 32 * CPT, M = NX / 2, RS = NX + 4, NRW = TY + 4, PL = NRW * RS, NR = 5, H = CPT / 2;
+    constexpr int W = NX * SEG;                           // cells in a grid row
     static_assert(CPT % 2 == 0 && TY >= 4 * H / 2 && TY >= 2 * H, "a warp per halo pair group");
+    static_assert(SEG == 1 || (SEG == 2 && 4 * NRW <= 32 * TY && 4 * TY <= 32 * TY), "x-halo threads");
     extern __shared__ float4 row_smem[];
     float2* XR = reinterpret_cast<float2*>(row_smem);
     const Geo& g = L.g;
     const int lane = threadIdx.x, wy = threadIdx.y, tid = lane + 32 * wy;
-    const int j0 = blockIdx.x * TY, k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
-    const int sz = NX * g.ny, i2 = 2 * lane;
+    const int j0 = (blockIdx.x / SEG) * TY, c0 = (blockIdx.x % SEG) * NX;
+    const int k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
+    const int sz = W * g.ny, i2 = 2 * lane;
     for (int t = tid; t < NR * NRW; t += 32 * TY) {      // the run-end ghosts: x = 0, rho = ROW_WALL
         const float2 gh = make_float2(0.f, ROW_WALL);
         XR[t * RS + run_e(M, -1)] = gh;
@@ -936,7 +939,23 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
     rowj(rT, jT);
     const bool hasS = uS < H, okS = hasS && rowj(rS, jS);
     const bool okF = uF < H && rowj(rF, jF);
-    const bool perx = g.bcx == LM_BC_PERIODIC;
+    // whole rows wrap around the staged row; a segment's x-neighbours outside
+    // it are the staged x-halo cells in the run-end slots
+    const bool perx = SEG == 1 && g.bcx == LM_BC_PERIODIC;
+
+    // x-halo of a segment (SEG > 1): threads 0 .. 4 NRW - 1 stage cell gG of
+    // staged row rG (gG = 0..3: columns c0 - 2, c0 - 1, c0 + NX, c0 + NX + 1,
+    // run slots E(-1), O(-1), E(M), O(M)); past a wall x = 0, rho = ROW_WALL
+    const bool hasG = SEG > 1 && tid < 4 * NRW;
+    const int rG = tid >> 2, gG = tid & 3;
+    int gCol = c0 + (gG == 0 ? -2 : gG == 1 ? -1 : gG == 2 ? NX : NX + 1);
+    bool gOK = true;
+    if (gCol < 0 || gCol >= W) {
+        if (g.bcx == LM_BC_PERIODIC) gCol = gCol < 0 ? gCol + W : gCol - W;
+        else gOK = false;
+    }
+    const int gSlot = gG == 0 ? run_e(M, -1) : gG == 1 ? run_o(M, -1) : gG == 2 ? run_e(M, M) : run_o(M, M);
+    float gxv = 0.f, grv = ROW_WALL, gev = 0.f;
 
     // staged plane: the own row (H pairs) and the halo pair, in registers
     float vx[CPT], vr[CPT], ve[CPT], sxh[2], srh[2], seh[2];
@@ -953,8 +972,8 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
         }
         if (PROLONG) {
             const int po = C.nx * (jw >> hy) + C.nx * C.ny * (pw >> hz);
-            E[0] = ec[po + ((64 * u + i2) >> hx)];
-            E[1] = ec[po + ((64 * u + i2 + 1) >> hx)];
+            E[0] = ec[po + ((c0 + 64 * u + i2) >> hx)];
+            E[1] = ec[po + ((c0 + 64 * u + i2 + 1) >> hx)];
         }
     };
     auto wall_pair = [&](float* X, float* R, float* E) {
@@ -967,12 +986,25 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
         const bool okp = plane(p, pw);
 #pragma unroll
         for (int u = 0; u < H; ++u) {
-            if (okp) fetch_pair(sz * pw + NX * jT + 64 * u + i2, pw, jT, u, vx + 2 * u, vr + 2 * u, ve + 2 * u);
+            if (okp) fetch_pair(sz * pw + W * jT + c0 + 64 * u + i2, pw, jT, u, vx + 2 * u, vr + 2 * u, ve + 2 * u);
             else wall_pair(vx + 2 * u, vr + 2 * u, ve + 2 * u);
         }
         if (hasS) {
-            if (okp && okS) fetch_pair(sz * pw + NX * jS + 64 * uS + i2, pw, jS, uS, sxh, srh, seh);
+            if (okp && okS) fetch_pair(sz * pw + W * jS + c0 + 64 * uS + i2, pw, jS, uS, sxh, srh, seh);
             else wall_pair(sxh, srh, seh);
+        }
+        if (SEG > 1 && hasG) {                            // x-halo cell gG of staged row rG
+            int jw = 0;
+            if (okp && rowj(rG, jw) && gOK) {
+                const int o = sz * pw + W * jw + gCol;
+                gxv = ZERO ? 0.f : xin[o];
+                grv = L.rho[o];
+                if (PROLONG) gev = ec[C.nx * (jw >> hy) + C.nx * C.ny * (pw >> hz) + (gCol >> hx)];
+            } else {
+                gxv = 0.f;
+                grv = ROW_WALL;
+                gev = 0.f;
+            }
         }
     };
     // pair m = lane + 32 u of row r: cell 2 m to run E, cell 2 m + 1 to run O
@@ -984,6 +1016,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
 #pragma unroll
         for (int u = 0; u < H; ++u) store_pair((s * NRW + rT) * RS, lane + 32 * u, vx + 2 * u, vr + 2 * u, ve + 2 * u);
         if (hasS) store_pair((s * NRW + rS) * RS, lane + 32 * uS, sxh, srh, seh);
+        if (SEG > 1 && hasG) XR[(s * NRW + rG) * RS + gSlot] = make_float2(PROLONG ? gxv + gev : gxv, grv);
     };
     // f and c~ of cells 2 (lane + 32 u) + a, u < n, of a row at offset rowoff of plane p
     auto load_fc = [&](int p, bool ok, int rowoff, int a, float* F, float* Cv, int n) {
@@ -1011,17 +1044,46 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
     // array and plane), PF_PLANES steps before their first use: x and rho of
     // plane P are staged at step P - 2, f and c~ first read at step P - 1.
     // Array a = 0..3 (x, rho, f, c~) is requested by thread a.
+    // (a segment's rows are not contiguous: one request per row, thread
+    // a * TY + r for array a and row r)
+    constexpr int NPF = SEG == 1 ? 4 : 4 * TY;
+    const int pfa = SEG == 1 ? tid : tid / TY, pfr = SEG == 1 ? 0 : tid % TY;
     auto prefetch = [&](int a, int P) {
         int pw = 0;
         if (P > (a < 2 ? k1 + 1 : k1) || (ZERO && a == 0) || !plane(P, pw)) return;
         const float* base = a == 0 ? xin : a == 1 ? L.rho : a == 2 ? f : L.ct;
-        prefetch_l2(base + sz * pw + NX * j0, NX * TY * sizeof(float));
+        if (SEG == 1) prefetch_l2(base + sz * pw + NX * j0, NX * TY * sizeof(float));
+        else prefetch_l2(base + sz * pw + W * (j0 + pfr) + c0, NX * sizeof(float));
     };
-    if (tid < 4)
-        for (int d = 1; d <= PF_PLANES; ++d) prefetch(tid, (tid < 2 ? k0 : k0 - 1) + d);
+    if (tid < NPF)
+        for (int d = 1; d <= PF_PLANES; ++d) prefetch(pfa, (pfa < 2 ? k0 : k0 - 1) + d);
     auto gs_row = [&](int a, int b, int dzm, int dzp, const float* F, const float* Cv) {
         if (a) gs_row_runs<CPT, 1>(XR, b, lane, perx, RS, dzm, dzp, F, Cv, L.c2x, L.c2y, L.c2z);
         else gs_row_runs<CPT, 0>(XR, b, lane, perx, RS, dzm, dzp, F, Cv, L.c2x, L.c2y, L.c2z);
+    };
+    // The first-colour x-halo cell of the warp's own row (SEG > 1): column
+    // c0 - 1 when the row's first colour is odd, c0 + NX when even; lane 0
+    // updates it with the first colour of its plane (the second-colour cells
+    // at the segment's ends read it), f and c~ loaded a step ahead.
+    float fX = 0.f, cX = 1.f;
+    int xCol = 0;
+    bool xOK = false;
+    auto load_fcx = [&](int p) {
+        if (SEG == 1 || lane != 0) return;
+        int pw = 0;
+        xOK = false;
+        if (p > k1 || !plane(p, pw)) return;
+        const int aT = parity(jTu, p, FIRST);
+        int col = aT ? c0 - 1 : c0 + NX;
+        if (col < 0 || col >= W) {
+            if (g.bcx != LM_BC_PERIODIC) return;
+            col = col < 0 ? col + W : col - W;
+        }
+        xCol = col;
+        xOK = true;
+        const int o = sz * pw + W * jT + col;
+        fX = f[o];
+        cX = L.ct[o];
     };
     float fT[H], cT[H], fS[H], cS[H], fF[1], cF[1];
 #pragma unroll
@@ -1038,17 +1100,26 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
     }
     // slots of planes p - 3 .. p + 1 at step p = k0 - 1 (rotated each step)
     int s_m3 = (k0 + 6) % NR, s_m2 = (k0 + 7) % NR, s_m1 = (k0 + 8) % NR, s_0 = (k0 + 9) % NR, s_p1 = (k0 + 10) % NR;
-    load_fc(k0 - 1, true, NX * jT, parity(jTu, k0 - 1, FIRST), fT, cT, H);
-    load_fc(k0 - 1, okF, NX * jF + 64 * uF, parity(jFu, k0 - 1, FIRST), fF, cF, 1);
+    load_fc(k0 - 1, true, W * jT + c0, parity(jTu, k0 - 1, FIRST), fT, cT, H);
+    load_fc(k0 - 1, okF, W * jF + c0 + 64 * uF, parity(jFu, k0 - 1, FIRST), fF, cF, 1);
+    load_fcx(k0 - 1);
     __syncthreads();
     for (int p = k0 - 1; p <= k1 + 2; ++p) {
         const bool stage = p + 2 <= k1 + 1;
-        if (tid < 4) prefetch(tid, (tid < 2 ? p + 2 : p + 1) + PF_PLANES);
+        if (tid < NPF) prefetch(pfa, (pfa < 2 ? p + 2 : p + 1) + PF_PLANES);
         if (stage) fetch(p + 2);
         int pw = 0;
         if (p <= k1 && plane(p, pw)) {                    // first colour on plane p
             const int dzm = (s_m1 - s_0) * PL, dzp = (s_p1 - s_0) * PL;
             gs_row(parity(jTu, p, FIRST), (s_0 * NRW + rT) * RS, dzm, dzp, fT, cT);
+            if (SEG > 1 && lane == 0 && xOK) {            // the own row's first-colour x-halo cell
+                const int b = (s_0 * NRW + rT) * RS;
+                if (parity(jTu, p, FIRST)) {
+                    XR[b + run_o(M, -1)].x = gs_run<1>(XR, b, M, -1, false, RS, dzm, dzp, fX, cX, L.c2x, L.c2y, L.c2z);
+                } else {
+                    XR[b + run_e(M, M)].x = gs_run<0>(XR, b, M, M, false, RS, dzm, dzp, fX, cX, L.c2x, L.c2y, L.c2z);
+                }
+            }
             if (okF) {                                    // this warp's pair group of a halo row
                 const int aF = parity(jFu, p, FIRST), b = (s_0 * NRW + rF) * RS, m = lane + 32 * uF;
                 const bool wrapF = perx && (aF ? (uF == H - 1 && lane == 31) : (uF == 0 && lane == 0));
@@ -1057,16 +1128,17 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
                 XR[b + (aF ? run_o(M, m) : run_e(M, m))].x = v;
             }
         }
-        load_fc(p + 1, p + 1 <= k1, NX * jT, parity(jTu, p + 1, FIRST), fT, cT, H);
-        load_fc(p + 1, okF && p + 1 <= k1, NX * jF + 64 * uF, parity(jFu, p + 1, FIRST), fF, cF, 1);
+        load_fc(p + 1, p + 1 <= k1, W * jT + c0, parity(jTu, p + 1, FIRST), fT, cT, H);
+        load_fc(p + 1, okF && p + 1 <= k1, W * jF + c0 + 64 * uF, parity(jFu, p + 1, FIRST), fF, cF, 1);
+        load_fcx(p + 1);
         const int q = p - 2;
         if (q >= k0 && q < k1)                            // second colour on plane p - 2
             gs_row(parity(jTu, q, 1 - FIRST), (s_m2 * NRW + rT) * RS, (s_m3 - s_m2) * PL, (s_m1 - s_m2) * PL, fS,
                    cS);
-        load_fc(q + 1, q + 1 >= k0 && q + 1 < k1, NX * jT, parity(jTu, q + 1, 1 - FIRST), fS, cS, H);
+        load_fc(q + 1, q + 1 >= k0 && q + 1 < k1, W * jT + c0, parity(jTu, q + 1, 1 - FIRST), fS, cS, H);
         if (p - 3 >= k0 && p - 3 < k1) {                  // plane p - 3 is final
             const int b = (s_m3 * NRW + rT) * RS;
-            float* dst = xout + sz * (p - 3) + NX * jT + i2;
+            float* dst = xout + sz * (p - 3) + W * jT + c0 + i2;
 #pragma unroll
             for (int u = 0; u < H; ++u) {
                 const int m = lane + 32 * u;
@@ -1637,15 +1709,15 @@ void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int h
 
 // The whole-row sweep's shared memory exceeds the default 48 KB: raise the
 // limit of every instantiation (host, once per hierarchy build).
-template <int CPT, int TY>
+template <int CPT, int TY, int SEG = 1>
 static void rbgs_row_allow() {
     const int sm = (int)rbgs_row_smem<CPT, TY>();
-    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 0, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 1, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 0, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 1, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 0, false, false, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 1, false, false, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 0, true, false, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 1, true, false, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 0, false, true, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 1, false, true, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 template <int CPT, int TY>
 static void apply_row_allow() {
@@ -1657,6 +1729,7 @@ static void apply_row_allow() {
 void rbgs_row_allow_smem() {
     rbgs_row_allow<8, 16>();
     rbgs_row_allow<4, 16>();
+    rbgs_row_allow<8, 16, 2>();
     apply_row_allow<8, 16>();
     apply_row_allow<4, 16>();
     cudaFuncSetAttribute(k_resid_restrict_row<8, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1668,17 +1741,28 @@ void rbgs_row_allow_smem() {
 static bool aligned8(const void* p) { return ((uintptr_t)p & 7) == 0; }
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
-template <int CPT>
+template <int CPT, int SEG = 1>
 static void launch_rbgs_row(const Lev32& L, cudaStream_t s, const float* xin, const float* ec, const Geo& Cg,
                             int hx, int hy, int hz, const float* f, float* xout, int first, int zero, int prolong) {
     constexpr int TY = 16;
     const Geo& g = L.g;
-    const int ntile = g.ny / TY;
-    const int chunks = std::max(1, std::min(g.nz / 2, 152 / ntile));
-    const int KZ = hdiv(g.nz, chunks);
+    const int ntile = g.ny / TY * SEG;
+    // z chunks (one block per SM fits): the count that maximises the busy
+    // fraction of the last wave times the share of planes a chunk does not
+    // stage twice (KZ / (KZ + 4))
+    int KZ = g.nz;
+    double best = -1.0;
+    for (int c = 1; c <= std::max(1, g.nz / 2); ++c) {
+        const int kz = hdiv(g.nz, c), blocks = ntile * hdiv(g.nz, kz);
+        const double eff = (double)blocks / (hdiv(blocks, 152) * 152.0) * kz / (kz + 4.0);
+        if (eff > best + 1e-9) {
+            best = eff;
+            KZ = kz;
+        }
+    }
     const dim3 grd(ntile, hdiv(g.nz, KZ)), blk(32, TY);
     const size_t sm = rbgs_row_smem<CPT, TY>();
-#define LM_ROW(F, Z, P) k_rbgs_row<CPT, TY, F, Z, P><<<grd, blk, sm, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout, KZ)
+#define LM_ROW(F, Z, P) k_rbgs_row<CPT, TY, F, Z, P, SEG><<<grd, blk, sm, s>>>(L, xin, ec, Cg, hx, hy, hz, f, xout, KZ)
     if (zero) { if (first) LM_ROW(1, true, false); else LM_ROW(0, true, false); }
     else if (prolong) { if (first) LM_ROW(1, false, true); else LM_ROW(0, false, true); }
     else { if (first) LM_ROW(1, false, false); else LM_ROW(0, false, false); }
@@ -1692,10 +1776,12 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
     const Geo& g = L.g;
     const Geo Cg = C ? C->g : g;
     count_launches(1);
-    if (kz <= 0 && g.ny > 1 && g.ny % 16 == 0 && g.nz >= 2 && (g.nx == 256 || g.nx == 128) && aligned8(xin) &&
-        aligned8(xout) && aligned8(ec)) {
-        // whole rows of 256 or 128 cells: a warp per row, 16 rows per block
-        if (g.nx == 256) launch_rbgs_row<8>(L, s, xin, ec, Cg, hx, hy, hz, f, xout, first, zero, prolong);
+    if (kz <= 0 && g.ny > 1 && g.ny % 16 == 0 && g.nz >= 2 && (g.nx == 512 || g.nx == 256 || g.nx == 128) &&
+        aligned8(xin) && aligned8(xout) && aligned8(ec)) {
+        // whole rows of 256 or 128 cells, or 512-cell rows as two 256-cell
+        // segments with an x-halo: a warp per row, 16 rows per block
+        if (g.nx == 512) launch_rbgs_row<8, 2>(L, s, xin, ec, Cg, hx, hy, hz, f, xout, first, zero, prolong);
+        else if (g.nx == 256) launch_rbgs_row<8>(L, s, xin, ec, Cg, hx, hy, hz, f, xout, first, zero, prolong);
         else launch_rbgs_row<4>(L, s, xin, ec, Cg, hx, hy, hz, f, xout, first, zero, prolong);
         return;
     }

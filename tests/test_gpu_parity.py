@@ -54,6 +54,11 @@ PROBLEMS = {
     "rows3d-256x32x8": lambda: I.make_problem(256, 8, 32, ma=0.01, contrast=15.0, noise=0.01, seed=12),
     "rows3d-walls-256x16x8": lambda: I.make_problem(256, 8, 16, ma=0.02, contrast=10.0, noise=0.01, seed=13,
                                                     bc=(NEU, NEU, NEU)),
+    # 512-cell rows as two 256-cell segments with an x-halo (periodic x, and
+    # walls at both x ends)
+    "rows3d-512x16x12": lambda: I.make_problem(512, 12, 16, ma=0.01, contrast=15.0, noise=0.01, seed=14),
+    "rows3d-walls-512x32x6": lambda: I.make_problem(512, 6, 32, ma=0.02, contrast=10.0, noise=0.01, seed=15,
+                                                    bc=(NEU, PER, NEU)),
 }
 
 
@@ -143,7 +148,8 @@ def test_apply_fp32(name):
                                      ("ragged2d-37x50-walls", 1), ("conv3d-16", 2), ("plain2d-64", 3),
                                      ("box3d-64x16x24", 1), ("box3d-64x16x24", 2), ("box3d-walls-32x8x16", 2),
                                      ("rows2d-256x24", 2), ("rows2d-walls-512x10", 1), ("rows3d-256x32x8", 2),
-                                     ("rows3d-walls-256x16x8", 1)])
+                                     ("rows3d-walls-256x16x8", 1), ("rows3d-512x16x12", 2),
+                                     ("rows3d-walls-512x32x6", 1)])
 def test_vcycle_matches_oracle(name, nu):
     """Row a4: one float32 V-cycle z = M r vs the oracle's float64 V-cycle on
     the same (float32-rounded) coefficients; same hierarchy."""
@@ -169,7 +175,8 @@ def test_vcycle_matches_oracle(name, nu):
 
 @pytest.mark.parametrize("name", ["plain2d-64", "conv3d-16", "ragged3d-12x6x10", "ragged2d-37x50-walls",
                                   "column-1x1x40", "box3d-64x16x24", "box3d-walls-32x8x16", "rows2d-256x24",
-                                  "rows2d-walls-512x10", "rows3d-256x32x8", "rows3d-walls-256x16x8"])
+                                  "rows2d-walls-512x10", "rows3d-256x32x8", "rows3d-walls-256x16x8",
+                                  "rows3d-512x16x12", "rows3d-walls-512x32x6"])
 @pytest.mark.parametrize("order", [0, 1])
 def test_sweep_matches_oracle(name, order):
     """Row a4 smoother: one float32 red-black (or black-red) Gauss-Seidel
@@ -218,13 +225,14 @@ def test_jacobi_pcg_parity(name):
 def test_multigrid_modes_parity(name, mode, bar):
     """Rows a4/a5: float64 FCG with the float32 V-cycle, and float64
     iterative refinement around float32 FCG + V-cycle, vs the direct solve.
-    The residual target is 1e-13, except on the 65 K-cell whole-row grid,
-    whose float64 residual floor (rounding in A x over longer rows and more
-    cells) lies just above it: 3e-13 there."""
+    The residual target is 1e-13, except on the large whole-row grids, whose
+    float64 residual floor (rounding in A x over longer rows and more cells)
+    lies above it: the oracle's own direct solution leaves 1.5e-13 on the
+    256 x 32 x 8 grid and 2.2e-13 on the 512 x 16 x 12 one."""
     p = PROBLEMS[name]()
     op = P.operator_from_problem(p)
     xs = _direct(name, p, op)
-    tol = 3e-13 if name == "rows3d-256x32x8" else 1e-13
+    tol = {"rows3d-256x32x8": 3e-13, "rows3d-512x16x12": 5e-13}.get(name, 1e-13)
     with _grid(p) as g:
         r = g.solve(mode=mode, rtol=tol, max_iter=2000, max_outer=30)
         x = g.solution()
