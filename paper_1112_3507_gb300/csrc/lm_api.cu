@@ -460,6 +460,117 @@ bool ensure_inner_graphs(lm_grid* g, const lm_solve_opts* o) {
     return true;
 }
 
+// Set-up of a device-side inner solve: the inner state (tolerance rtol,
+// nothing done) and the iteration counter.
+__global__ void k_inner_init(SolveState* st, double rtol, int* it) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        SolveState h{};
+        h.rtol = rtol;
+        *st = h;
+        *it = 0;
+    }
+}
+
+// End of an inner iteration of the device-side loop: count it and keep
+// looping while the inner solve has neither broken down nor reached its
+// tolerance, below the iteration limit.
+__global__ void k_inner_cond(SolveState* st, int* it, int max_it, cudaGraphConditionalHandle loop) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int n = *it + 1;
+        *it = n;
+        st->iters = n;
+        const bool more = !st->status && st->rel > st->rtol && n < max_it;
+        cudaGraphSetConditional(loop, more ? 1u : 0u);
+    }
+}
+
+// The inner solve with the V-cycle as one graph: e = 0, the inner state,
+// ||r||, the first iteration, then a while node (condition set by
+// k_inner_cond) repeating the later iteration.  Captured once per
+// hierarchy version, smoothing counts, tolerance and iteration limit;
+// returns false when capture is unavailable.
+bool ensure_loop_graph(lm_grid* g, const lm_solve_opts* o) {
+    if (g->loop_exec && g->loop_version == g->version && g->loop_nu1 == o->nu1 && g->loop_nu2 == o->nu2 &&
+        g->loop_max == o->inner_max_iter && g->loop_rtol == o->inner_rtol)
+        return true;
+    if (g->loop_exec) {
+        cudaGraphExecDestroy(g->loop_exec);
+        g->loop_exec = nullptr;
+    }
+    if (!g->cap_stream && cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (!g->cap_body && cudaStreamCreateWithFlags(&g->cap_body, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (!g->d_inner_it && cudaMalloc(&g->d_inner_it, sizeof(int)) != cudaSuccess) return false;
+    const Red red{g->part, g->scal, g->ctr};
+    cudaStream_t cs = g->cap_stream;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    const long long before = lm_kernel_launches();
+    bool ok = cudaMemsetAsync(g->e32, 0, sizeof(float) * g->N, cs) == cudaSuccess;
+    k_inner_init<<<1, 32, 0, cs>>>(g->st_in, o->inner_rtol, g->d_inner_it);
+    count_launches(1);
+    launch_dot32(g->N, g->G, cs, g->r32, g->r32, red, 4, g->st_in);
+    inner_iteration(g, o, cs, true);
+    cudaGraphConditionalHandle loop{};
+    cudaGraph_t cg = nullptr;
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    ok = ok && cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps) == cudaSuccess &&
+         cudaGraphConditionalHandleCreate(&loop, cg, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        k_inner_cond<<<1, 32, 0, cs>>>(g->st_in, g->d_inner_it, o->inner_max_iter, loop);
+        count_launches(1);
+        ok = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps) == cudaSuccess;
+    }
+    const long long n_pro = lm_kernel_launches() - before;
+    long long n_body = 0;
+    cudaGraphNode_t cnode{};
+    if (ok) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = loop;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp) == cudaSuccess;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if (ok && cudaStreamBeginCaptureToGraph(g->cap_body, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const long long b0 = lm_kernel_launches();
+            inner_iteration(g, o, g->cap_body, false);
+            k_inner_cond<<<1, 32, 0, g->cap_body>>>(g->st_in, g->d_inner_it, o->inner_max_iter, loop);
+            count_launches(1);
+            n_body = lm_kernel_launches() - b0;
+            ok = cudaStreamEndCapture(g->cap_body, &body) == cudaSuccess;
+        } else {
+            ok = false;
+        }
+        ok = ok && cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                       cudaSuccess;
+    }
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    count_launches(-(n_pro + n_body));                 // captured, not launched
+    if (!ok || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return false;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&g->loop_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        g->loop_exec = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    g->loop_nk[0] = n_pro;
+    g->loop_nk[1] = n_body;
+    g->loop_version = g->version;
+    g->loop_nu1 = o->nu1;
+    g->loop_nu2 = o->nu2;
+    g->loop_max = o->inner_max_iter;
+    g->loop_rtol = o->inner_rtol;
+    return true;
+}
+
 // Inner float32 flexible CG on A32 e = r (r overwritten).  Preconditioner:
 // the V-cycle, or (*use_net) the learned two-level cycle above; a network
 // preconditioner that leaves the inner residual above 1/2 after 4
@@ -469,6 +580,16 @@ int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, in
     int rc;
     MgLevel& M = g->mg[0];
     const Red red{g->part, g->scal, g->ctr};
+    if (!(use_net && *use_net) && ensure_loop_graph(g, o)) {
+        // the whole inner solve on the device: one launch, one host check
+        CK(cudaGraphLaunch(g->loop_exec, s));
+        if ((rc = sync_state(g, g->st_in, s))) return rc;
+        const int n = std::max(1, g->st_host->iters);
+        count_launches(g->loop_nk[0] + (long long)(n - 1) * g->loop_nk[1]);
+        *iters += n;
+        *vcycles += n;
+        return LM_OK;
+    }
     CK(cudaMemsetAsync(g->e32, 0, sizeof(float) * g->N, s));
     if ((rc = init_state(g, g->st_in, o->inner_rtol, s))) return rc;
     // the inner problem's reference norm: ||r|| of its right-hand side
@@ -782,7 +903,10 @@ void lm_grid_destroy(lm_grid* g) {
     if (g->ev1) cudaEventDestroy(g->ev1);
     for (cudaGraphExec_t& e : g->ig_exec)
         if (e) cudaGraphExecDestroy(e);
+    if (g->loop_exec) cudaGraphExecDestroy(g->loop_exec);
+    cudaFree(g->d_inner_it);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->cap_body) cudaStreamDestroy(g->cap_body);
     delete g;
 }
 

@@ -85,6 +85,17 @@ struct lm_grid {
     // first and the later ones), captured on cap_stream for hierarchy
     // version ig_version and smoothing (ig_nu1, ig_nu2); ig_nk kernels each
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_body = nullptr;     // captures the body of the device-side loop
+    // The whole inner solve as one graph: its set-up, the first iteration,
+    // then a conditional while node repeating the later iteration until the
+    // inner tolerance or the iteration limit (loop_nk: kernels before the
+    // loop and in one loop pass); keyed like ig_exec plus the limit
+    cudaGraphExec_t loop_exec = nullptr;
+    long long loop_nk[2] = {0, 0};
+    unsigned loop_version = ~0u;
+    int loop_nu1 = -1, loop_nu2 = -1, loop_max = -1;
+    double loop_rtol = -1.0;
+    int* d_inner_it = nullptr;           // iterations of the current inner solve (device)
     cudaGraphExec_t ig_exec[2] = {nullptr, nullptr};
     long long ig_nk[2] = {0, 0};
     unsigned ig_version = ~0u;
