@@ -736,7 +736,7 @@ def run_fe(args):
     torch.cuda.synchronize()
     t_jac = time.perf_counter() - b0
 
-    # roofline of the float32 finite-element apply (k_fe3t_32), timed alone
+    # roofline of the float32 finite-element apply (k_fe3_32), timed alone
     x32 = torch.randn(N, dtype=torch.float32, device=dev)
     y32 = torch.empty_like(x32)
     reps = 20
@@ -770,7 +770,7 @@ def run_fe(args):
             "speedup_vs_fp64_pcg": t_jac / t_solve,
             "e2e": {"value": job_value(N, args.steps, world, e2e_t), "unit": UNIT,
                     "h2d_bytes_per_step": 4 * 8 * N, "d2h_bytes_per_step": 8 * N},
-            "roofline": {"kernel": "k_fe3t_32 (float32 Q1 finite-element apply, row f1)", "bound": "hbm",
+            "roofline": {"kernel": "k_fe3_32 (float32 Q1 finite-element apply, row f1)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "bytes_per_point": ap_bytes, "launch_us": t_ap * 1e6,
                          "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks

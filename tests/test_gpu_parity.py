@@ -401,3 +401,23 @@ def test_first_call_in_a_fresh_process_is_the_float32_apply():
     root = __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("inner_max", [1, 3])
+def test_inner_iteration_limit(inner_max):
+    """The device-side inner loop stops at inner_max_iter iterations per
+    refinement step: with 1 the counts of inner iterations and refinement
+    steps agree, with 3 no step exceeds 3; both still reach the oracle's
+    solution."""
+    p = PROBLEMS["plain2d-64"]()
+    op = P.operator_from_problem(p)
+    xs = _direct("plain2d-64", p, op)
+    with _grid(p) as g:
+        r = g.solve(mode="mixed", rtol=1e-10, inner_max_iter=inner_max, max_outer=400, max_iter=4000)
+        x = g.solution()
+    assert r["rel_residual"] <= 1e-10
+    if inner_max == 1:
+        assert r["iters"] == r["outer_iters"]
+    else:
+        assert r["iters"] <= inner_max * r["outer_iters"]
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
