@@ -1,5 +1,5 @@
 // Arithmetic-rate probes: the measured float64 roof that the float64 kernels
-// of the solver are judged against.
+// of the solver are measured against.
 //
 // GB300 issues float64 at a small fraction of its float32 rate, so a float64
 // stencil can be bound by its arithmetic rather than by HBM.  These kernels
