@@ -490,8 +490,12 @@ __device__ __forceinline__ float stencil3p(const float (&Xm)[3][3], const float 
 // Three plane arrays rotate roles (the loop unrolled three times, so no
 // value moves).  (Issuing the next plane's loads before the point's
 // arithmetic, with a fourth array, measured slower: 148 against 140 us.)
+// (Four blocks per SM, 64 registers, for the solver's variants: measured
+// 24.2 against 25.8 ms per 256^3 solve; the plain apply is faster at three
+// blocks, 135 against 154 us, and keeps its 80 registers.)
 template <int MODE, int DOTS, bool FACES>
-__global__ void __launch_bounds__(256) k_fe3_32(FeOp<float> op, FeIO32 io, Red red, int KZ) {
+__global__ void __launch_bounds__(256, (MODE == M_APPLY && DOTS == 0) ? 1 : 4)
+    k_fe3_32(FeOp<float> op, FeIO32 io, Red red, int KZ) {
     const FeGeo& g = op.g;
     const int ti = blockIdx.x * 32 + threadIdx.x, tj = blockIdx.y * 8 + threadIdx.y;
     const bool live = ti < g.nx && tj < g.ny;
