@@ -127,3 +127,106 @@ def test_row_schedule_catches_a_one_plane_lag():
     np.testing.assert_allclose(good, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
     bad = _row_schedule_sweep(level, x, f, 0, 16, 3, lag=1)
     assert not np.allclose(bad, ref, rtol=1e-6, atol=1e-6)
+
+
+def _segment_schedule_sweep(level, x_in, f, first, NX, KZ, halo_update=True):
+    """The schedule of the segmented sweeps (the 2D sweep's warp per 128-cell
+    segment and half chunk, and the 3D sweep's 512-cell rows in two
+    segments), replayed on a 2D grid: a segment stages its NX cells plus two
+    cells each side (wrapped, or absent past a wall), updates at step p the
+    first colour of row p on its cells and on the one outside cell of that
+    colour, and the second colour of row p - 2 on its cells; row p - 3 is
+    then final.  halo_update=False plants the mistake of leaving the outside
+    cell at its input value."""
+    nz, _, nx = level.shape
+    bcx, _, bcz = level.bc
+    g = _faces(level)
+    ct = level.ct
+    out = np.full_like(x_in, np.nan)
+
+    def wrap(n, c, bc):
+        if 0 <= c < n:
+            return c
+        return c % n if bc == PER else None
+
+    for c0 in range(0, nx, NX):
+        cols = [wrap(nx, c0 - 2 + t, bcx) for t in range(NX + 4)]
+        for k0 in range(0, nz, KZ):
+            k1 = min(k0 + KZ, nz)
+
+            def stage(p):
+                kw = wrap(nz, p, bcz)
+                a = np.zeros(NX + 4)
+                if kw is not None:
+                    for t, cw in enumerate(cols):
+                        if cw is not None:
+                            a[t] = x_in[kw, 0, cw]
+                return a
+
+            ring = {p: stage(p) for p in (k0 - 2, k0 - 1, k0)}
+
+            def value(snap, p, t):
+                """Gauss-Seidel value of staged position t of row p."""
+                kw, cw = wrap(nz, p, bcz), cols[t]
+                xc = snap[p]
+                num = f[kw, 0, cw] + g[0][kw, 0, cw] * xc[t - 1] + g[1][kw, 0, cw] * xc[t + 1]
+                num = num + g[4][kw, 0, cw] * snap[p - 1][t] + g[5][kw, 0, cw] * snap[p + 1][t]
+                d = ct[kw, 0, cw] + sum(g[q][kw, 0, cw] for q in (0, 1, 4, 5))
+                return num / d
+
+            for p in range(k0 - 1, k1 + 3):
+                snap = {q: a.copy() for q, a in ring.items()}
+                writes = []
+                if p <= k1 and wrap(nz, p, bcz) is not None:
+                    kw = wrap(nz, p, bcz)
+                    for t in range(2, NX + 2):
+                        if ((cols[t] + kw) & 1) == first:
+                            writes.append((p, t, value(snap, p, t)))
+                    if halo_update:
+                        for t in (1, NX + 2):                # the outside cell of the first colour
+                            if cols[t] is not None and ((cols[t] + kw) & 1) == first:
+                                writes.append((p, t, value(snap, p, t)))
+                q = p - 2
+                if k0 <= q < k1:
+                    kw = wrap(nz, q, bcz)
+                    for t in range(2, NX + 2):
+                        if ((cols[t] + kw) & 1) == 1 - first:
+                            writes.append((q, t, value(snap, q, t)))
+                for pl, t, v in writes:
+                    ring[pl][t] = v
+                w = p - 3
+                if k0 <= w < k1:
+                    out[w, 0, c0:c0 + NX] = ring[w][2:NX + 2]
+                    del ring[w]
+                if p + 2 <= k1 + 1:
+                    ring[p + 2] = stage(p + 2)
+    return out
+
+
+@pytest.mark.parametrize("shape,bc,NX,KZ", [
+    ((9, 1, 16), (PER, PER, NEU), 8, 3),         # (nz, 1, nx); bc per axis x, y, z
+    ((8, 1, 24), (NEU, PER, PER), 8, 4),
+    ((7, 1, 16), (NEU, PER, NEU), 4, 2),
+    ((6, 1, 8), (PER, PER, PER), 8, 6),          # one segment: its outside cells wrap onto itself
+])
+@pytest.mark.parametrize("order", ["RB", "BR"])
+def test_segment_schedule_equals_sequential_sweep(shape, bc, NX, KZ, order):
+    rng = np.random.default_rng(sum(shape) + NX)
+    level = OM.Level(rng.uniform(0.05, 1.0, shape), rng.uniform(1.0, 20.0, shape), (0.3, 1.0, 0.7), bc)
+    x, f = rng.standard_normal(shape), rng.standard_normal(shape)
+    ref = OM.sweep(level, x, f, order)
+    got = _segment_schedule_sweep(level, x, f, 0 if order == "RB" else 1, NX, KZ)
+    assert not np.isnan(got).any()
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_segment_schedule_needs_the_outside_update():
+    """Planted mistake: without the first-colour update of the outside cell,
+    the second colour at a segment's end reads a stale neighbour."""
+    shape, bc = (8, 1, 24), (NEU, PER, PER)
+    rng = np.random.default_rng(7)
+    level = OM.Level(rng.uniform(0.05, 1.0, shape), rng.uniform(1.0, 20.0, shape), (0.3, 1.0, 0.7), bc)
+    x, f = rng.standard_normal(shape), rng.standard_normal(shape)
+    ref = OM.sweep(level, x, f, "RB")
+    bad = _segment_schedule_sweep(level, x, f, 0, 8, 4, halo_update=False)
+    assert not np.allclose(bad, ref, rtol=1e-6, atol=1e-6)
