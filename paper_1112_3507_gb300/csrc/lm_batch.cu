@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(128, 8) kb_rbgs(const BTask* __restrict__ T, c
     const float* xin = ZERO ? nullptr : lev_buf(V, src);
     float* xout = lev_buf(V, dst);
     if (V.L.g.nx % 256 == 0 && V.L.g.nz >= 2)        // whole 256-cell rows: the z-march (same tiles)
-        zm2d_tile<FIRST, ZERO, PROLONG>(V.L, xin, PROLONG ? V.ec : nullptr, V.C, PROLONG ? V.hx : 0,
+        zrow2d_tile<FIRST, ZERO, PROLONG>(V.L, xin, PROLONG ? V.ec : nullptr, V.C, PROLONG ? V.hx : 0,
                                         PROLONG ? V.hz : 0, V.f, xout, V.kz, t.bx, t.by);
     else
         rbgs_tile<128, 1, false, FIRST, ZERO, PROLONG>(V.L, xin, PROLONG ? V.ec : nullptr, V.C, PROLONG ? V.hx : 0,
@@ -410,11 +410,11 @@ std::string gpu_name() {
 // on this level's own data (into its scratch buffer), remembered per shape.
 int tune_sweep_kz(const MgLevel& M, const float* fin, float* scratch, cudaStream_t s, bool* changed) {
     char key[256];
-    snprintf(key, sizeof key, "%s|rbgs2d-zm|%dx%d|bc%d%d|f32", gpu_name().c_str(), M.L.g.nx, M.L.g.nz, M.L.g.bcx,
+    snprintf(key, sizeof key, "%s|rbgs2d-zrow|%dx%d|bc%d%d|f32", gpu_name().c_str(), M.L.g.nx, M.L.g.nz, M.L.g.bcx,
              M.L.g.bcz);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) return it->second;
-    const int cands[] = {4, 8, 16, 32, 64};
+    const int cands[] = {8, 16, 32, 64, 128, 256};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -446,7 +446,7 @@ int hdiv(int a, int b) { return (a + b - 1) / b; }
 // Batched z-chunk: the chunk of the sweeps at multigrid depth d of a batch,
 // timed on the batched sweep itself (every grid's tiles of that depth in one
 // launch: the per-grid choice above fills the GPU with one grid's blocks,
-// which a batch does not need) over the candidates 4..64, and remembered
+// which a batch does not need) over the candidates 8..256, and remembered
 // per depth and batch composition (an FNV-1a hash of the level shapes and
 // boundary conditions).  Sets the chunk of every level at that depth.
 int tune_batch_kz(lm_grid* const* grids, int count, std::vector<BLev>& hl, const std::vector<int>& lev0,
@@ -477,7 +477,7 @@ int tune_batch_kz(lm_grid* const* grids, int count, std::vector<BLev>& hl, const
         }
         if (!nlev) continue;
         char key[256];
-        snprintf(key, sizeof key, "%s|rbgs2d-batch|d%d|%016llx", gpu_name().c_str(), d, h);
+        snprintf(key, sizeof key, "%s|rbgs2d-batch-zrow|d%d|%016llx", gpu_name().c_str(), d, h);
         int best = -1;
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
@@ -491,8 +491,8 @@ int tune_batch_kz(lm_grid* const* grids, int count, std::vector<BLev>& hl, const
                 }
             }
             float best_ms = 1e30f;
-            for (int kz : {4, 8, 16, 32, 64}) {
-                if (kz > maxnz && kz != 4) continue;
+            for (int kz : {8, 16, 32, 64, 128, 256}) {
+                if (kz > maxnz && kz != 8) continue;
                 std::vector<BTask> tasks;
                 for (int i = 0; i < count; ++i) {
                     if (d >= lstop[i]) continue;

@@ -1157,10 +1157,10 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
 }
 
 template <int FIRST, bool ZERO, bool PROLONG>
-__global__ void __launch_bounds__(128) k_rbgs_zm2d(Lev32 L, const float* __restrict__ xin,
+__global__ void __launch_bounds__(128, 8) k_rbgs_zm2d(Lev32 L, const float* __restrict__ xin,
                                                   const float* __restrict__ ec, Geo C, int hx, int hz,
                                                   const float* __restrict__ f, float* __restrict__ xout, int KZ) {
-    zm2d_tile<FIRST, ZERO, PROLONG>(L, xin, ec, C, hx, hz, f, xout, KZ, blockIdx.x, blockIdx.y);
+    zrow2d_tile<FIRST, ZERO, PROLONG>(L, xin, ec, C, hx, hz, f, xout, KZ, blockIdx.x, blockIdx.y);
 }
 
 template <int BX, int TY, bool HAS_Y, int FIRST, bool ZERO, bool PROLONG>
@@ -1819,11 +1819,17 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
         else { if (first) LM_RB(1, false, false); else LM_RB(0, false, false); }
 #undef LM_RB
     } else if (g.ny == 1 && g.nx % 256 == 0 && g.nz >= 2) {
-        // 2D whole 256-cell rows: the in-place z-march; KZ rows per block
+        // 2D rows of 256-cell tiles: a warp per 128-cell segment and half
+        // chunk; KZ rows per block, about eight blocks (32 warps) per SM in
+        // all -- four blocks per SM left the loads too few to cover the HBM
+        // latency (0.43 against 0.58 of the copy bandwidth at 4096^2) --
+        // but at least 8 rows a warp
         const int tiles = g.nx / 256;
-        int KZ = kz > 0 ? kz : 32;
-        if (kz <= 0)
-            while (KZ > 2 && (long long)tiles * hdiv(g.nz, KZ) < 1216) KZ /= 2;
+        int KZ = kz;
+        if (kz <= 0) {
+            const int chunks = std::max(1, std::min(hdiv(1216, tiles), g.nz / 16));
+            KZ = hdiv(g.nz, chunks);
+        }
         const dim3 grd(tiles, hdiv(g.nz, KZ));
 #define LM_RB2(F, Z, P) k_rbgs_zm2d<F, Z, P><<<grd, 128, 0, s>>>(L, xin, ec, Cg, hx, hz, f, xout, KZ)
         if (zero) { if (first) LM_RB2(1, true, false); else LM_RB2(0, true, false); }

@@ -601,222 +601,243 @@ __device__ __forceinline__ void coarse_solve_block(int n, const float* __restric
     x[i] = s;
 }
 
-// ---- 2D red-black sweep on whole 256-cell rows: in-place z-march -----------
-//
-// The 2D counterpart of the 3D z-march sweep, for levels (ny = 1) whose nx is
-// a multiple of 256, on blocks of 128 threads: the block owns 256 columns
-// over a chunk of KZ rows and marches up z with a five-row ring of (x, rho)
-// staged on the row plus two cells (periodic x wrapped; past a wall x = 0
-// and rho = +inf, so that face's weight is 0).  At step p it stores row
-// p + 1 and issues the loads of row p + 2, updates the FIRST colour of row p
-// on the tile plus one cell each side in place (a first-colour update reads
-// only second-colour neighbours), the second colour of row p - 1, and
-// writes row p - 2.  Used by the single-grid sweep and the batched solver
-// (the same 256-wide tiles and row chunks as rbgs_tile).
+// float32 reciprocal by the hardware approximation (flushes denormals)
 __device__ __forceinline__ float rcp_hw(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 
+// ---- 2D red-black sweep: a warp per row segment and z-chunk ------------------
+//
+// For 2D levels whose nx is a multiple of 256.  The four warps of a 128-thread
+// block take a 256-column task (tile bx, chunk of KZ rows bz) as two 128-cell
+// segments times two halves of the chunk, and each warp marches up its rows
+// on its own: no block barrier, only warp synchronisation.  A warp keeps a
+// five-row ring of (x, rho) in shared memory, each staged row an even-cell
+// run and an odd-cell run (conflict-free accesses) between run-end slots that
+// hold the neighbouring cells outside the segment (two each side; wrapped on
+// a periodic x axis, x = 0 and rho = Z2_WALL past a wall).  At step p the warp
+// updates the first colour of row p -- and, in lane 0, the segment's
+// first-colour neighbour outside it, the value the neighbouring segment
+// computes for its own cell -- and the second colour of row p - 2, whose
+// first-colour neighbours (rows p - 3 .. p - 1) are final; neither update
+// reads a cell the other writes.  Row p - 3 is then final and written, and
+// row p + 2, loaded at the start of the step, is staged into its slot.  The
+// two faces of an axis share one reciprocal.  f and c~ are loaded a step
+// ahead, and x, rho, f, c~ of later rows are prefetched into L2.
+constexpr float Z2_WALL = 1e30f;                    // rho past a wall: face weight negligible, products finite
+__device__ __forceinline__ int z2_e(int m) { return 1 + m; }             // even cell 2m of the segment
+__device__ __forceinline__ int z2_o(int m) { return 3 + 64 + m; }        // odd cell 2m + 1 (64 pairs)
+
+// Gauss-Seidel value of cell 2m + A of the staged row at b (dzm, dzp: ring
+// offsets of the rows below and above)
+template <int A>
+__device__ __forceinline__ float z2_gs(const float2* __restrict__ XR, int b, int m, int dzm, int dzp, float fv,
+                                       float cv, float c2x, float c2z) {
+    const int cc = b + (A ? z2_o(m) : z2_e(m));
+    const int im = b + (A ? z2_e(m) : z2_o(m - 1));
+    const int ip = b + (A ? z2_e(m + 1) : z2_o(m));
+    const float2 me = XR[cc], xm = XR[im], xp = XR[ip], zm = XR[cc + dzm], zp = XR[cc + dzp];
+    const float axm = me.y + xm.y, axp = me.y + xp.y, tx = rcp_hw(axm * axp);
+    const float azm = me.y + zm.y, azp = me.y + zp.y, tz = rcp_hw(azm * azp);
+    const float rxm = axp * tx, rxp = axm * tx, rzm = azp * tz, rzp = azm * tz;
+    const float sx = fmaf(rxp, xp.x, rxm * xm.x);
+    const float sz = fmaf(rzp, zp.x, rzm * zm.x);
+    const float num = fmaf(c2z, sz, fmaf(c2x, sx, fv));
+    const float d = fmaf(c2z, rzm + rzp, fmaf(c2x, rxm + rxp, cv));
+    return num * rcp_hw(d);
+}
+
 template <int FIRST, bool ZERO, bool PROLONG>
-__device__ __forceinline__ void zm2d_tile(const Lev32& L, const float* __restrict__ xin,
-                                          const float* __restrict__ ec, const Geo& C, int hx, int hz,
-                                          const float* __restrict__ f, float* __restrict__ xout, int KZ, int bx,
-                                          int bz) {
-    constexpr int NT2 = 128, TX = 256, SX = TX + 4, NR = 5;
-    constexpr int NA = (TX + 2) / 2, NB = TX / 2;
-    constexpr int QS = (SX + NT2 - 1) / NT2, QA = (NA + NT2 - 1) / NT2, QW = TX / NT2;
-    __shared__ float2 XR[NR * SX];
-    __shared__ int ox[SX], px[SX];
-    __syncthreads();                                     // shared tiles may be reused by the next task
+__device__ __forceinline__ void zrow2d_tile(const Lev32& L, const float* __restrict__ xin,
+                                            const float* __restrict__ ec, const Geo& C, int hx, int hz,
+                                            const float* __restrict__ f, float* __restrict__ xout, int KZ, int bx,
+                                            int bz) {
+    constexpr int NX = 128, M = 64, RS = NX + 4, NR = 5, H = 2;
+    __shared__ float2 z2_ring[4][NR * RS];
     const Geo& g = L.g;
-    const int tid = threadIdx.x;
-    const int i0 = bx * TX;
-    const int k0 = bz * KZ, k1 = min(k0 + KZ, g.nz);
-    for (int t = tid; t < SX; t += NT2) {
-        int c = i0 - 2 + t;
-        if (c < 0) c = g.bcx == LM_BC_PERIODIC ? c + g.nx : -1;
-        else if (c >= g.nx) c = g.bcx == LM_BC_PERIODIC ? c - g.nx : -1;
-        ox[t] = c;
-        px[t] = c >> hx;
-    }
-    __syncthreads();
-    auto zwrap = [&](int p) -> int { return ((p % g.nz) + g.nz) % g.nz; };
-    auto zoff = [&](int p) -> int {
-        if (p >= 0 && p < g.nz) return g.nx * p;
-        return g.bcz == LM_BC_PERIODIC ? g.nx * zwrap(p) : -1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float2* XR = z2_ring[w];
+    const int c0 = bx * 256 + (w & 1) * NX;
+    const int t0 = bz * KZ, t1 = min(t0 + KZ, g.nz), tm = t0 + (t1 - t0 + 1) / 2;
+    const int k0 = (w >> 1) ? tm : t0, k1 = (w >> 1) ? t1 : tm;
+    if (k0 >= k1) return;                                // warp-uniform: no block barrier follows
+    const int W = g.nx, i2 = 2 * lane;
+    auto plane = [&](int p, int& pw) -> bool {           // row p wrapped; false past a wall
+        if (p < 0 || p >= g.nz) {
+            if (g.bcz != LM_BC_PERIODIC) return false;
+            p = p < 0 ? p + g.nz : p - g.nz;
+        }
+        pw = p;
+        return true;
     };
-    auto zpar = [&](int p) -> int { return C.nx * (zwrap(p) >> hz); };
-    int spos[QS], sbase[QS], spar[QS];
-    bool sok[QS];
-#pragma unroll
-    for (int q = 0; q < QS; ++q) {
-        spos[q] = tid + q * NT2;
-        const bool use = spos[q] < SX;
-        sok[q] = use && ox[use ? spos[q] : 0] >= 0;
-        sbase[q] = use ? ox[spos[q]] : 0;
-        spar[q] = use ? px[spos[q]] : 0;
-        if (!use) spos[q] = -1;
+    // lanes 0..3 stage the outside cells: columns c0 - 2, c0 - 1, c0 + NX, c0 + NX + 1
+    int gCol = c0 + (lane == 0 ? -2 : lane == 1 ? -1 : lane == 2 ? NX : NX + 1);
+    bool gOK = lane < 4;
+    if (gCol < 0 || gCol >= W) {
+        if (g.bcx == LM_BC_PERIODIC) gCol = gCol < 0 ? gCol + W : gCol - W;
+        else gOK = false;
     }
-    float vx[QS], vr[QS], ve[QS];
-    auto fetch = [&](int zo, int zp) {
+    const int gSlot = lane == 0 ? z2_e(-1) : lane == 1 ? z2_o(-1) : lane == 2 ? z2_e(M) : z2_o(M);
+    float vx[2 * H], vr[2 * H], ve[2 * H], gx = 0.f, gr = Z2_WALL, ge = 0.f;
+    auto fetch = [&](int p) {
+        int pw = 0;
+        const bool okp = plane(p, pw);
 #pragma unroll
-        for (int q = 0; q < QS; ++q) {
-            vx[q] = 0.f;
-            ve[q] = 0.f;
-            vr[q] = __int_as_float(0x7f800000);          // +inf
-            if (sok[q] && zo >= 0) {
-                const int idx = sbase[q] + zo;
-                vr[q] = L.rho[idx];
+        for (int u = 0; u < H; ++u) {
+            if (okp) {
+                const int o = W * pw + c0 + 64 * u + i2;
+                const float2 r2 = *reinterpret_cast<const float2*>(L.rho + o);
+                vr[2 * u] = r2.x;
+                vr[2 * u + 1] = r2.y;
                 if (!ZERO) {
-                    vx[q] = xin[idx];
-                    if (PROLONG) ve[q] = ec[spar[q] + zp];
+                    const float2 x2 = *reinterpret_cast<const float2*>(xin + o);
+                    vx[2 * u] = x2.x;
+                    vx[2 * u + 1] = x2.y;
+                } else {
+                    vx[2 * u] = vx[2 * u + 1] = 0.f;
                 }
+                if (PROLONG) {
+                    const int po = C.nx * (pw >> hz);
+                    ve[2 * u] = ec[po + ((c0 + 64 * u + i2) >> hx)];
+                    ve[2 * u + 1] = ec[po + ((c0 + 64 * u + i2 + 1) >> hx)];
+                }
+            } else {
+                vx[2 * u] = vx[2 * u + 1] = 0.f;
+                vr[2 * u] = vr[2 * u + 1] = Z2_WALL;
+                ve[2 * u] = ve[2 * u + 1] = 0.f;
+            }
+        }
+        if (lane < 4) {
+            if (okp && gOK) {
+                const int o = W * pw + gCol;
+                gx = ZERO ? 0.f : xin[o];
+                gr = L.rho[o];
+                ge = PROLONG ? ec[C.nx * (pw >> hz) + (gCol >> hx)] : 0.f;
+            } else {
+                gx = 0.f;
+                gr = Z2_WALL;
+                ge = 0.f;
             }
         }
     };
-    auto store = [&](int o) {
+    auto store = [&](int s) {
+        float2* R = XR + s * RS;
 #pragma unroll
-        for (int q = 0; q < QS; ++q)
-            if (spos[q] >= 0) XR[o + spos[q]] = make_float2(PROLONG ? vx[q] + ve[q] : vx[q], vr[q]);
+        for (int u = 0; u < H; ++u) {
+            const int m = lane + 32 * u;
+            R[z2_e(m)] = make_float2(PROLONG ? vx[2 * u] + ve[2 * u] : vx[2 * u], vr[2 * u]);
+            R[z2_o(m)] = make_float2(PROLONG ? vx[2 * u + 1] + ve[2 * u + 1] : vx[2 * u + 1], vr[2 * u + 1]);
+        }
+        if (lane < 4) R[gSlot] = make_float2(PROLONG ? gx + ge : gx, gr);
     };
-    auto gs = [&](int e, int sm, int s0, int sp, float fv, float cv) -> float {
-        const int c = s0 + e;
-        const float rc = XR[c].y;
-        const float2 nxm = XR[c - 1], nxp = XR[c + 1], nzm = XR[sm + e], nzp = XR[sp + e];
-        const float wxm = L.c2x * rcp_hw(rc + nxm.y);
-        const float wxp = L.c2x * rcp_hw(rc + nxp.y);
-        const float wzm = L.c2z * rcp_hw(rc + nzm.y);
-        const float wzp = L.c2z * rcp_hw(rc + nzp.y);
-        const float d = cv + (wxm + wxp) + (wzm + wzp);
-        float num = fv;
-        num = fmaf(wxm, nxm.x, num);
-        num = fmaf(wxp, nxp.x, num);
-        num = fmaf(wzm, nzm.x, num);
-        num = fmaf(wzp, nzp.x, num);
-        return num * rcp_hw(d);
-    };
-    // first-colour tasks: pair am of the halo row (x positions 2am and 2am + 1
-    // of the staged row shifted by one); second-colour task: pair bm of the tile
-    bool hasA[QA];
-    int aeE[QA], aoE[QA], aoO[QA];
+    // f and c~ of the updated cell of each of the lane's pairs in row p (a: 0 even, 1 odd)
+    auto load_fc = [&](int p, bool ok, int a, float* F, float* Cv) {
+        int pw = 0;
+        if (ok && plane(p, pw)) {
+            const int o = W * pw + c0 + i2 + a;
 #pragma unroll
-    for (int u = 0; u < QA; ++u) {
-        const int am = tid + u * NT2;
-        hasA[u] = am < NA;
-        aeE[u] = 2 * (hasA[u] ? am : 0) + 1;
-        aoE[u] = ox[aeE[u]];
-        aoO[u] = ox[aeE[u] + 1];
+            for (int u = 0; u < H; ++u) {
+                F[u] = f[o + 64 * u];
+                Cv[u] = L.ct[o + 64 * u];
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                F[u] = 0.f;
+                Cv[u] = 1.f;
+            }
+        }
+    };
+    auto par = [&](int p, int col) -> int { return (col + p) & 1; };   // updated cell of each pair
+    // the first-colour outside cell of row p (lane 0): column c0 - 1 when the
+    // row's first colour is odd, c0 + NX when even; its f and c~ a step ahead
+    float fX = 0.f, cX = 1.f;
+    bool xOK = false;
+    auto load_fcx = [&](int p) {
+        if (lane != 0) return;
+        int pw = 0;
+        xOK = false;
+        if (p > k1 || !plane(p, pw)) return;
+        int col = par(p, FIRST) ? c0 - 1 : c0 + NX;
+        if (col < 0 || col >= W) {
+            if (g.bcx != LM_BC_PERIODIC) return;
+            col = col < 0 ? col + W : col - W;
+        }
+        xOK = true;
+        fX = f[W * pw + col];
+        cX = L.ct[W * pw + col];
+    };
+    auto prefetch = [&](int P) {                          // lane a < 4: x, rho, f, c~ of row P
+        int pw = 0;
+        if (lane >= 4 || P > (lane < 2 ? k1 + 1 : k1) || (ZERO && lane == 0) || !plane(P, pw)) return;
+        const float* base = lane == 0 ? xin : lane == 1 ? L.rho : lane == 2 ? f : L.ct;
+        prefetch_l2(base + W * pw + c0, NX * sizeof(float));
+    };
+    auto run_row = [&](int a, int b, int dzm, int dzp, const float* F, const float* Cv) {
+        float nv[H];
+#pragma unroll
+        for (int u = 0; u < H; ++u)
+            nv[u] = a ? z2_gs<1>(XR, b, lane + 32 * u, dzm, dzp, F[u], Cv[u], L.c2x, L.c2z)
+                      : z2_gs<0>(XR, b, lane + 32 * u, dzm, dzp, F[u], Cv[u], L.c2x, L.c2z);
+#pragma unroll
+        for (int u = 0; u < H; ++u) XR[b + (a ? z2_o(lane + 32 * u) : z2_e(lane + 32 * u))].x = nv[u];
+    };
+    for (int d = 1; d <= PF_PLANES; ++d) prefetch((lane < 2 ? k0 : k0 - 1) + d);
+    // prologue: rows k0 - 2 .. k0 staged; f, c~ of the first step's cells
+    for (int q = 0; q < 3; ++q) {
+        fetch(k0 - 2 + q);
+        store(q);
     }
-    const int apar = (FIRST + i0) & 1;
-    const int bpar = (1 - FIRST + i0) & 1;
-    const int beE = 2 * tid + 2;
-    const int bidxE = i0 + 2 * tid;
-    int wpos[QW], wbase[QW];
+    int s_m3 = 3, s_m2 = 4, s_m1 = 0, s_0 = 1, s_p1 = 2;    // slots of rows p - 3 .. p + 1 at p = k0 - 1
+    float fT[H], cT[H], fS[H], cS[H];
+    load_fc(k0 - 1, true, par(k0 - 1, FIRST), fT, cT);
 #pragma unroll
-    for (int v = 0; v < QW; ++v) {
-        wpos[v] = tid + v * NT2 + 2;
-        wbase[v] = i0 + tid + v * NT2;
+    for (int u = 0; u < H; ++u) {
+        fS[u] = 0.f;
+        cS[u] = 1.f;
     }
-    int om2 = 0 * SX, om1 = 1 * SX, o0 = 2 * SX, op1 = 3 * SX, op2 = 4 * SX;
-    int z0 = zoff(k0 - 1), z1 = zoff(k0), z2 = zoff(k0 + 1);
-    int zp2 = PROLONG ? zpar(k0 + 1) : 0;
-    fetch(zoff(k0 - 2), PROLONG ? zpar(k0 - 2) : 0);
-    store(om1);
-    fetch(z0, PROLONG ? zpar(k0 - 1) : 0);
-    store(o0);
-    fetch(z1, PROLONG ? zpar(k0) : 0);
-    float fa[QA], ca[QA];
-    bool okA[QA];
-    int eA[QA];
-    auto load_a = [&](int p, int zo, bool in_chunk) {
-#pragma unroll
-        for (int u = 0; u < QA; ++u) {
-            // staged position aeE + odd is global x = i0 - 1 + 2 am + odd, of
-            // colour (x + p) & 1 = FIRST when odd = (FIRST + i0 + p + 1) & 1
-            const int odd = (apar + p + 1) & 1;
-            const int a = odd ? aoO[u] : aoE[u];
-            okA[u] = hasA[u] && in_chunk && (a | zo) >= 0;
-            eA[u] = aeE[u] + odd;
-            fa[u] = 0.f;
-            ca[u] = 1.f;
-            if (okA[u]) {
-                fa[u] = f[a + zo];
-                ca[u] = L.ct[a + zo];
+    load_fcx(k0 - 1);
+    __syncwarp();
+    for (int p = k0 - 1; p <= k1 + 2; ++p) {
+        const bool stage = p + 2 <= k1 + 1;
+        prefetch((lane < 2 ? p + 2 : p + 1) + PF_PLANES);
+        if (stage) fetch(p + 2);
+        int pw = 0;
+        if (p <= k1 && plane(p, pw)) {                    // first colour on row p
+            const int dzm = (s_m1 - s_0) * RS, dzp = (s_p1 - s_0) * RS, b = s_0 * RS;
+            run_row(par(p, FIRST), b, dzm, dzp, fT, cT);
+            if (lane == 0 && xOK) {
+                if (par(p, FIRST)) XR[b + z2_o(-1)].x = z2_gs<1>(XR, b, -1, dzm, dzp, fX, cX, L.c2x, L.c2z);
+                else XR[b + z2_e(M)].x = z2_gs<0>(XR, b, M, dzm, dzp, fX, cX, L.c2x, L.c2z);
             }
         }
-    };
-    // L2 prefetch of the tile's row segments (256 cells, contiguous) PF_PLANES
-    // steps ahead: x and rho of row P are fetched at step P - 2, f and c~ of
-    // row P first read at step P - 1; array a = 0..3 by thread a
-    auto prefetch = [&](int a, int P) {
-        if (P > (a < 2 ? k1 + 1 : k1) || (ZERO && a == 0)) return;
-        const int zo = zoff(P);
-        if (zo < 0) return;
-        const float* base = a == 0 ? xin : a == 1 ? L.rho : a == 2 ? f : L.ct;
-        prefetch_l2(base + zo + i0, TX * sizeof(float));
-    };
-    if (tid < 4)
-        for (int d = 1; d <= PF_PLANES; ++d) prefetch(tid, (tid < 2 ? k0 : k0 - 1) + d);
-    load_a(k0 - 1, z0, true);
-    float fb = 0.f, cb = 1.f;
-    bool okB = false;
-    int eB = 0;
-    for (int p = k0 - 1; p <= k1 + 1; ++p) {
-        if (tid < 4) prefetch(tid, (tid < 2 ? p + 2 : p + 1) + PF_PLANES);
-        if (p <= k1) store(op1);
-        if (p + 1 <= k1) fetch(z2, zp2);
-        float fA[QA], cA[QA];
-        bool doA[QA];
-        int eAc[QA];
+        load_fc(p + 1, p + 1 <= k1, par(p + 1, FIRST), fT, cT);
+        load_fcx(p + 1);
+        const int q = p - 2;
+        if (q >= k0 && q < k1)                           // second colour on row p - 2
+            run_row(par(q, 1 - FIRST), s_m2 * RS, (s_m3 - s_m2) * RS, (s_m1 - s_m2) * RS, fS, cS);
+        load_fc(q + 1, q + 1 >= k0 && q + 1 < k1, par(q + 1, 1 - FIRST), fS, cS);
+        __syncwarp();
+        if (p - 3 >= k0 && p - 3 < k1) {                 // row p - 3 is final
+            const float2* R = XR + s_m3 * RS;
+            float* dst = xout + W * (p - 3) + c0 + i2;
 #pragma unroll
-        for (int u = 0; u < QA; ++u) {
-            fA[u] = fa[u];
-            cA[u] = ca[u];
-            doA[u] = okA[u] && p <= k1;
-            eAc[u] = eA[u];
-        }
-        const float fB = fb, cB = cb;
-        const bool doB = okB;
-        const int eBc = eB;
-        {
-            const int odd = (bpar + p) & 1;
-            okB = p >= k0 && p < k1;
-            eB = beE + odd;
-            if (okB) {
-                const int idx = bidxE + odd + g.nx * p;
-                fb = f[idx];
-                cb = L.ct[idx];
+            for (int u = 0; u < H; ++u) {
+                const int m = lane + 32 * u;
+                *reinterpret_cast<float2*>(dst + 64 * u) = make_float2(R[z2_e(m)].x, R[z2_o(m)].x);
             }
         }
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < QA; ++u)
-            if (doA[u]) XR[o0 + eAc[u]].x = gs(eAc[u], om1, o0, op1, fA[u], cA[u]);
-        load_a(p + 1, z1, p + 1 <= k1);
-        __syncthreads();
-        if (doB) XR[om1 + eBc].x = gs(eBc, om2, om1, o0, fB, cB);
-        if (p - 2 >= k0) {
-#pragma unroll
-            for (int v = 0; v < QW; ++v) xout[wbase[v] + g.nx * (p - 2)] = XR[om2 + wpos[v]].x;
-        }
-        const int t = om2;
-        om2 = om1;
-        om1 = o0;
-        o0 = op1;
-        op1 = op2;
-        op2 = t;
-        z0 = z1;
-        z1 = z2;
-        {
-            int c = p + 3;
-            if (c >= g.nz) c -= g.nz;
-            if (c >= g.nz) c -= g.nz;
-            const bool ok = (p + 3 < g.nz || g.bcz == LM_BC_PERIODIC) && c >= 0 && c < g.nz;
-            z2 = ok ? g.nx * c : -1;
-            if (PROLONG) zp2 = C.nx * ((ok ? c : 0) >> hz);
-        }
+        __syncwarp();
+        if (stage) store(s_m3);                           // row p + 2 takes row p - 3's slot
+        __syncwarp();
+        const int t = s_m3;
+        s_m3 = s_m2;
+        s_m2 = s_m1;
+        s_m1 = s_0;
+        s_0 = s_p1;
+        s_p1 = t;
     }
 }
 

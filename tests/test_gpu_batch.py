@@ -64,7 +64,8 @@ def test_batch_matches_oracle_and_single_path(lm, tmp_path):
         for g in grids:
             g.close()
     tuned = json.loads(cache.read_text())
-    assert any("|rbgs2d-zm|" in k for k in tuned) and all(v in (4, 8, 16, 32, 64) for v in tuned.values())
+    assert any("|rbgs2d-zrow|" in k for k in tuned) and any("|rbgs2d-batch-zrow|" in k for k in tuned)
+    assert all(v in (8, 16, 32, 64, 128, 256) for v in tuned.values())
 
 
 def test_batch_whole_row_grids_match_oracle(lm, tmp_path):
