@@ -46,6 +46,7 @@ struct BLev {
     Geo C;              // the next (coarser) level
     int hx, hy, hz;     // halving to the next level
     int kz;             // sweep z-chunk (autotuned)
+    int kr;             // coarse rows per warp of the 2D residual-restriction (0: the generic tile)
     float* xa;          // pre-smoothed iterate
     float* xb;          // sweep scratch (sweeps beyond the first of a pre- or post-smoothing chain)
     float* xo;          // V-cycle output (level 0: the grid's z)
@@ -65,7 +66,8 @@ struct BGrid {
     SolveState* st_in;  // inner state: done = inner tolerance met
     Red red;
     int N;
-    int kz_apply;
+    int kz_apply;       // rows per thread of the apply (seg_apply: rows per warp)
+    int seg_apply;      // 1: the level-0 apply runs as apply2d_rows (seg2d_ok)
 };
 
 // scal slots per grid: 0 p.q, 1 r.r, 2 p.r, 3 z.q_old, 4 r0.r0, 5 float64 r.r, 6 f.f
@@ -163,9 +165,9 @@ __global__ void __launch_bounds__(128, 8) kb_rbgs(const BTask* __restrict__ T, c
     const BLev& V = Ls[t.l];
     const float* xin = ZERO ? nullptr : lev_buf(V, src);
     float* xout = lev_buf(V, dst);
-    if (V.L.g.nx % 256 == 0 && V.L.g.nz >= 2)        // whole 256-cell rows: the z-march (same tiles)
+    if (V.L.g.nx % 128 == 0 && V.L.g.nz >= 2)        // rows of 128-cell segments: the warp z-march
         zrow2d_tile<FIRST, ZERO, PROLONG>(V.L, xin, PROLONG ? V.ec : nullptr, V.C, PROLONG ? V.hx : 0,
-                                        PROLONG ? V.hz : 0, V.f, xout, V.kz, t.bx, t.by);
+                                        PROLONG ? V.hz : 0, V.f, xout, V.kz, t.bx, t.by, zrow2d_width(V.L.g.nx));
     else
         rbgs_tile<128, 1, false, FIRST, ZERO, PROLONG>(V.L, xin, PROLONG ? V.ec : nullptr, V.C, PROLONG ? V.hx : 0,
                                                         PROLONG ? V.hy : 0, PROLONG ? V.hz : 0, V.f, xout, V.kz,
@@ -177,6 +179,11 @@ __global__ void __launch_bounds__(256) kb_resid_restrict(const BTask* __restrict
     const BTask t = T[blockIdx.x];
     if (inner_off(Gs[t.g])) return;
     const BLev& V = Ls[t.l];
+    if (V.kr) {                                    // rr2d_ok levels: a warp per segment and V.kr coarse rows
+        const int K0 = (t.by * 8 + threadIdx.y) * V.kr;
+        if (K0 < V.C.nz) rr2d_rows(V.L, V.C, V.xa, V.f, V.fc, t.bx * 128, K0, min(K0 + V.kr, V.C.nz));
+        return;
+    }
     resid_restrict_tile(V.L, V.C, V.hx, V.hy, V.hz, V.xa, V.f, V.fc, t.bx, t.by, t.bz);
 }
 
@@ -242,7 +249,14 @@ __global__ void __launch_bounds__(256) kb_apply(const BTask* __restrict__ T, con
     if (inner_off(G)) return;
     __shared__ double sm[64];
     FF axy{0.f, 0.f}, axr{0.f, 0.f};
-    apply32z_tile<false, true, true>(Ls[lev0[t.g]].L, G.p32, G.q32, G.r32, G.kz_apply, t.bx, t.by, 0, axy, axr);
+    const Lev32& L = Ls[lev0[t.g]].L;
+    if (G.seg_apply) {
+        const int k0 = (t.by * 8 + threadIdx.y) * G.kz_apply;
+        if (k0 < L.g.nz)
+            apply2d_rows<true, true>(L, G.p32, G.q32, G.r32, t.bx * 128, k0, min(k0 + G.kz_apply, L.g.nz), axy, axr);
+    } else {
+        apply32z_tile<false, true, true>(L, G.p32, G.q32, G.r32, G.kz_apply, t.bx, t.by, 0, axy, axr);
+    }
     double v[2] = {ff_value(axy), ff_value(axr)};
     const int sl[2] = {0, 2};
     grid_reduce_n<2>(v, G.red, sl, sm, t.lblk, t.nblk);
@@ -443,6 +457,10 @@ int tune_sweep_kz(const MgLevel& M, const float* fin, float* scratch, cudaStream
 
 int hdiv(int a, int b) { return (a + b - 1) / b; }
 
+// columns of a task of the batched sweep: zrow2d_tile's width on levels of
+// 128-cell segments, rbgs_tile's 256 on the others
+int sweep_tile_width(const Geo& g) { return g.nx % 128 == 0 && g.nz >= 2 ? zrow2d_width(g.nx) : 256; }
+
 // Batched z-chunk: the chunk of the sweeps at multigrid depth d of a batch,
 // timed on the batched sweep itself (every grid's tiles of that depth in one
 // launch: the per-grid choice above fills the GPU with one grid's blocks,
@@ -498,7 +516,7 @@ int tune_batch_kz(lm_grid* const* grids, int count, std::vector<BLev>& hl, const
                     if (d >= lstop[i]) continue;
                     BLev& V = hl[lev0[i] + d];
                     V.kz = kz;
-                    const int gx = hdiv(V.L.g.nx, 256), gy = hdiv(V.L.g.nz, kz);
+                    const int gx = hdiv(V.L.g.nx, sweep_tile_width(V.L.g)), gy = hdiv(V.L.g.nz, kz);
                     for (int by = 0; by < gy; ++by)
                         for (int bx = 0; bx < gx; ++bx) tasks.push_back(BTask{i, lev0[i] + d, bx, by, 0, 0, 0});
                 }
@@ -660,6 +678,9 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
         int kz = 8;
         while ((long long)hdiv(g->n[0], 32) * hdiv(hdiv(g->n[2], kz), 8) > 4096) kz *= 2;
         G.kz_apply = kz;
+        // 2D grids of 128-column segments: a warp per segment and 8 rows
+        G.seg_apply = seg2d_ok(g->mg[0].L.g, g->p32, g->q32, g->r32, g->mg[0].L.rho, g->mg[0].L.ct) ? 1 : 0;
+        if (G.seg_apply) G.kz_apply = 8;
         lev0[i] = (int)hl.size();
         nlev[i] = (int)g->mg.size();
         P->max_depth = std::max(P->max_depth, nlev[i]);
@@ -687,6 +708,8 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
             V.xo = l == 0 ? g->z32 : M.xo;
             V.f = l == 0 ? g->r32 : M.f;
             V.ainv = M.ainv;
+            V.kr = !last && rr2d_ok(V.L, V.hx, V.hy, V.hz, V.xa, V.f, V.fc) ? std::max(1, std::min(8, V.C.nz / 16))
+                                                                             : 0;
             hl.push_back(V);
         }
     }
@@ -706,7 +729,8 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
     TaskList tap{(int)tasks.size(), 0};
     for (int i = 0; i < count; ++i) {
         const Geo& g = hg[i].geo;
-        const int gx = hdiv(g.nx, 32), gy = hdiv(hdiv(g.nz, hg[i].kz_apply), 8);
+        const int gx = hg[i].seg_apply ? g.nx / 128 : hdiv(g.nx, 32);
+        const int gy = hg[i].seg_apply ? hdiv(g.nz, 8 * hg[i].kz_apply) : hdiv(hdiv(g.nz, hg[i].kz_apply), 8);
         for (int by = 0; by < gy; ++by)
             for (int bx = 0; bx < gx; ++bx) tasks.push_back(BTask{i, lev0[i], bx, by, 0, bx + gx * by, gx * gy});
     }
@@ -753,7 +777,7 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
         for (int i = 0; i < count; ++i) {
             if (d >= lstop[i]) continue;
             const BLev& V = hl[lev0[i] + d];
-            const int gx = hdiv(V.L.g.nx, 256), gy = hdiv(V.L.g.nz, V.kz);
+            const int gx = hdiv(V.L.g.nx, sweep_tile_width(V.L.g)), gy = hdiv(V.L.g.nz, V.kz);
             for (int by = 0; by < gy; ++by)
                 for (int bx = 0; bx < gx; ++bx) tasks.push_back(BTask{i, lev0[i] + d, bx, by, 0, 0, 0});
         }
@@ -762,7 +786,7 @@ int build_plan(lm_grid* const* grids, int count, const lm_solve_opts* o, cudaStr
         for (int i = 0; i < count; ++i) {
             if (d >= lstop[i]) continue;
             const BLev& V = hl[lev0[i] + d];
-            const int gx = hdiv(V.C.nx, 32), gy = hdiv(V.C.nz, 8);
+            const int gx = V.kr ? V.L.g.nx / 128 : hdiv(V.C.nx, 32), gy = V.kr ? hdiv(V.C.nz, 8 * V.kr) : hdiv(V.C.nz, 8);
             for (int by = 0; by < gy; ++by)
                 for (int bx = 0; bx < gx; ++bx) tasks.push_back(BTask{i, lev0[i] + d, bx, by, 0, 0, 0});
         }

@@ -33,6 +33,27 @@ __global__ void __launch_bounds__(256) k_apply32z(Lev32 L, const float* __restri
     }
 }
 
+// 2D levels passing seg2d_ok: warp w of block (bx, by) takes columns
+// 128 bx .. 128 bx + 127 and rows (8 by + w) KR .. + KR - 1.
+template <bool DOT_XY, bool DOT_XR>
+__global__ void __launch_bounds__(256) k_apply32_2d(Lev32 L, const float* __restrict__ x, float* __restrict__ y,
+                                                    const float* __restrict__ r, Red red, int slot_xy, int slot_xr,
+                                                    int KR) {
+    __shared__ double sm[64];
+    FF axy{0.f, 0.f}, axr{0.f, 0.f};
+    const int k0 = (blockIdx.y * 8 + threadIdx.y) * KR;
+    if (k0 < L.g.nz) apply2d_rows<DOT_XY, DOT_XR>(L, x, y, r, blockIdx.x * 128, k0, min(k0 + KR, L.g.nz), axy, axr);
+    if (DOT_XY && DOT_XR) {
+        double v[2] = {ff_value(axy), ff_value(axr)};
+        const int sl[2] = {slot_xy, slot_xr};
+        grid_reduce<2>(v, red, sl, sm);
+    } else if (DOT_XY) {
+        double v[1] = {ff_value(axy)};
+        const int sl[1] = {slot_xy};
+        grid_reduce<1>(v, red, sl, sm);
+    }
+}
+
 // ---- 3D apply on whole tiles: a z-march over staged planes ----------------
 // y = A x with x.y and x.r accumulated to float64 accuracy, for 3D levels
 // whose nx, ny are multiples of the TX x 8 tile.  A block owns a tile's
@@ -538,6 +559,16 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Lev32 F, Geo C, int hx, 
                                                         const float* __restrict__ x, const float* __restrict__ f,
                                                         float* __restrict__ fc) {
     resid_restrict_tile(F, C, hx, hy, hz, x, f, fc, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// 2D levels passing rr2d_ok: warp w of block (bx, by) takes fine columns
+// 128 bx .. 128 bx + 127 and coarse rows (8 by + w) KR .. + KR - 1.
+__global__ void __launch_bounds__(256, 3) k_resid_restrict_2d(Lev32 F, Geo C, const float* __restrict__ x,
+                                                           const float* __restrict__ f, float* __restrict__ fc,
+                                                           int KR) {
+    const int K0 = (blockIdx.y * 8 + threadIdx.y) * KR;
+    if (K0 >= C.nz) return;
+    rr2d_rows(F, C, x, f, fc, blockIdx.x * 128, K0, min(K0 + KR, C.nz));
 }
 
 // ---- 3D red-black sweep on whole tiles: in-place z-march ------------------
@@ -1159,8 +1190,9 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
 template <int FIRST, bool ZERO, bool PROLONG>
 __global__ void __launch_bounds__(128, 8) k_rbgs_zm2d(Lev32 L, const float* __restrict__ xin,
                                                   const float* __restrict__ ec, Geo C, int hx, int hz,
-                                                  const float* __restrict__ f, float* __restrict__ xout, int KZ) {
-    zrow2d_tile<FIRST, ZERO, PROLONG>(L, xin, ec, C, hx, hz, f, xout, KZ, blockIdx.x, blockIdx.y);
+                                                  const float* __restrict__ f, float* __restrict__ xout, int KZ,
+                                                  int TW) {
+    zrow2d_tile<FIRST, ZERO, PROLONG>(L, xin, ec, C, hx, hz, f, xout, KZ, blockIdx.x, blockIdx.y, TW);
 }
 
 template <int BX, int TY, bool HAS_Y, int FIRST, bool ZERO, bool PROLONG>
@@ -1624,6 +1656,19 @@ void launch_apply32(const Lev32& L, cudaStream_t s, const float* x, float* y, co
 #undef LM_AZ
         return;
     }
+    if (seg2d_ok(g, x, y, L.rho, L.ct, slot_xr >= 0 ? r : nullptr)) {
+        // 2D rows of 128-column segments: a warp per segment and KR rows, KR
+        // as large as still gives about 32 warps per SM
+        const int segs = g.nx / 128;
+        int KR = 16;
+        while (KR > 1 && (long long)segs * hdiv(g.nz, KR) < 32 * 152) KR /= 2;
+        const dim3 grd(segs, hdiv(g.nz, 8 * KR)), blk(32, 8);
+        count_launches(1);
+        if (slot_xy >= 0 && slot_xr >= 0) k_apply32_2d<true, true><<<grd, blk, 0, s>>>(L, x, y, r, red, slot_xy, slot_xr, KR);
+        else if (slot_xy >= 0) k_apply32_2d<true, false><<<grd, blk, 0, s>>>(L, x, y, r, red, slot_xy, slot_xr, KR);
+        else k_apply32_2d<false, false><<<grd, blk, 0, s>>>(L, x, y, r, red, slot_xy, slot_xr, KR);
+        return;
+    }
     const dim3 blk(32, 8);
     const bool y3 = g.ny > 1;
     int kz = 1;
@@ -1693,6 +1738,15 @@ void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int h
         return;
     }
     count_launches(1);
+    if (rr2d_ok(F, hx, hy, hz, x, f, fc)) {
+        // 2D rows: a warp per 128-column segment and KR coarse rows, KR as
+        // large as still gives about 32 warps per SM
+        const int segs = g.nx / 128;
+        int KR = 8;
+        while (KR > 1 && (long long)segs * hdiv(C.g.nz, KR) < 32 * 152) KR /= 2;
+        k_resid_restrict_2d<<<dim3(segs, hdiv(C.g.nz, 8 * KR)), dim3(32, 8), 0, s>>>(F, C.g, x, f, fc, KR);
+        return;
+    }
     if (g.ny > 1 && g.nx % 32 == 0 && g.ny % 8 == 0 && g.nz >= 2 && (!hz || g.nz % 2 == 0)) {
         // whole TX x 8 tiles: the staged z-march; KZ (even) planes per block
         const int TXc = g.nx % 64 == 0 ? 64 : 32;
@@ -1739,7 +1793,6 @@ void rbgs_row_allow_smem() {
 }
 
 static bool aligned8(const void* p) { return ((uintptr_t)p & 7) == 0; }
-static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 template <int CPT, int SEG = 1>
 static void launch_rbgs_row(const Lev32& L, cudaStream_t s, const float* xin, const float* ec, const Geo& Cg,
@@ -1818,20 +1871,20 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
         else if (prolong) { if (first) LM_RB(1, false, true); else LM_RB(0, false, true); }
         else { if (first) LM_RB(1, false, false); else LM_RB(0, false, false); }
 #undef LM_RB
-    } else if (g.ny == 1 && g.nx % 256 == 0 && g.nz >= 2) {
-        // 2D rows of 256-cell tiles: a warp per 128-cell segment and half
-        // chunk; KZ rows per block, about eight blocks (32 warps) per SM in
-        // all -- four blocks per SM left the loads too few to cover the HBM
-        // latency (0.43 against 0.58 of the copy bandwidth at 4096^2) --
-        // but at least 8 rows a warp
-        const int tiles = g.nx / 256;
+    } else if (g.ny == 1 && g.nx % 128 == 0 && g.nz >= 2) {
+        // 2D rows of 256- (or 128-) cell tiles: a warp per 128-cell segment
+        // and half (quarter) chunk; KZ rows per block, about eight blocks (32
+        // warps) per SM in all -- four blocks per SM left the loads too few
+        // to cover the HBM latency (0.43 against 0.58 of the copy bandwidth
+        // at 4096^2) -- but at least 8 rows a warp
+        const int TW = zrow2d_width(g.nx), tiles = g.nx / TW, parts = 512 / TW;
         int KZ = kz;
         if (kz <= 0) {
-            const int chunks = std::max(1, std::min(hdiv(1216, tiles), g.nz / 16));
+            const int chunks = std::max(1, std::min(hdiv(1216, tiles), g.nz / (8 * parts)));
             KZ = hdiv(g.nz, chunks);
         }
         const dim3 grd(tiles, hdiv(g.nz, KZ));
-#define LM_RB2(F, Z, P) k_rbgs_zm2d<F, Z, P><<<grd, 128, 0, s>>>(L, xin, ec, Cg, hx, hz, f, xout, KZ)
+#define LM_RB2(F, Z, P) k_rbgs_zm2d<F, Z, P><<<grd, 128, 0, s>>>(L, xin, ec, Cg, hx, hz, f, xout, KZ, TW)
         if (zero) { if (first) LM_RB2(1, true, false); else LM_RB2(0, true, false); }
         else if (prolong) { if (first) LM_RB2(1, false, true); else LM_RB2(0, false, true); }
         else { if (first) LM_RB2(1, false, false); else LM_RB2(0, false, false); }

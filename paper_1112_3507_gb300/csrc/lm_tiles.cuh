@@ -280,6 +280,145 @@ __device__ __forceinline__ void resid_restrict_tile(const Lev32& F, const Geo& C
     fc[I + C.nx * (J + C.ny * K)] = s * (1.f / (float)((1 << hx) << hy << hz));
 }
 
+// ---- 2D operator on 128-column segments: residual-restriction and apply -----
+//
+// For 2D levels (ny = 1) whose nx is a multiple of 128.  A warp takes the 128
+// fine columns c0 .. c0 + 127 over a run of rows and walks up them: lane l
+// holds cells c0 + 4l .. c0 + 4l + 3 of a row (one float4 of each array), gets
+// its x-neighbours from the next lanes by shuffles (the two cells outside the
+// segment come from lanes 0 and 31), and keeps x and rho of the rows below and
+// above in registers, so every value is loaded once, plus two rows of x and
+// rho per warp.  The operator's arithmetic is that of apply32_at, term by
+// term.  seg2d_ok: the shape, and 16-byte aligned arrays (float4 accesses).
+__host__ __device__ inline bool seg2d_ok(const Geo& g, const void* a, const void* b, const void* c, const void* d,
+                                         const void* e) {
+    const uintptr_t u = (uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d | (uintptr_t)e;
+    return g.ny == 1 && g.nx % 128 == 0 && g.nz >= 2 && (u & 15) == 0;
+}
+// the residual-restriction's case: halved in x and z (fc is written as float2)
+__host__ __device__ inline bool rr2d_ok(const Lev32& F, int hx, int hy, int hz, const float* x, const float* f,
+                                        const float* fc) {
+    return hx == 1 && hy == 0 && hz == 1 && seg2d_ok(F.g, x, f, F.rho, F.ct, nullptr) && ((uintptr_t)fc & 7) == 0;
+}
+
+struct Row4 {
+    float4 x, rho;     // the lane's four cells
+    float gx, grho;    // lane 0: the cell left of the segment; lane 31: right
+};
+
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+struct Seg2D {
+    const Lev32& L;
+    int lane, cl, cg;  // cl: the lane's first column; cg: its outside cell (-1: a wall or none)
+    bool fl, fr;       // x faces at the lane's two ends
+    __device__ __forceinline__ Seg2D(const Lev32& L_, int c0) : L(L_) {
+        const Geo& g = L.g;
+        lane = threadIdx.x & 31;
+        cl = c0 + 4 * lane;
+        cg = -1;
+        if (lane == 0) cg = c0 > 0 ? c0 - 1 : (g.bcx == LM_BC_PERIODIC ? g.nx - 1 : -1);
+        if (lane == 31) cg = c0 + 128 < g.nx ? c0 + 128 : (g.bcx == LM_BC_PERIODIC ? 0 : -1);
+        fl = lane > 0 || cg >= 0;
+        fr = lane < 31 || cg >= 0;
+    }
+    // x and rho of row r (wrapped on a periodic z axis; zeros past a wall, where no face reads them)
+    __device__ __forceinline__ Row4 load(const float* __restrict__ x, int r) const {
+        const Geo& g = L.g;
+        Row4 v;
+        if (r < 0) r = g.bcz == LM_BC_PERIODIC ? r + g.nz : -1;
+        else if (r >= g.nz) r = g.bcz == LM_BC_PERIODIC ? r - g.nz : -1;
+        if (r < 0) {
+            v.x = v.rho = make_float4(0.f, 0.f, 0.f, 0.f);
+            v.gx = v.grho = 0.f;
+            return v;
+        }
+        const size_t o = (size_t)r * g.nx;
+        v.x = ld4(x + o + cl);
+        v.rho = ld4(L.rho + o + cl);
+        v.gx = cg >= 0 ? __ldg(x + o + cg) : 0.f;
+        v.grho = cg >= 0 ? __ldg(L.rho + o + cg) : 0.f;
+        return v;
+    }
+    // (A x) on the lane's four cells of row r (B, M, A: rows r - 1, r, r + 1; every lane calls it)
+    __device__ __forceinline__ void apply(int r, const Row4& B, const Row4& M, const Row4& A, float y[4]) const {
+        const Geo& g = L.g;
+        const unsigned FULL = 0xffffffffu;
+        float xl = __shfl_up_sync(FULL, M.x.w, 1), rl = __shfl_up_sync(FULL, M.rho.w, 1);
+        float xr = __shfl_down_sync(FULL, M.x.x, 1), rr = __shfl_down_sync(FULL, M.rho.x, 1);
+        if (lane == 0) xl = M.gx, rl = M.grho;
+        if (lane == 31) xr = M.gx, rr = M.grho;
+        const float4 cv = ld4(L.ct + (size_t)r * g.nx + cl);
+        const bool zm = face_minus(r, g.nz, g.bcz), zp = face_plus(r, g.nz, g.bcz);
+        const float xc[4] = {M.x.x, M.x.y, M.x.z, M.x.w}, rc[4] = {M.rho.x, M.rho.y, M.rho.z, M.rho.w};
+        const float xb[4] = {B.x.x, B.x.y, B.x.z, B.x.w}, rb[4] = {B.rho.x, B.rho.y, B.rho.z, B.rho.w};
+        const float xa[4] = {A.x.x, A.x.y, A.x.z, A.x.w}, ra[4] = {A.rho.x, A.rho.y, A.rho.z, A.rho.w};
+        const float ct[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float xm = e ? xc[e - 1] : xl, rm = e ? rc[e - 1] : rl;
+            const float xp = e < 3 ? xc[e + 1] : xr, rp = e < 3 ? rc[e + 1] : rr;
+            float v = ct[e] * xc[e];
+            if (e > 0 || fl) v += face32(rc[e], rm, L.c2x) * (xc[e] - xm);
+            if (e < 3 || fr) v += face32(rc[e], rp, L.c2x) * (xc[e] - xp);
+            if (zm) v += face32(rc[e], rb[e], L.c2z) * (xc[e] - xb[e]);
+            if (zp) v += face32(rc[e], ra[e], L.c2z) * (xc[e] - xa[e]);
+            y[e] = v;
+        }
+    }
+};
+
+// fc = mean over the four children of (f - A x) on the coarse rows K0 .. K1 - 1
+// of a warp's segment: per coarse row it loads x and rho of fine rows 2K + 1,
+// 2K + 2 and f, c~ of rows 2K, 2K + 1, and writes the lane's two coarse cells
+// as one float2.  Sums in resid_restrict_tile's order.
+__device__ __forceinline__ void rr2d_rows(const Lev32& F, const Geo& C, const float* __restrict__ x,
+                                          const float* __restrict__ f, float* __restrict__ fc, int c0, int K0,
+                                          int K1) {
+    const Seg2D S(F, c0);
+    const int nx = F.g.nx;
+    Row4 rB = S.load(x, 2 * K0 - 1), rM = S.load(x, 2 * K0);
+    for (int K = K0; K < K1; ++K) {
+        const Row4 r1 = S.load(x, 2 * K + 1), r2 = S.load(x, 2 * K + 2);
+        const float4 f0 = ld4(f + (size_t)(2 * K) * nx + S.cl), f1 = ld4(f + (size_t)(2 * K + 1) * nx + S.cl);
+        float y0[4], y1[4];
+        S.apply(2 * K, rB, rM, r1, y0);
+        S.apply(2 * K + 1, rM, r1, r2, y1);
+        float2 v;
+        v.x = ((((0.f + (f0.x - y0[0])) + (f0.y - y0[1])) + (f1.x - y1[0])) + (f1.y - y1[1])) * 0.25f;
+        v.y = ((((0.f + (f0.z - y0[2])) + (f0.w - y0[3])) + (f1.z - y1[2])) + (f1.w - y1[3])) * 0.25f;
+        *reinterpret_cast<float2*>(fc + (size_t)K * C.nx + (c0 >> 1) + 2 * S.lane) = v;
+        rB = r1;
+        rM = r2;
+    }
+}
+
+// y = A x on the rows k0 .. k1 - 1 of a warp's segment (float4 stores), with
+// the lane's x.y and x.r accumulated into axy, axr (DOT_XR: r read too).
+template <bool DOT_XY, bool DOT_XR>
+__device__ __forceinline__ void apply2d_rows(const Lev32& L, const float* __restrict__ x, float* __restrict__ y,
+                                             const float* __restrict__ r, int c0, int k0, int k1, FF& axy, FF& axr) {
+    const Seg2D S(L, c0);
+    const int nx = L.g.nx;
+    Row4 rB = S.load(x, k0 - 1), rM = S.load(x, k0);
+    for (int k = k0; k < k1; ++k) {
+        const Row4 rA = S.load(x, k + 1);
+        const size_t o = (size_t)k * nx + S.cl;
+        const float4 rv = DOT_XR ? ld4(r + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float v[4];
+        S.apply(k, rB, rM, rA, v);
+        *reinterpret_cast<float4*>(y + o) = make_float4(v[0], v[1], v[2], v[3]);
+        const float xc[4] = {rM.x.x, rM.x.y, rM.x.z, rM.x.w}, rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (DOT_XY) ff_add_prod(axy, xc[e], v[e]);
+            if (DOT_XR) ff_add_prod(axr, xc[e], rr[e]);
+        }
+        rB = rM;
+        rM = rA;
+    }
+}
+
 // ---- fused red-black Gauss-Seidel sweep ------------------------------------
 //
 // xout = one red-black Gauss-Seidel sweep applied to xold, the FIRST colour
@@ -610,10 +749,11 @@ __device__ __forceinline__ float rcp_hw(float x) {
 
 // ---- 2D red-black sweep: a warp per row segment and z-chunk ------------------
 //
-// For 2D levels whose nx is a multiple of 256.  The four warps of a 128-thread
-// block take a 256-column task (tile bx, chunk of KZ rows bz) as two 128-cell
-// segments times two halves of the chunk, and each warp marches up its rows
-// on its own: no block barrier, only warp synchronisation.  A warp keeps a
+// For 2D levels whose nx is a multiple of 128.  The four warps of a 128-thread
+// block take a task (tile bx of TW = 256 or 128 columns, chunk of KZ rows bz)
+// as two 128-cell segments times two halves of the chunk, or (TW = 128) one
+// segment times four quarters, and each warp marches up its rows on its own:
+// no block barrier, only warp synchronisation.  A warp keeps a
 // five-row ring of (x, rho) in shared memory, each staged row an even-cell
 // run and an odd-cell run (conflict-free accesses) between run-end slots that
 // hold the neighbouring cells outside the segment (two each side; wrapped on
@@ -626,6 +766,8 @@ __device__ __forceinline__ float rcp_hw(float x) {
 // row p + 2, loaded at the start of the step, is staged into its slot.  The
 // two faces of an axis share one reciprocal.  f and c~ are loaded a step
 // ahead, and x, rho, f, c~ of later rows are prefetched into L2.
+// columns of a task of zrow2d_tile on a level of nx (a multiple of 128) cells
+__host__ __device__ inline int zrow2d_width(int nx) { return nx % 256 == 0 ? 256 : 128; }
 constexpr float Z2_WALL = 1e30f;                    // rho past a wall: face weight negligible, products finite
 __device__ __forceinline__ int z2_e(int m) { return 1 + m; }             // even cell 2m of the segment
 __device__ __forceinline__ int z2_o(int m) { return 3 + 64 + m; }        // odd cell 2m + 1 (64 pairs)
@@ -653,15 +795,18 @@ template <int FIRST, bool ZERO, bool PROLONG>
 __device__ __forceinline__ void zrow2d_tile(const Lev32& L, const float* __restrict__ xin,
                                             const float* __restrict__ ec, const Geo& C, int hx, int hz,
                                             const float* __restrict__ f, float* __restrict__ xout, int KZ, int bx,
-                                            int bz) {
+                                            int bz, int TW) {
     constexpr int NX = 128, M = 64, RS = NX + 4, NR = 5, H = 2;
     __shared__ float2 z2_ring[4][NR * RS];
     const Geo& g = L.g;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float2* XR = z2_ring[w];
-    const int c0 = bx * 256 + (w & 1) * NX;
-    const int t0 = bz * KZ, t1 = min(t0 + KZ, g.nz), tm = t0 + (t1 - t0 + 1) / 2;
-    const int k0 = (w >> 1) ? tm : t0, k1 = (w >> 1) ? t1 : tm;
+    // a task of TW = 256 columns: two segments times two halves of the chunk;
+    // of TW = 128 columns: one segment times four quarters
+    const int nseg = TW >> 7, parts = 4 / nseg, part = w / nseg;
+    const int c0 = bx * TW + (w % nseg) * NX;
+    const int t0 = bz * KZ, t1 = min(t0 + KZ, g.nz), len = t1 - t0;
+    const int k0 = t0 + len * part / parts, k1 = t0 + len * (part + 1) / parts;
     if (k0 >= k1) return;                                // warp-uniform: no block barrier follows
     const int W = g.nx, i2 = 2 * lane;
     auto plane = [&](int p, int& pw) -> bool {           // row p wrapped; false past a wall

@@ -49,6 +49,10 @@ PROBLEMS = {
     "rows2d-256x24": lambda: I.make_problem(256, 24, ma=0.01, contrast=15.0, noise=0.01, seed=10),
     "rows2d-walls-512x10": lambda: I.make_problem(512, 10, ma=0.05, contrast=8.0, noise=0.01, seed=11,
                                                   bc=(NEU, PER, NEU)),
+    # 384-cell rows: three 128-column segments of the 2D residual-restriction
+    # (x walls, periodic z), the tiled 2D sweep
+    "rows2d-walls-384x40": lambda: I.make_problem(384, 40, ma=0.02, contrast=12.0, noise=0.01, seed=16,
+                                                  bc=(NEU, PER, PER)),
     # whole 256- and 128-cell rows, 16 rows a block: the 3D whole-row sweep
     # (several row tiles and z chunks; the next level has 128-cell rows)
     "rows3d-256x32x8": lambda: I.make_problem(256, 8, 32, ma=0.01, contrast=15.0, noise=0.01, seed=12),
@@ -140,6 +144,14 @@ def test_apply_fp32(name):
         dot = g.apply(xd, yd, prec=lm().PREC_FP32, with_dot=True)
         y = yd.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(y - y_ref) <= 1e-5 * np.linalg.norm(y_ref)
+    # per element, against the magnitude of the row's terms: float32 face
+    # weights (an approximate division) and float32 sums, a few ulp of each
+    xs = x.astype(np.float64).reshape(op32.shape)
+    mag = np.abs(op32.ct * xs)
+    for a in range(3):
+        mag = mag + op32.g_minus[a] * np.abs(xs - np.roll(xs, 1, axis=2 - a))
+        mag = mag + op32.g_plus(a) * np.abs(xs - np.roll(xs, -1, axis=2 - a))
+    assert np.all(np.abs(y - y_ref) <= 1e-5 * mag.ravel())
     # the dot of the float32 vectors actually produced, to float64 accuracy
     assert dot == pytest.approx(float(np.vdot(x.astype(np.float64), y)), rel=1e-9)
 
@@ -147,7 +159,8 @@ def test_apply_fp32(name):
 @pytest.mark.parametrize("name,nu", [("plain2d-64", 1), ("conv3d-16", 1), ("ragged3d-12x6x10", 1),
                                      ("ragged2d-37x50-walls", 1), ("conv3d-16", 2), ("plain2d-64", 3),
                                      ("box3d-64x16x24", 1), ("box3d-64x16x24", 2), ("box3d-walls-32x8x16", 2),
-                                     ("rows2d-256x24", 2), ("rows2d-walls-512x10", 1), ("rows3d-256x32x8", 2),
+                                     ("rows2d-256x24", 2), ("rows2d-walls-512x10", 1), ("rows2d-walls-384x40", 1),
+                                     ("rows3d-256x32x8", 2),
                                      ("rows3d-walls-256x16x8", 1), ("rows3d-512x16x12", 2),
                                      ("rows3d-walls-512x32x6", 1)])
 def test_vcycle_matches_oracle(name, nu):
