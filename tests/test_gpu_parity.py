@@ -254,6 +254,23 @@ def test_multigrid_modes_parity(name, mode, bar):
     assert np.linalg.norm(x - xs) <= bar * np.linalg.norm(xs)
 
 
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("rtol", [1e-8, 1e-9])
+def test_mixed_reported_residual(name, rtol):
+    """Row a5 at the workloads' tolerances: the residual the mixed solver
+    reports (its last float64 refinement residual) meets the tolerance and
+    agrees with the oracle's float64 recomputation for the GPU's solution to
+    1e-3 of the tolerance."""
+    p = PROBLEMS[name]()
+    op = P.operator_from_problem(p)
+    with _grid(p) as g:
+        r = g.solve(mode="mixed", rtol=rtol)
+        x = g.solution()
+    rel = P.rel_residual(op, x, p.f)
+    assert r["status"] == 0 and r["rel_residual"] <= rtol and r["outer_iters"] >= 1
+    assert abs(rel - r["rel_residual"]) <= 1e-3 * rtol, (rel, r["rel_residual"])
+
+
 def test_mixed_config1_at_its_tolerance():
     p = I.config_plain_2d(64, seed=3)
     op = P.operator_from_problem(p)
