@@ -933,6 +933,9 @@ def run_kernel(args):
         if args.kernel == "sweep512":
             from paper_1112_3507_gb300 import inputs as I
             p = I.make_problem(512, 64, 512, ma=0.01, contrast=20.0, noise=0.01, seed=1)
+        elif args.kernel == "ops2d":
+            from paper_1112_3507_gb300 import inputs as I
+            p = I.make_problem(4096, 4096, ma=0.01, contrast=15.0, noise=0.01, seed=3)
         else:
             p = make_problem(args.workload, 1)
         g = lm.Grid.for_problem(p)
@@ -941,9 +944,9 @@ def run_kernel(args):
         f = torch.randn_like(x)
         y = torch.empty_like(x)
         for _ in range(4):
-            if args.kernel in ("sweep", "sweep512"):
+            if args.kernel in ("sweep", "sweep512", "ops2d"):
                 g.mg_sweep(x, f, y, 0, stream=stream)
-            else:
+            if args.kernel in ("apply32", "ops2d"):
                 g.apply(x, y, prec=lm.PREC_FP32, stream=stream)
         torch.cuda.synchronize()
         g.close()
@@ -965,10 +968,11 @@ def main():
                     help="run warm-up and timed solves only (for profiler launch lists)")
     ap.add_argument("--dt-factor", type=float, default=1.0,
                     help="gresho256: the time step as a multiple of the sound-speed-induced one (CFL 0.5)")
-    ap.add_argument("--kernel", choices=["sweep", "sweep512", "apply32", "net", "fe32"], default=None,
+    ap.add_argument("--kernel", choices=["sweep", "sweep512", "apply32", "ops2d", "net", "fe32"], default=None,
                     help="profiling runs: a few launches of one kernel on the workload's finest grid "
                          "(sweep: lm_mg_sweep, apply32: lm_apply in float32; sweep512: lm_mg_sweep on a "
-                         "512 x 512 x 64 grid of the convection recipe, 512-cell rows; net: U-Net forward on "
+                         "512 x 512 x 64 grid of the convection recipe, 512-cell rows; ops2d: lm_mg_sweep and "
+                         "float32 lm_apply on a 4096^2 2D grid; net: U-Net forward on "
                          "16 images of 256^2; fe32: lm_fe_apply in float32 on the fe256 points), then exit")
     args = ap.parse_args()
     if args.kernel:

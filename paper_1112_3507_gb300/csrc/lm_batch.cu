@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(NT) kb_ir_residual(const BTask* __restrict__ T
         const double ri = zero_x ? fi : fi - apply64_at(idx, G.geo, G.op, G.x);
         G.r32[idx] = (float)ri;
         acc[0] += ri * ri;
-        acc[1] += fi * fi;
+        if (first) acc[1] += fi * fi;                 // ||f|| is kept from the first residual
     }
     if (zero_x)
         for (int idx = t.lblk * NT + threadIdx.x; idx < G.N; idx += stride) G.x[idx] = 0.0;
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256) kb_apply(const BTask* __restrict__ T, con
     grid_reduce_n<2>(v, G.red, sl, sm, t.lblk, t.nblk);
 }
 
-__global__ void __launch_bounds__(NT) kb_update(const BTask* __restrict__ T, const BGrid* __restrict__ Gs) {
+__global__ void __launch_bounds__(NT, 4) kb_update(const BTask* __restrict__ T, const BGrid* __restrict__ Gs) {
     const BTask t = T[blockIdx.x];
     const BGrid& G = Gs[t.g];
     if (inner_off(G)) return;

@@ -165,11 +165,33 @@ __device__ __forceinline__ void apply32z_tile(const Lev32& L, const float* __res
 }
 
 // ---- 1D vector steps over a block range (block blk of nblk, NT threads) --
+//
+// With N a multiple of 4 and 16-byte aligned vectors (every vector the
+// library allocates; the test is uniform over a launch) a thread takes four
+// consecutive elements per float4 access, otherwise one.
+
+__device__ __forceinline__ bool vec4_ok(int N, const void* a, const void* b, const void* c = nullptr,
+                                        const void* d = nullptr) {
+    return (N & 3) == 0 && (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d) & 15) == 0;
+}
+__device__ __forceinline__ float4 ld4v(const float* p, int i4) { return reinterpret_cast<const float4*>(p)[i4]; }
+__device__ __forceinline__ void st4v(float* p, int i4, float4 v) { reinterpret_cast<float4*>(p)[i4] = v; }
 
 __device__ __forceinline__ FF dot32_range(int N, const float* __restrict__ a, const float* __restrict__ b, int blk,
                                           int nblk) {
     FF acc{0.f, 0.f};
     const int stride = nblk * NT;
+    if (vec4_ok(N, a, b)) {
+#pragma unroll 2
+        for (int i4 = blk * NT + threadIdx.x; i4 < (N >> 2); i4 += stride) {
+            const float4 x = ld4v(a, i4), y = ld4v(b, i4);
+            ff_add_prod(acc, x.x, y.x);
+            ff_add_prod(acc, x.y, y.y);
+            ff_add_prod(acc, x.z, y.z);
+            ff_add_prod(acc, x.w, y.w);
+        }
+        return acc;
+    }
 #pragma unroll 4
     for (int idx = blk * NT + threadIdx.x; idx < N; idx += stride) ff_add_prod(acc, a[idx], b[idx]);
     return acc;
@@ -184,6 +206,20 @@ __device__ __forceinline__ void fcg_beta_p_range(int N, const float* __restrict_
         beta = pq > 0.0 ? (float)(-scal[3] / pq) : 0.f;
     }
     const int stride = nblk * NT;
+    if (vec4_ok(N, z, p)) {
+#pragma unroll 2
+        for (int i4 = blk * NT + threadIdx.x; i4 < (N >> 2); i4 += stride) {
+            const float4 zv = ld4v(z, i4);
+            if (first) {
+                st4v(p, i4, zv);
+            } else {
+                const float4 pv = ld4v(p, i4);
+                st4v(p, i4, make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y), fmaf(beta, pv.z, zv.z),
+                                        fmaf(beta, pv.w, zv.w)));
+            }
+        }
+        return;
+    }
 #pragma unroll 4
     for (int idx = blk * NT + threadIdx.x; idx < N; idx += stride) p[idx] = first ? z[idx] : fmaf(beta, p[idx], z[idx]);
 }
@@ -197,6 +233,22 @@ __device__ __forceinline__ FF fcg_update_range(int N, float* __restrict__ e, flo
     const float alpha = bad ? 0.f : (float)(pr / pq);
     FF rr{0.f, 0.f};
     const int stride = nblk * NT;
+    if (vec4_ok(N, e, r, p, q)) {
+#pragma unroll 2
+        for (int i4 = blk * NT + threadIdx.x; i4 < (N >> 2); i4 += stride) {
+            const float4 pv = ld4v(p, i4), qv = ld4v(q, i4), ev = ld4v(e, i4), rv = ld4v(r, i4);
+            st4v(e, i4, make_float4(fmaf(alpha, pv.x, ev.x), fmaf(alpha, pv.y, ev.y), fmaf(alpha, pv.z, ev.z),
+                                    fmaf(alpha, pv.w, ev.w)));
+            const float4 rn = make_float4(fmaf(-alpha, qv.x, rv.x), fmaf(-alpha, qv.y, rv.y),
+                                          fmaf(-alpha, qv.z, rv.z), fmaf(-alpha, qv.w, rv.w));
+            st4v(r, i4, rn);
+            ff_add_prod(rr, rn.x, rn.x);
+            ff_add_prod(rr, rn.y, rn.y);
+            ff_add_prod(rr, rn.z, rn.z);
+            ff_add_prod(rr, rn.w, rn.w);
+        }
+        return rr;
+    }
 #pragma unroll 4
     for (int idx = blk * NT + threadIdx.x; idx < N; idx += stride) {
         const float pi = p[idx];
