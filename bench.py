@@ -72,7 +72,7 @@ def sweep_kernel(n):
         return "k_rbgs_row"
     if ny > 1 and nx % 32 == 0 and ny % 8 == 0 and nz >= 2:
         return "k_rbgs_zm"
-    if ny == 1 and nx % 256 == 0 and nz >= 2:
+    if ny == 1 and nx % 128 == 0 and nz >= 2:
         return "k_rbgs_zm2d"
     return "k_rbgs"
 WEIGHTS = os.path.join(ROOT, "paper_1112_3507_gb300", "weights", "unet_16_32_48_64.bin")
