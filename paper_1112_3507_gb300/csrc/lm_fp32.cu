@@ -1656,9 +1656,11 @@ void launch_apply32(const Lev32& L, cudaStream_t s, const float* x, float* y, co
 #undef LM_AZ
         return;
     }
-    if (seg2d_ok(g, x, y, L.rho, L.ct, slot_xr >= 0 ? r : nullptr)) {
+    if (seg2d_ok(g, x, y, L.rho, L.ct, slot_xr >= 0 ? r : nullptr) && (long long)(g.nx / 128) * g.nz >= 16 * 152) {
         // 2D rows of 128-column segments: a warp per segment and KR rows, KR
-        // as large as still gives about 32 warps per SM
+        // as large as still gives about 32 warps per SM (grids too small for
+        // 16 warps per SM at one row a warp take the thread-per-column walk
+        // below, whose 32-column warps give more parallelism)
         const int segs = g.nx / 128;
         int KR = 16;
         while (KR > 1 && (long long)segs * hdiv(g.nz, KR) < 32 * 152) KR /= 2;
@@ -1738,9 +1740,10 @@ void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int h
         return;
     }
     count_launches(1);
-    if (rr2d_ok(F, hx, hy, hz, x, f, fc)) {
+    if (rr2d_ok(F, hx, hy, hz, x, f, fc) && (long long)(g.nx / 128) * C.g.nz >= 16 * 152) {
         // 2D rows: a warp per 128-column segment and KR coarse rows, KR as
-        // large as still gives about 32 warps per SM
+        // large as still gives about 32 warps per SM (smaller grids: the
+        // thread-per-coarse-cell kernel below)
         const int segs = g.nx / 128;
         int KR = 8;
         while (KR > 1 && (long long)segs * hdiv(C.g.nz, KR) < 32 * 152) KR /= 2;
@@ -1876,11 +1879,13 @@ void launch_rbgs_kz(const Lev32& L, cudaStream_t s, const float* xin, const floa
         // and half (quarter) chunk; KZ rows per block, about eight blocks (32
         // warps) per SM in all -- four blocks per SM left the loads too few
         // to cover the HBM latency (0.43 against 0.58 of the copy bandwidth
-        // at 4096^2) -- but at least 8 rows a warp
+        // at 4096^2) -- and at least 2 rows a warp (small grids, which cannot
+        // fill the GPU, get as many warps as that allows: their time is the
+        // length of one warp's march)
         const int TW = zrow2d_width(g.nx), tiles = g.nx / TW, parts = 512 / TW;
         int KZ = kz;
         if (kz <= 0) {
-            const int chunks = std::max(1, std::min(hdiv(1216, tiles), g.nz / (8 * parts)));
+            const int chunks = std::max(1, std::min(hdiv(1216, tiles), g.nz / (2 * parts)));
             KZ = hdiv(g.nz, chunks);
         }
         const dim3 grd(tiles, hdiv(g.nz, KZ));
