@@ -466,6 +466,8 @@ def run_ours(args):
     if mode == "learned":
         g.load_network(WEIGHTS)
     solve_kw = dict(mode=mode, rtol=p.rtol, max_iter=args.max_iter)
+    if args.host_checks:
+        solve_kw["check_every"] = 1
     small = 4 * 8 * N < 2 * 129e6           # inputs that fit in L2 get it flushed between steps
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev) if small else None
 
@@ -964,6 +966,10 @@ def main():
     ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--oracle-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-checks", action="store_true",
+                    help="single-grid solves check the inner residual on the host after every iteration "
+                         "(check_every = 1: one graph launch per iteration instead of the device-side loop), "
+                         "so that ncu can time each kernel; for launch lists, not for timing")
     ap.add_argument("--only-steps", action="store_true",
                     help="run warm-up and timed solves only (for profiler launch lists)")
     ap.add_argument("--dt-factor", type=float, default=1.0,

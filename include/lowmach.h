@@ -105,7 +105,14 @@ typedef struct {
                                symmetric                                          */
     double inner_rtol;      /* relative reduction asked of each inner solve      */
     int    inner_max_iter;  /* inner iterations per refinement step               */
-    int    check_every;     /* Krylov iterations between host convergence checks */
+    int    check_every;     /* Krylov iterations between host convergence checks
+                               (float64 modes).  Mixed modes check the inner
+                               solve on the device (one host check per
+                               refinement step) unless check_every == 1: then
+                               the host checks after every inner iteration,
+                               each iteration one CUDA graph launch (slower;
+                               every kernel a plain graph node, which profilers
+                               that time kernels one by one can see)          */
     int    net_precond;     /* LM_MIXED_LEARNED_FCG_IR, the inner preconditioner:
                                0 = the V-cycle (the network gives the warm
                                start only); 1 = the learned two-level cycle,

@@ -580,8 +580,10 @@ int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, in
     int rc;
     MgLevel& M = g->mg[0];
     const Red red{g->part, g->scal, g->ctr};
-    if (!(use_net && *use_net) && ensure_loop_graph(g, o)) {
+    if (!(use_net && *use_net) && o->check_every != 1 && ensure_loop_graph(g, o)) {
         // the whole inner solve on the device: one launch, one host check
+        // (check_every == 1 asks for a host check after every iteration: the
+        // loop below, one graph launch per iteration)
         CK(cudaGraphLaunch(g->loop_exec, s));
         if ((rc = sync_state(g, g->st_in, s))) return rc;
         const int n = std::max(1, g->st_host->iters);

@@ -271,6 +271,23 @@ def test_mixed_reported_residual(name, rtol):
     assert abs(rel - r["rel_residual"]) <= 1e-3 * rtol, (rel, r["rel_residual"])
 
 
+@pytest.mark.parametrize("name", ["conv3d-16", "rows2d-256x24", "rows3d-256x32x8"])
+def test_host_checked_inner_loop(name):
+    """check_every = 1 runs the mixed solve's inner iterations as one graph
+    launch each with a host check after each, instead of the device-side
+    loop: the same kernels in the same order, so the same iterations and
+    the same solution."""
+    p = PROBLEMS[name]()
+    with _grid(p) as g:
+        r0 = g.solve(mode="mixed", rtol=1e-10)
+        x0 = g.solution()
+        r1 = g.solve(mode="mixed", rtol=1e-10, check_every=1)
+        x1 = g.solution()
+    assert r0["status"] == 0 and r1["status"] == 0
+    assert (r0["iters"], r0["outer_iters"]) == (r1["iters"], r1["outer_iters"])
+    np.testing.assert_allclose(x1, x0, rtol=0, atol=1e-12 * np.abs(x0).max())
+
+
 def test_mixed_config1_at_its_tolerance():
     p = I.config_plain_2d(64, seed=3)
     op = P.operator_from_problem(p)
