@@ -722,22 +722,56 @@ int assemble(lm_grid* g, const double* a_in, const double* rho_new, const double
     const double* R = rho_new;
     const double* C = cs2;
     int rc;
-    if (!on_device) {
-        if (!g->stage && (rc = dalloc(&g->stage, (size_t)3 * g->N))) return rc;
-        // the host buffers are free again once the assembly below has been
-        // waited for, before this call returns
-        if ((rc = copy_in(g, g->stage, a_in, 0, s, false))) return rc;
-        if ((rc = copy_in(g, g->stage + g->N, rho_new, 0, s, false))) return rc;
-        if (!raw && (rc = copy_in(g, g->stage + 2 * (size_t)g->N, cs2, 0, s, false))) return rc;
-        A = g->stage;
-        R = g->stage + g->N;
-        C = raw ? nullptr : g->stage + 2 * (size_t)g->N;
-    }
     // flags: max 0, min all ones, no failures
     CK(cudaMemsetAsync(g->asm_fl, 0, sizeof(AsmFlags), s));
     CK(cudaMemsetAsync(&g->asm_fl->rho_min, 0xff, sizeof(unsigned long long), s));
     Op64Out dst{g->ct, g->gx, g->gy, g->gz, g->dinv, g->ct32, g->rho32};
-    launch_assemble(g->geo, g->G, s, A, R, C, dt, raw, g->h, dst, g->asm_fl);
+    if (!on_device) {
+        // Host inputs: copied in chunks of planes on the grid's copy stream,
+        // each chunk assembled on s as soon as it has arrived, so the copies
+        // (bound by the host link) and the assembly (bound by the float64
+        // pipe) overlap.  A cell reads rho^{n+1} of its own plane and the one
+        // below (minus faces only); on a periodic z axis plane 0 reads the
+        // last plane, which is copied first.  The host buffers are free again
+        // once the stream is waited for, before this call returns.
+        if (!g->stage && (rc = dalloc(&g->stage, (size_t)3 * g->N))) return rc;
+        if (!g->copy_stream) {
+            CK(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming));
+            for (cudaEvent_t& e : g->ev_chunk) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        A = g->stage;
+        R = g->stage + g->N;
+        C = raw ? nullptr : g->stage + 2 * (size_t)g->N;
+        const double* src[3] = {a_in, rho_new, cs2};
+        double* dstp[3] = {g->stage, g->stage + g->N, g->stage + 2 * (size_t)g->N};
+        const int narr = raw ? 2 : 3, nz = g->n[2];
+        const size_t plane = (size_t)g->n[0] * g->n[1];
+        // one chunk for small grids: the copies and launches of several cost more than they hide
+        const int nch = g->N >= (1 << 20) ? std::min(8, nz) : 1;
+        const bool wrap_z = nch > 1 && g->bc[2] == LM_BC_PERIODIC;
+        CK(cudaEventRecord(g->ev_in, s));                    // an earlier assembly may still read the stage
+        CK(cudaStreamWaitEvent(g->copy_stream, g->ev_in, 0));
+        auto copy = [&](int a, int k0, int k1) -> cudaError_t {
+            const size_t o = (size_t)k0 * plane;
+            return cudaMemcpyAsync(dstp[a] + o, src[a] + o, sizeof(double) * plane * (k1 - k0), cudaMemcpyHostToDevice,
+                                   g->copy_stream);
+        };
+        if (wrap_z) CK(copy(1, nz - 1, nz));
+        for (int c = 0; c < nch; ++c) {
+            const int k0 = (int)((long long)nz * c / nch), k1 = (int)((long long)nz * (c + 1) / nch);
+            for (int a = 0; a < narr; ++a) {
+                const int e1 = (a == 1 && wrap_z && c == nch - 1) ? k1 - 1 : k1;   // the last plane is there already
+                if (e1 > k0) CK(copy(a, k0, e1));
+            }
+            CK(cudaEventRecord(g->ev_chunk[c], g->copy_stream));
+            CK(cudaStreamWaitEvent(s, g->ev_chunk[c], 0));
+            launch_assemble(g->geo, g->G, s, A, R, C, dt, raw, g->h, dst, g->asm_fl, (int)(k0 * plane),
+                            (int)(k1 * plane));
+        }
+    } else {
+        launch_assemble(g->geo, g->G, s, A, R, C, dt, raw, g->h, dst, g->asm_fl);
+    }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(g->asm_fl_host, g->asm_fl, sizeof(AsmFlags), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -909,6 +943,10 @@ void lm_grid_destroy(lm_grid* g) {
     cudaFree(g->d_inner_it);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     if (g->cap_body) cudaStreamDestroy(g->cap_body);
+    if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
+    if (g->ev_in) cudaEventDestroy(g->ev_in);
+    for (cudaEvent_t e : g->ev_chunk)
+        if (e) cudaEventDestroy(e);
     delete g;
 }
 

@@ -15,8 +15,9 @@ namespace lm {
 
 // ---- coefficient assembly (step (v); Eqs. cpoiss, kappapoiss) -------------
 
-__global__ void __launch_bounds__(NT) k_assemble(AsmArgs a) {
-    assemble_range(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+// cells i0 .. i1 - 1 (one launch per chunk of planes when the inputs arrive in chunks)
+__global__ void __launch_bounds__(NT) k_assemble(AsmArgs a, int i0, int i1) {
+    assemble_range(a, i0 + blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, i1);
 }
 
 __global__ void __launch_bounds__(NT) k_scale32(int N, float* __restrict__ x, float scale) {
@@ -404,9 +405,10 @@ __global__ void __launch_bounds__(NT) k_set_fnorm(const double* part, int slot, 
 // ---- host launchers ---------------------------------------------------------
 
 void launch_assemble(const Geo& g, int G, cudaStream_t s, const double* a_in, const double* rho_new,
-                     const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, AsmFlags* fl) {
+                     const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, AsmFlags* fl,
+                     int i0, int i1) {
     count_launches(1);
-    k_assemble<<<G, NT, 0, s>>>(asm_args(g, a_in, rho_new, cs2, dt, raw, h, out, fl));
+    k_assemble<<<G, NT, 0, s>>>(asm_args(g, a_in, rho_new, cs2, dt, raw, h, out, fl), i0, i1 < 0 ? g.N : i1);
 }
 void launch_scale32(int N, int G, cudaStream_t s, float* x, float scale) {
     count_launches(1);

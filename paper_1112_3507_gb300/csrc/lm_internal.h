@@ -53,6 +53,11 @@ struct lm_grid {
     double* scal = nullptr;         // reduction results (float32 kernels)
     unsigned int* ctr = nullptr;    // last-block arrival counter
     double* stage = nullptr;        // 3N host-input staging (allocated on first use)
+    // host inputs of an assembly arrive in chunks of planes on copy_stream
+    // (one event per chunk) while the assembly of the chunks before runs
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_in = nullptr;
+    cudaEvent_t ev_chunk[8] = {};
     double* part = nullptr;         // NSLOT * MAX_PARTIALS
     double* dscal = nullptr;        // device scalars for lm_apply dots
     SolveState* st = nullptr;       // outer solve state

@@ -81,7 +81,8 @@ inline AsmArgs asm_args(const Geo& g, const double* a_in, const double* rho_new,
 
 // fp64
 void launch_assemble(const Geo& g, int G, cudaStream_t s, const double* a_in, const double* rho_new,
-                     const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, AsmFlags* fl);
+                     const double* cs2, double dt, int raw, const double h[3], const Op64Out& out, AsmFlags* fl,
+                     int i0 = 0, int i1 = -1);
 // x *= scale (float32; scale a power of two, so the scaling is exact)
 void launch_scale32(int N, int G, cudaStream_t s, float* x, float scale);
 void launch_jacobi_diag(const Geo& g, int G, cudaStream_t s, const Op64& op, double* dinv);

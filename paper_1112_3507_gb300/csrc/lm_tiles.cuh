@@ -35,7 +35,7 @@ __device__ __forceinline__ double apply64_at(int idx, const Geo& g, const Op64& 
 // start, start + stride, ... of one grid, with the range of rho^{n+1} and
 // the failure flags reduced per warp into a.fl (every lane of a warp must
 // call this; the launches use whole warps).
-__device__ __forceinline__ void assemble_range(const AsmArgs& a, int start, int stride) {
+__device__ __forceinline__ void assemble_range(const AsmArgs& a, int start, int stride, int end = -1) {
     const Geo& g = a.g;
     const double *a_in = a.a_in, *rho_new = a.rho_new, *cs2 = a.cs2;
     const double dt = a.dt, c2x = a.c2x, c2y = a.c2y, c2z = a.c2z;
@@ -44,7 +44,8 @@ __device__ __forceinline__ void assemble_range(const AsmArgs& a, int start, int 
     AsmFlags* fl = a.fl;
     unsigned long long rmax = 0ull, rmin = ~0ull;        // range of the valid rho^{n+1}
     bool bad32 = false;
-    for (int idx = start; idx < g.N; idx += stride) {
+    const int stop = end < 0 ? g.N : end;
+    for (int idx = start; idx < stop; idx += stride) {
         const double rn = rho_new[idx];
         double c;
         bool ok = rn > 0.0 && isfinite(rn);

@@ -288,6 +288,32 @@ def test_host_checked_inner_loop(name):
     np.testing.assert_allclose(x1, x0, rtol=0, atol=1e-12 * np.abs(x0).max())
 
 
+@pytest.mark.parametrize("shape,bc", [((128, 128, 64), (PER, PER, PER)),       # (nx, nz, ny), bc x, y, z
+                                      ((1024, 1024, 1), (NEU, PER, PER)),
+                                      ((96, 120, 96), (PER, PER, NEU))])
+@pytest.mark.parametrize("raw", [False, True])
+def test_host_inputs_assembled_in_chunks(shape, bc, raw):
+    """Grids of a million cells or more take host inputs in chunks of planes,
+    each assembled as it arrives (a periodic z axis copies the last plane
+    first): the coefficients equal, bit for bit, those assembled in one
+    launch from the same inputs in device memory."""
+    nx, nz, ny = shape
+    p = I.make_problem(nx, nz, ny, ma=0.01, contrast=15.0, noise=0.01, seed=21, bc=bc)
+    assert p.size >= 1 << 20
+    op = P.operator_from_problem(p)
+    with _grid(p) as gh, _grid(p) as gd:
+        if raw:
+            gh.set_coefficients_raw(op.ct, p.rho_new)
+            gd.set_coefficients_raw(_dev(op.ct), _dev(p.rho_new))
+        else:
+            gh.set_coefficients(p.rho_old, p.rho_new, p.cs2, p.dt)
+            gd.set_coefficients(_dev(p.rho_old), _dev(p.rho_new), _dev(p.cs2), p.dt)
+        for a, b in zip(gh.coefficients(), gd.coefficients()):
+            assert torch.equal(a, b)
+        ct = gh.coefficients()[0].cpu().numpy()
+    np.testing.assert_array_equal(ct, op.ct.ravel())
+
+
 def test_mixed_config1_at_its_tolerance():
     p = I.config_plain_2d(64, seed=3)
     op = P.operator_from_problem(p)
