@@ -166,7 +166,7 @@ int build_mg(lm_grid* g, cudaStream_t s, bool defer_inverse = false) {
         g->mg.push_back(C);
     }
     MgLevel& Lc = g->mg.back();
-    if (Lc.L.g.N <= COARSE_MAX) {
+    if (Lc.L.g.N <= COARSE_EXACT) {
         int rc = dalloc(&Lc.ainv, (size_t)Lc.L.g.N * Lc.L.g.N);
         if (rc) return rc;
         inverse(Lc);

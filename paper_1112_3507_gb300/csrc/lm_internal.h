@@ -12,7 +12,8 @@
 
 namespace lm {
 
-constexpr int COARSE_MAX = 64;      // coarsest level solved exactly below this size
+constexpr int COARSE_MAX = 16;      // coarsen while a level has more cells than this and an axis halves
+constexpr int COARSE_EXACT = 64;    // a coarsest level of at most this many cells is solved exactly
 constexpr int COARSE_SWEEPS = 32;   // (RB, BR) sweep pairs when it cannot be
 
 struct MgLevel {

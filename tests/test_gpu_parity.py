@@ -31,6 +31,8 @@ def lm():
 
 
 NEU, PER = I.BC_NEUMANN, I.BC_PERIODIC
+LIB_COARSE_MAX = 16     # the library coarsens while a level has more cells than this and an axis halves,
+LIB_COARSE_EXACT = 64   # and solves a coarsest level of at most this many cells exactly
 
 PROBLEMS = {
     "plain2d-64": lambda: I.config_plain_2d(64, seed=1),
@@ -170,9 +172,10 @@ def test_vcycle_matches_oracle(name, nu):
     op = P.operator_from_problem(p)
     ct32 = op.ct.astype(np.float32).astype(np.float64)
     rho32 = p.rho_new.astype(np.float32).astype(np.float64)
-    levels = OM.build_hierarchy(ct32, rho32, p.h, p.bc)
+    levels = OM.build_hierarchy(ct32, rho32, p.h, p.bc, coarse_max=LIB_COARSE_MAX)
     r = np.random.default_rng(9).standard_normal(p.size).astype(np.float32)
-    z_ref = OM.vcycle(levels, r.astype(np.float64).reshape(p.shape3), nu1=nu, nu2=nu).ravel()
+    z_ref = OM.vcycle(levels, r.astype(np.float64).reshape(p.shape3), nu1=nu, nu2=nu,
+                      coarse_max=LIB_COARSE_EXACT).ravel()
     with _grid(p) as g:
         shapes = g.mg_levels()
         assert [tuple(reversed(L.shape)) for L in levels] == shapes
