@@ -576,20 +576,38 @@ bool ensure_loop_graph(lm_grid* g, const lm_solve_opts* o) {
 // preconditioner that leaves the inner residual above 1/2 after 4
 // iterations, or returns a non-finite value, switches the rest of the solve
 // to the V-cycle (*use_net = false).
-int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, int* vcycles, bool* use_net) {
+// Inner iterations and launches of a device-side inner solve whose state
+// the caller copied into st_host[1] and has waited for.
+void account_device_inner(lm_grid* g, int* iters, int* vcycles) {
+    const int n = std::max(1, g->st_host[1].iters);
+    count_launches(g->loop_nk[0] + (long long)(n - 1) * g->loop_nk[1]);
+    *iters += n;
+    *vcycles += n;
+}
+
+// *deferred (when given) lets the device-side inner solve return without a
+// host wait: its state is queued for copy into st_host[1], and the caller
+// waits once for it and the next refinement residual together, then calls
+// account_device_inner.
+int inner_fcg(lm_grid* g, const lm_solve_opts* o, cudaStream_t s, int* iters, int* vcycles, bool* use_net,
+              bool* deferred = nullptr) {
     int rc;
     MgLevel& M = g->mg[0];
     const Red red{g->part, g->scal, g->ctr};
+    if (deferred) *deferred = false;
     if (!(use_net && *use_net) && o->check_every != 1 && ensure_loop_graph(g, o)) {
         // the whole inner solve on the device: one launch, one host check
         // (check_every == 1 asks for a host check after every iteration: the
         // loop below, one graph launch per iteration)
         CK(cudaGraphLaunch(g->loop_exec, s));
-        if ((rc = sync_state(g, g->st_in, s))) return rc;
-        const int n = std::max(1, g->st_host->iters);
-        count_launches(g->loop_nk[0] + (long long)(n - 1) * g->loop_nk[1]);
-        *iters += n;
-        *vcycles += n;
+        CK(cudaMemcpyAsync(g->st_host + 1, g->st_in, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        if (deferred) {
+            *deferred = true;
+            return LM_OK;
+        }
+        CK(cudaStreamSynchronize(s));
+        account_device_inner(g, iters, vcycles);
+        g->st_host[0] = g->st_host[1];
         return LM_OK;
     }
     CK(cudaMemsetAsync(g->e32, 0, sizeof(float) * g->N, s));
@@ -684,13 +702,18 @@ int solve_mixed_ir(lm_grid* g, const lm_solve_opts* o, lm_solve_result* res, boo
     int outer = 0, iters = 0, vc = 0;
     int status = LM_OK;
     while (rel > o->rtol && outer < o->max_outer && iters < o->max_iter) {
-        if ((rc = inner_fcg(g, o, s, &iters, &vc, &use_net))) return rc;
-        if (g->st_host->status) status = g->st_host->status;
+        bool deferred = false;
+        if ((rc = inner_fcg(g, o, s, &iters, &vc, &use_net, &deferred))) return rc;
+        if (!deferred && g->st_host->status) status = g->st_host->status;
         launch_ir_correct(g->N, g->G, s, g->x, g->e32, 1.0 / rs);
         const double rs_next = pow2_near_inv(rel * fnorm * std::max(o->inner_rtol, 1e-12) / sqN);
         launch_ir_residual(g->geo, g->G, s, op64(g), g->f, g->x, g->r32, g->part, 0, g->st, 0, nullptr, rs_next);
         CK(cudaGetLastError());
-        if ((rc = sync_state(g, g->st, s))) return rc;
+        if ((rc = sync_state(g, g->st, s))) return rc;     // also the inner state queued before
+        if (deferred) {
+            account_device_inner(g, &iters, &vc);
+            if (g->st_host[1].status) status = g->st_host[1].status;
+        }
         const double nrel = g->st_host->rel;
         g->history.push_back(nrel);
         ++outer;
@@ -910,7 +933,8 @@ int lm_grid_create(int ndim, const int64_t n[3], const double h[3], const int bc
     if ((rc = dalloc(&g->st, 1))) return fail(rc);
     if ((rc = dalloc(&g->st_in, 1))) return fail(rc);
     if ((rc = dalloc(&g->asm_fl, 1))) return fail(rc);
-    if (cudaMallocHost((void**)&g->st_host, sizeof(SolveState)) != cudaSuccess) return fail(LM_ERR_OUT_OF_MEMORY);
+    // st_host[0]: the state last waited for; st_host[1]: a device-side inner solve's
+    if (cudaMallocHost((void**)&g->st_host, 2 * sizeof(SolveState)) != cudaSuccess) return fail(LM_ERR_OUT_OF_MEMORY);
     if (cudaMallocHost((void**)&g->asm_fl_host, sizeof(AsmFlags)) != cudaSuccess) return fail(LM_ERR_OUT_OF_MEMORY);
     if (cudaMallocHost((void**)&g->dscal_host, 8 * sizeof(double)) != cudaSuccess) return fail(LM_ERR_OUT_OF_MEMORY);
     if (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess) return fail(LM_ERR_CUDA);
