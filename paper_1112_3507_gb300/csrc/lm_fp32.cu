@@ -211,24 +211,28 @@ constexpr size_t apply_row_smem() {
     return sizeof(float2) * 4 * (TY + 2) * (32 * CPT + 4);
 }
 
-template <int CPT, int TY, bool DOT_XY, bool DOT_XR>
+template <int CPT, int TY, bool DOT_XY, bool DOT_XR, int SEG = 1>
 __global__ void __launch_bounds__(32 * TY, 1) k_apply32_row(Lev32 L, const float* __restrict__ x,
                                                            float* __restrict__ y, const float* __restrict__ r,
                                                            Red red, int slot_xy, int slot_xr, int KZ) {
     constexpr int NX = 32 * CPT, RS = NX + 4, NRW = TY + 2, PL = NRW * RS, H = CPT / 2;
+    constexpr int W = NX * SEG;                           // cells in a grid row
+    static_assert(SEG == 1 || (SEG == 2 && 2 * NRW <= 32 * TY && 4 * TY <= 32 * TY), "x-halo threads");
     static_assert(CPT % 2 == 0 && TY >= 2 * H, "a warp per halo pair group");
     extern __shared__ float4 ap_smem[];
     float2* XR = reinterpret_cast<float2*>(ap_smem);
     __shared__ double sm[64];
     const Geo& g = L.g;
     const int lane = threadIdx.x, wy = threadIdx.y, tid = lane + 32 * wy;
-    const int j0 = blockIdx.x * TY, k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
-    const int sz = NX * g.ny, i2 = 2 * lane;
+    const int j0 = (blockIdx.x / SEG) * TY, c0 = (blockIdx.x % SEG) * NX, k0 = blockIdx.y * KZ,
+              k1 = min(k0 + KZ, g.nz);
+    const int sz = W * g.ny, i2 = 2 * lane;
     const float INF = __int_as_float(0x7f800000);
     for (int t = tid; t < 4 * NRW; t += 32 * TY) {       // row-end ghosts: x = 0, rho = +inf
         XR[t * RS + 1] = make_float2(0.f, INF);
         XR[t * RS + NX + 2] = make_float2(0.f, INF);
     }
+    if (SEG > 1) __syncthreads();                         // segments stage those slots: after the walls
     auto rowj = [&](int r_, int& jw) -> bool {           // staged row -> grid row; false past a wall
         int j = j0 - 1 + r_;
         if (j < 0 || j >= g.ny) {
@@ -251,7 +255,20 @@ __global__ void __launch_bounds__(32 * TY, 1) k_apply32_row(Lev32 L, const float
     int jT = 0, jS = 0;
     rowj(rT, jT);
     const bool hasS = uS < H, okS = hasS && rowj(rS, jS);
-    const bool perx = g.bcx == LM_BC_PERIODIC;
+    // whole rows wrap around the staged row; a segment's x-neighbours outside
+    // it are staged into the row-end slots each plane (SEG > 1): thread
+    // 2 r + e stages staged row r's cell c0 - 1 (e = 0) or c0 + NX (e = 1);
+    // past a wall x = 0, rho = +inf
+    const bool perx = SEG == 1 && g.bcx == LM_BC_PERIODIC;
+    const bool hasG = SEG > 1 && tid < 2 * NRW;
+    const int rG = tid >> 1, gG = tid & 1;
+    int gCol = gG ? c0 + NX : c0 - 1;
+    bool gOK = true;
+    if (gCol < 0 || gCol >= W) {
+        if (g.bcx == LM_BC_PERIODIC) gCol = gCol < 0 ? gCol + W : gCol - W;
+        else gOK = false;
+    }
+    float gxv = 0.f, grv = INF;
     float vx[CPT], vr[CPT], hx2[2], hr2[2];
     auto fetch = [&](int p) {
         int pw = 0;
@@ -259,7 +276,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_apply32_row(Lev32 L, const float
 #pragma unroll
         for (int u = 0; u < H; ++u) {
             if (okp) {
-                const int o = sz * pw + NX * jT + 64 * u + i2;
+                const int o = sz * pw + W * jT + c0 + 64 * u + i2;
                 const float2 a = *reinterpret_cast<const float2*>(x + o), b = *reinterpret_cast<const float2*>(L.rho + o);
                 vx[2 * u] = a.x; vx[2 * u + 1] = a.y; vr[2 * u] = b.x; vr[2 * u + 1] = b.y;
             } else {
@@ -269,12 +286,23 @@ __global__ void __launch_bounds__(32 * TY, 1) k_apply32_row(Lev32 L, const float
         }
         if (hasS) {
             if (okp && okS) {
-                const int o = sz * pw + NX * jS + 64 * uS + i2;
+                const int o = sz * pw + W * jS + c0 + 64 * uS + i2;
                 const float2 a = *reinterpret_cast<const float2*>(x + o), b = *reinterpret_cast<const float2*>(L.rho + o);
                 hx2[0] = a.x; hx2[1] = a.y; hr2[0] = b.x; hr2[1] = b.y;
             } else {
                 hx2[0] = hx2[1] = 0.f;
                 hr2[0] = hr2[1] = INF;
+            }
+        }
+        if (SEG > 1 && hasG) {                            // x-halo cell of staged row rG
+            int jw = 0;
+            if (okp && rowj(rG, jw) && gOK) {
+                const int o = sz * pw + W * jw + gCol;
+                gxv = x[o];
+                grv = L.rho[o];
+            } else {
+                gxv = 0.f;
+                grv = INF;
             }
         }
     };
@@ -286,10 +314,11 @@ __global__ void __launch_bounds__(32 * TY, 1) k_apply32_row(Lev32 L, const float
         if (hasS)
             *reinterpret_cast<float4*>(XR + (s * NRW + rS) * RS + 2 + 64 * uS + i2) =
                 make_float4(hx2[0], hr2[0], hx2[1], hr2[1]);
+        if (SEG > 1 && hasG) XR[(s * NRW + rG) * RS + (gG ? NX + 2 : 1)] = make_float2(gxv, grv);
     };
     float ctv[CPT], rrv[CPT];
     auto load_c = [&](int p) {                            // c~ (and r) of the warp's row on plane p
-        const int o = sz * p + NX * jT + lane;
+        const int o = sz * p + W * jT + c0 + lane;
 #pragma unroll
         for (int v = 0; v < CPT; ++v) {
             ctv[v] = L.ct[o + 32 * v];
@@ -300,15 +329,19 @@ __global__ void __launch_bounds__(32 * TY, 1) k_apply32_row(Lev32 L, const float
     const int rrel = (lane == 31 && perx) ? 1 - NX : 1;
     // L2 prefetch of the block's own rows, PF_PLANES steps ahead: x and rho of
     // plane P are staged at step P - 2, c~ and r read at step P - 1; array
-    // a = 0..3 (x, rho, c~, r) is requested by thread a.
+    // a = 0..3 (x, rho, c~, r) is requested by thread a (a segment's rows are
+    // not contiguous: one request per row, thread a TY + r for row r)
+    constexpr int NPF = SEG == 1 ? 4 : 4 * TY;
+    const int pfa = SEG == 1 ? tid : tid / TY, pfr = SEG == 1 ? 0 : tid % TY;
     auto prefetch = [&](int a, int P) {
         int pw = 0;
         if (P > (a < 2 ? k1 : k1 - 1) || (!DOT_XR && a == 3) || !plane(P, pw)) return;
         const float* base = a == 0 ? x : a == 1 ? L.rho : a == 2 ? L.ct : r;
-        prefetch_l2(base + sz * pw + NX * j0, NX * TY * sizeof(float));
+        if (SEG == 1) prefetch_l2(base + sz * pw + NX * j0, NX * TY * sizeof(float));
+        else prefetch_l2(base + sz * pw + W * (j0 + pfr) + c0, NX * sizeof(float));
     };
-    if (tid < 4)
-        for (int d = 1; d <= PF_PLANES; ++d) prefetch(tid, (tid < 2 ? k0 + 1 : k0) + d);
+    if (tid < NPF)
+        for (int d = 1; d <= PF_PLANES; ++d) prefetch(pfa, (pfa < 2 ? k0 + 1 : k0) + d);
     FF axy{0.f, 0.f}, axr{0.f, 0.f};
     int sm1 = 0, s0 = 1, sp1 = 2, sp2 = 3;                // slots of planes p - 1 .. p + 2
     fetch(k0 - 1);
@@ -321,10 +354,10 @@ __global__ void __launch_bounds__(32 * TY, 1) k_apply32_row(Lev32 L, const float
     __syncthreads();
     for (int p = k0; p < k1; ++p) {
         const bool stage = p + 2 <= k1;
-        if (tid < 4) prefetch(tid, (tid < 2 ? p + 2 : p + 1) + PF_PLANES);
+        if (tid < NPF) prefetch(pfa, (pfa < 2 ? p + 2 : p + 1) + PF_PLANES);
         if (stage) fetch(p + 2);
         const int b0 = (s0 * NRW + rT) * RS + 2 + lane, dzm = (sm1 - s0) * PL, dzp = (sp1 - s0) * PL;
-        float* yrow = y + sz * p + NX * jT + lane;
+        float* yrow = y + sz * p + W * jT + c0 + lane;
 #pragma unroll
         for (int v = 0; v < CPT; ++v) {
             const int c = b0 + 32 * v;
@@ -942,6 +975,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_rbgs_row(Lev32 L, const float* _
         XR[t * RS + run_o(M, -1)] = gh;
         XR[t * RS + run_o(M, M)] = gh;
     }
+    if (SEG > 1) __syncthreads();                         // segments stage those slots: after the walls
     // staged row r <-> grid row j0 - 2 + r, wrapped; false past a wall
     auto rowj = [&](int r, int& jw) -> bool {
         int j = j0 - 2 + r;
@@ -1431,23 +1465,27 @@ static dim3 cell_grid(const Geo& g) {
 // shuffle, and the odd row of each row pair stores its sums in fc, which the
 // even row adds to its own and scales at the next step (after the step's
 // barrier).  For levels halved along all three axes.
-template <int CPT, int TY>
+template <int CPT, int TY, int SEG = 1>
 __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo C, const float* __restrict__ x,
                                                                   const float* __restrict__ f,
                                                                   float* __restrict__ fc, int KZ) {
     constexpr int NX = 32 * CPT, RS = NX + 4, NRW = TY + 2, PL = NRW * RS, H = CPT / 2;
     static_assert(CPT % 2 == 0 && TY % 2 == 0 && TY >= 2 * H, "row pairs; a warp per halo pair group");
+    constexpr int W = NX * SEG;                           // cells in a grid row
+    static_assert(SEG == 1 || (SEG == 2 && 2 * NRW <= 32 * TY && 4 * TY <= 32 * TY), "x-halo threads");
     extern __shared__ float4 ap_smem[];
     float2* XR = reinterpret_cast<float2*>(ap_smem);
     const Geo& g = L.g;
     const int lane = threadIdx.x, wy = threadIdx.y, tid = lane + 32 * wy;
-    const int j0 = blockIdx.x * TY, k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
-    const int sz = NX * g.ny, i2 = 2 * lane;
+    const int j0 = (blockIdx.x / SEG) * TY, c0 = (blockIdx.x % SEG) * NX, k0 = blockIdx.y * KZ,
+              k1 = min(k0 + KZ, g.nz);
+    const int sz = W * g.ny, i2 = 2 * lane;
     const float INF = __int_as_float(0x7f800000);
     for (int t = tid; t < 4 * NRW; t += 32 * TY) {
         XR[t * RS + 1] = make_float2(0.f, INF);
         XR[t * RS + NX + 2] = make_float2(0.f, INF);
     }
+    if (SEG > 1) __syncthreads();                         // segments stage those slots: after the walls
     auto rowj = [&](int r_, int& jw) -> bool {
         int j = j0 - 1 + r_;
         if (j < 0 || j >= g.ny) {
@@ -1470,7 +1508,17 @@ __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo 
     int jT = 0, jS = 0;
     rowj(rT, jT);
     const bool hasS = uS < H, okS = hasS && rowj(rS, jS);
-    const bool perx = g.bcx == LM_BC_PERIODIC;
+    // a segment's x-neighbours outside it: staged into the row-end slots (as in k_apply32_row)
+    const bool perx = SEG == 1 && g.bcx == LM_BC_PERIODIC;
+    const bool hasG = SEG > 1 && tid < 2 * NRW;
+    const int rG = tid >> 1, gG = tid & 1;
+    int gCol = gG ? c0 + NX : c0 - 1;
+    bool gOK = true;
+    if (gCol < 0 || gCol >= W) {
+        if (g.bcx == LM_BC_PERIODIC) gCol = gCol < 0 ? gCol + W : gCol - W;
+        else gOK = false;
+    }
+    float gxv = 0.f, grv = INF;
     float vx[CPT], vr[CPT], hx2[2], hr2[2];
     auto fetch = [&](int p) {
         int pw = 0;
@@ -1478,7 +1526,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo 
 #pragma unroll
         for (int u = 0; u < H; ++u) {
             if (okp) {
-                const int o = sz * pw + NX * jT + 64 * u + i2;
+                const int o = sz * pw + W * jT + c0 + 64 * u + i2;
                 const float2 a = *reinterpret_cast<const float2*>(x + o), b = *reinterpret_cast<const float2*>(L.rho + o);
                 vx[2 * u] = a.x; vx[2 * u + 1] = a.y; vr[2 * u] = b.x; vr[2 * u + 1] = b.y;
             } else {
@@ -1488,12 +1536,23 @@ __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo 
         }
         if (hasS) {
             if (okp && okS) {
-                const int o = sz * pw + NX * jS + 64 * uS + i2;
+                const int o = sz * pw + W * jS + c0 + 64 * uS + i2;
                 const float2 a = *reinterpret_cast<const float2*>(x + o), b = *reinterpret_cast<const float2*>(L.rho + o);
                 hx2[0] = a.x; hx2[1] = a.y; hr2[0] = b.x; hr2[1] = b.y;
             } else {
                 hx2[0] = hx2[1] = 0.f;
                 hr2[0] = hr2[1] = INF;
+            }
+        }
+        if (SEG > 1 && hasG) {
+            int jw = 0;
+            if (okp && rowj(rG, jw) && gOK) {
+                const int o = sz * pw + W * jw + gCol;
+                gxv = x[o];
+                grv = L.rho[o];
+            } else {
+                gxv = 0.f;
+                grv = INF;
             }
         }
     };
@@ -1505,10 +1564,11 @@ __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo 
         if (hasS)
             *reinterpret_cast<float4*>(XR + (s * NRW + rS) * RS + 2 + 64 * uS + i2) =
                 make_float4(hx2[0], hr2[0], hx2[1], hr2[1]);
+        if (SEG > 1 && hasG) XR[(s * NRW + rG) * RS + (gG ? NX + 2 : 1)] = make_float2(gxv, grv);
     };
     float ctv[CPT], fv[CPT], acc[CPT];
     auto load_c = [&](int p) {
-        const int o = sz * p + NX * jT + lane;
+        const int o = sz * p + W * jT + c0 + lane;
 #pragma unroll
         for (int v = 0; v < CPT; ++v) {
             ctv[v] = L.ct[o + 32 * v];
@@ -1518,14 +1578,17 @@ __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo 
     const int lrel = (lane == 0 && perx) ? NX - 1 : -1;
     const int rrel = (lane == 31 && perx) ? 1 - NX : 1;
     // L2 prefetch as in k_apply32_row; arrays x, rho, c~, f
+    constexpr int NPF = SEG == 1 ? 4 : 4 * TY;
+    const int pfa = SEG == 1 ? tid : tid / TY, pfr = SEG == 1 ? 0 : tid % TY;
     auto prefetch = [&](int a, int P) {
         int pw = 0;
         if (P > (a < 2 ? k1 : k1 - 1) || !plane(P, pw)) return;
         const float* base = a == 0 ? x : a == 1 ? L.rho : a == 2 ? L.ct : f;
-        prefetch_l2(base + sz * pw + NX * j0, NX * TY * sizeof(float));
+        if (SEG == 1) prefetch_l2(base + sz * pw + NX * j0, NX * TY * sizeof(float));
+        else prefetch_l2(base + sz * pw + W * (j0 + pfr) + c0, NX * sizeof(float));
     };
-    if (tid < 4)
-        for (int d = 1; d <= PF_PLANES; ++d) prefetch(tid, (tid < 2 ? k0 + 1 : k0) + d);
+    if (tid < NPF)
+        for (int d = 1; d <= PF_PLANES; ++d) prefetch(pfa, (pfa < 2 ? k0 + 1 : k0) + d);
     int sm1 = 0, s0 = 1, sp1 = 2, sp2 = 3;
     // an even row's pair sums wait one step (one barrier) for the odd row's
     float accP[CPT];
@@ -1547,7 +1610,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo 
     };
     for (int p = k0; p < k1; ++p) {
         const bool stage = p + 2 <= k1;
-        if (tid < 4) prefetch(tid, (tid < 2 ? p + 2 : p + 1) + PF_PLANES);
+        if (tid < NPF) prefetch(pfa, (pfa < 2 ? p + 2 : p + 1) + PF_PLANES);
         if (stage) fetch(p + 2);
         finish_pairs();
         const int b0 = (s0 * NRW + rT) * RS + 2 + lane, dzm = (sm1 - s0) * PL, dzp = (sp1 - s0) * PL;
@@ -1568,7 +1631,7 @@ __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo 
             const float rv = fv[v] - val;
             acc[v] = odd ? acc[v] + rv : rv;
         }
-        float* const dst = fc + C.nx * (((j0 + wy) >> 1) + C.ny * (p >> 1)) + (lane >> 1);
+        float* const dst = fc + C.nx * (((j0 + wy) >> 1) + C.ny * (p >> 1)) + (c0 >> 1) + (lane >> 1);
         if (odd) {                                        // x pairs; the odd row's sums to fc
 #pragma unroll
             for (int v = 0; v < CPT; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], 1);
@@ -1595,44 +1658,49 @@ __global__ void __launch_bounds__(32 * TY, 1) k_resid_restrict_row(Lev32 L, Geo 
     finish_pairs();                                       // the last step ended with a barrier
 }
 
-template <int CPT>
+template <int CPT, int SEG = 1>
 static void launch_resid_restrict_row(const Lev32& F, const Geo& C, cudaStream_t s, const float* x, const float* f,
                                       float* fc) {
     constexpr int TY = 16;
     const Geo& g = F.g;
-    const int ntile = g.ny / TY;
+    const int ntile = g.ny / TY * SEG;
     int chunks = std::max(1, std::min(g.nz / 2, 152 / ntile));
     int KZ = hdiv(g.nz, chunks);
     KZ += KZ & 1;                                         // chunks start on even planes
     const dim3 grd(ntile, hdiv(g.nz, KZ)), blk(32, TY);
     const size_t sm = apply_row_smem<CPT, TY>();
     count_launches(1);
-    k_resid_restrict_row<CPT, TY><<<grd, blk, sm, s>>>(F, C, x, f, fc, KZ);
+    k_resid_restrict_row<CPT, TY, SEG><<<grd, blk, sm, s>>>(F, C, x, f, fc, KZ);
 }
 
-template <int CPT>
+template <int CPT, int SEG = 1>
 static void launch_apply32_row(const Lev32& L, cudaStream_t s, const float* x, float* y, const float* r,
                                const Red& red, int slot_xy, int slot_xr) {
     constexpr int TY = 16;
     const Geo& g = L.g;
-    const int ntile = g.ny / TY;
+    const int ntile = g.ny / TY * SEG;
     const int chunks = std::max(1, std::min(g.nz / 2, 152 / ntile));
     const int KZ = hdiv(g.nz, chunks);
     const dim3 grd(ntile, hdiv(g.nz, KZ)), blk(32, TY);
     const size_t sm = apply_row_smem<CPT, TY>();
     const bool dxy = slot_xy >= 0, dxr = slot_xr >= 0;
     count_launches(1);
-    if (dxy && dxr) k_apply32_row<CPT, TY, true, true><<<grd, blk, sm, s>>>(L, x, y, r, red, slot_xy, slot_xr, KZ);
-    else if (dxy) k_apply32_row<CPT, TY, true, false><<<grd, blk, sm, s>>>(L, x, y, r, red, slot_xy, slot_xr, KZ);
-    else k_apply32_row<CPT, TY, false, false><<<grd, blk, sm, s>>>(L, x, y, r, red, slot_xy, slot_xr, KZ);
+#define LM_AR(A, B) k_apply32_row<CPT, TY, A, B, SEG><<<grd, blk, sm, s>>>(L, x, y, r, red, slot_xy, slot_xr, KZ)
+    if (dxy && dxr) LM_AR(true, true);
+    else if (dxy) LM_AR(true, false);
+    else LM_AR(false, false);
+#undef LM_AR
 }
 
 void launch_apply32(const Lev32& L, cudaStream_t s, const float* x, float* y, const float* r, const Red& red,
                     int slot_xy, int slot_xr) {
     const Geo& g = L.g;
-    if (g.ny > 1 && g.ny % 16 == 0 && g.nz >= 2 && (g.nx == 256 || g.nx == 128) && ((uintptr_t)x & 7) == 0) {
-        // whole rows of 256 or 128 cells: a warp per row, 16 rows per block
-        if (g.nx == 256) launch_apply32_row<8>(L, s, x, y, r, red, slot_xy, slot_xr);
+    if (g.ny > 1 && g.ny % 16 == 0 && g.nz >= 2 && (g.nx == 512 || g.nx == 256 || g.nx == 128) &&
+        ((uintptr_t)x & 7) == 0) {
+        // whole rows of 256 or 128 cells, or 512-cell rows as two 256-cell
+        // segments with an x-halo: a warp per row, 16 rows per block
+        if (g.nx == 512) launch_apply32_row<8, 2>(L, s, x, y, r, red, slot_xy, slot_xr);
+        else if (g.nx == 256) launch_apply32_row<8>(L, s, x, y, r, red, slot_xy, slot_xr);
         else launch_apply32_row<4>(L, s, x, y, r, red, slot_xy, slot_xr);
         return;
     }
@@ -1732,10 +1800,12 @@ void launch_coarsen(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cuda
 void launch_resid_restrict(const Lev32& F, const Lev32& C, int hx, int hy, int hz, cudaStream_t s,
                            const float* x, const float* f, float* fc) {
     const Geo& g = F.g;
-    if (hx && hy && hz && g.ny % 16 == 0 && g.nz % 2 == 0 && (g.nx == 256 || g.nx == 128) &&
+    if (hx && hy && hz && g.ny % 16 == 0 && g.nz % 2 == 0 && (g.nx == 512 || g.nx == 256 || g.nx == 128) &&
         ((uintptr_t)x & 7) == 0) {
-        // whole rows of 256 or 128 cells: a warp per row, 16 rows per block
-        if (g.nx == 256) launch_resid_restrict_row<8>(F, C.g, s, x, f, fc);
+        // whole rows of 256 or 128 cells, or 512-cell rows as two 256-cell
+        // segments with an x-halo: a warp per row, 16 rows per block
+        if (g.nx == 512) launch_resid_restrict_row<8, 2>(F, C.g, s, x, f, fc);
+        else if (g.nx == 256) launch_resid_restrict_row<8>(F, C.g, s, x, f, fc);
         else launch_resid_restrict_row<4>(F, C.g, s, x, f, fc);
         return;
     }
@@ -1776,12 +1846,12 @@ static void rbgs_row_allow() {
     cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 0, false, true, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_rbgs_row<CPT, TY, 1, false, true, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
-template <int CPT, int TY>
+template <int CPT, int TY, int SEG = 1>
 static void apply_row_allow() {
     const int sm = (int)apply_row_smem<CPT, TY>();
-    cudaFuncSetAttribute(k_apply32_row<CPT, TY, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_apply32_row<CPT, TY, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_apply32_row<CPT, TY, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_apply32_row<CPT, TY, true, true, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_apply32_row<CPT, TY, true, false, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_apply32_row<CPT, TY, false, false, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 void rbgs_row_allow_smem() {
     rbgs_row_allow<8, 16>();
@@ -1789,10 +1859,13 @@ void rbgs_row_allow_smem() {
     rbgs_row_allow<8, 16, 2>();
     apply_row_allow<8, 16>();
     apply_row_allow<4, 16>();
+    apply_row_allow<8, 16, 2>();
     cudaFuncSetAttribute(k_resid_restrict_row<8, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)apply_row_smem<8, 16>());
     cudaFuncSetAttribute(k_resid_restrict_row<4, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)apply_row_smem<4, 16>());
+    cudaFuncSetAttribute(k_resid_restrict_row<8, 16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)apply_row_smem<8, 16>());
 }
 
 static bool aligned8(const void* p) { return ((uintptr_t)p & 7) == 0; }
