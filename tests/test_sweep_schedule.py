@@ -11,7 +11,11 @@ the sweep's input.  This test replays that schedule with numpy on small grids
 reproduces the oracle's sequential red-black sweep: the reading that the
 lag-two schedule needs no second barrier and no cross-block communication.
 The arithmetic of each update uses the oracle's face conductances; only the
-order of the updates is under test.
+order of the updates is under test.  The segmented kernels (512-cell rows as
+two segments; the 2D sweep's 128-cell warp segments) are replayed the same
+way: the segment schedule of the sweep, and the row-end staging of the
+apply and residual kernels, whose end slots hold the neighbouring segment's
+cells.
 """
 import numpy as np
 import pytest
@@ -229,4 +233,71 @@ def test_segment_schedule_needs_the_outside_update():
     x, f = rng.standard_normal(shape), rng.standard_normal(shape)
     ref = OM.sweep(level, x, f, "RB")
     bad = _segment_schedule_sweep(level, x, f, 0, 8, 4, halo_update=False)
+    assert not np.allclose(bad, ref, rtol=1e-6, atol=1e-6)
+
+
+def _segmented_apply(level, x, NX, whole_row_wrap=False):
+    """A x by the segmented row kernels' staging, replayed with numpy: the
+    grid's rows are cut into segments of NX cells; a segment's staged row
+    holds its cells plus one row-end slot each side, filled with the cell
+    just outside the segment (wrapped on a periodic x axis, a wall -- no
+    face -- past a wall), and the x faces at the segment's ends read those
+    slots; y and z neighbours come from the grid.  whole_row_wrap plants
+    the mistake of wrapping inside the segment, as a whole-row kernel does."""
+    nz, ny, nx = level.shape
+    bcx = level.bc[0]
+    op = level.op
+    g = _faces(level)
+    y = op.ct * x
+    for a in (1, 2):                                     # y and z faces from the grid
+        xm = np.roll(x, 1, axis=2 - a)
+        xp = np.roll(x, -1, axis=2 - a)
+        y = y + g[2 * a] * (x - xm) + g[2 * a + 1] * (x - xp)
+    for c0 in range(0, nx, NX):
+        cols = np.arange(c0, c0 + NX)
+        left = c0 - 1 if not whole_row_wrap else c0 + NX - 1
+        right = c0 + NX if not whole_row_wrap else c0
+        xl = np.empty_like(x[..., cols])
+        xr = np.empty_like(x[..., cols])
+        xl[..., 1:] = x[..., cols[:-1]]
+        xr[..., :-1] = x[..., cols[1:]]
+        okl = left >= 0 or bcx == PER or whole_row_wrap
+        okr = right < nx or bcx == PER or whole_row_wrap
+        xl[..., 0] = x[..., left % nx] if okl else 0.0
+        xr[..., -1] = x[..., right % nx] if okr else 0.0
+        wl = g[0][..., cols].copy()
+        wr = g[1][..., cols].copy()
+        if not okl:
+            wl[..., 0] = 0.0
+        if not okr:
+            wr[..., -1] = 0.0
+        y[..., cols] += wl * (x[..., cols] - xl) + wr * (x[..., cols] - xr)
+    return y
+
+
+@pytest.mark.parametrize("shape,bc,NX", [
+    ((4, 6, 16), (PER, PER, NEU), 8),        # (nz, ny, nx); bc per axis x, y, z
+    ((3, 4, 24), (NEU, PER, NEU), 8),
+    ((5, 2, 12), (PER, NEU, PER), 4),
+    ((2, 3, 8), (NEU, NEU, NEU), 8),         # one segment: both ends are walls
+])
+def test_segmented_apply_equals_operator(shape, bc, NX):
+    rng = np.random.default_rng(sum(shape) + NX)
+    level = OM.Level(rng.uniform(0.05, 1.0, shape), rng.uniform(1.0, 20.0, shape), (0.3, 0.5, 0.7), bc)
+    x = rng.standard_normal(shape)
+    ref = level.op.apply(x)
+    got = _segmented_apply(level, x, NX)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_segmented_apply_needs_the_outside_cells():
+    """Planted mistake: a segment of a periodic row wrapping onto itself (the
+    whole-row rule) instead of reading the neighbouring segment's cell."""
+    shape, bc = (4, 6, 16), (PER, PER, NEU)
+    rng = np.random.default_rng(3)
+    level = OM.Level(rng.uniform(0.05, 1.0, shape), rng.uniform(1.0, 20.0, shape), (0.3, 0.5, 0.7), bc)
+    x = rng.standard_normal(shape)
+    ref = level.op.apply(x)
+    np.testing.assert_allclose(_segmented_apply(level, x, 16), ref, rtol=1e-12, atol=1e-12)   # one segment: fine
+    bad = _segmented_apply(level, x, 8, whole_row_wrap=True)
     assert not np.allclose(bad, ref, rtol=1e-6, atol=1e-6)
